@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""DPar2 time-to-fit on one GB300 (and replicas on N GPUs).
+
+One step = the whole hot path on device-resident X: two-stage compression
+(stage-1 sketch + CholeskyQR2 + projection + small SVDs, stage-2 randomized
+SVD of M) + 32 ALS iterations + the fitness (Sec. IV-A), through the C ABI.
+Default workload: FMA-shaped spectrogram-like tensor, K=8000 slices with
+I_k ~ U{100..704}, J=2049, R=10, p=10, X stored in BF16 (13.2 GB, larger
+than L2, so no L2 flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  `value` is seconds per fit (lower is better);
+`e2e` repeats the measurement with X in pinned host memory, the host->device
+upload inside the timed region; `roofline` reports the dominant stage-1
+kernel's algorithmic HBM bytes per launch over its CUDA-event duration on the
+library's stream; `cpu_baseline` times the FP64 oracle on a bounded sample.
+`--impl reference` times the oracle alone (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPar2 time-to-fit (s) & stage-1 HBM GB/s vs peak; chosen vs plain at Δfit≤1e-3"
+WORKLOAD = dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=10, q=0, seed=1002, iters=32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32"])
+    ap.add_argument("--K", type=int, default=WORKLOAD["K"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--with-plain", action="store_true", help="also time the plain form (FP32 X, per-slice launches)")
+    ap.add_argument("--cpu-slices", type=int, default=400)
+    ap.add_argument("--out", default=None)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU baseline ----
+def cpu_oracle_time(n_slices: int, seed: int = 1002):
+    """Oracle (FP64 numpy) compress + 32 iterations + direct fitness on a
+    sample of n_slices slices of the same workload; returns (seconds for the
+    sample, seconds extrapolated to K slices, cores)."""
+    import numpy as np
+
+    import synth
+    from oracle import dpar2 as od
+
+    w = WORKLOAD
+    d = synth.spectrogram_like(K=n_slices, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=seed,
+                               out_dtype=__import__("torch").bfloat16)
+    X = d["X"].double().numpy()
+    off = d["offsets"].tolist()
+    Xs = [X[off[k]:off[k + 1]] for k in range(n_slices)]
+    rng = np.random.default_rng(seed)
+    ell = w["R"] + w["p"]
+    om, om2 = rng.standard_normal((w["J"], ell)), rng.standard_normal((n_slices * w["R"], ell))
+    V0 = rng.standard_normal((w["J"], w["R"]))
+    t0 = time.perf_counter()
+    comp = od.compress(Xs, w["R"], om, om2)
+    fit = od.dpar2_als(comp, V0, max_iter=w["iters"])
+    od.fitness(Xs, fit["U"], fit["W"], fit["V"])
+    t = time.perf_counter() - t0
+    return t, t * w["K"] / n_slices, os.cpu_count()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = max(50, args.cpu_slices // 2)
+    for _ in range(args.warmup):
+        cpu_oracle_time(n)
+    ts = []
+    for _ in range(args.steps):
+        _, ext, cores = cpu_oracle_time(n)
+        ts.append(ext)
+    v = statistics.mean(ts)
+    sample = f"{n} of {WORKLOAD['K']} slices per step, FP64 numpy oracle, extrapolated linearly in K"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+                      "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": workload_config(args),
+                      "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def workload_config(args):
+    w = WORKLOAD
+    return {"workload": f"spectrogram-like |PARAFAC2+noise| K={args.K} I_k~U{{{w['Imin']}..{w['Imax']}}} "
+                        f"J={w['J']} R={w['R']} p={w['p']} q={w['q']} {w['iters']} ALS iters",
+            "K": args.K, "J": w["J"], "R": w["R"], "p": w["p"], "q": w["q"], "iters": w["iters"],
+            "x_dtype": args.dtype, "l2": "inputs larger than L2 (X > 129 MB), no flush",
+            "parallelism": "single GPU" if args.gpus == 1 else f"{args.gpus} independent replicas"}
+
+
+# ------------------------------------------------------------------- ours ----
+def main_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_12798_gb300 as pkg
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pkg.build()
+    api = pkg.load()
+    w = WORKLOAD
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}[args.dtype]
+    es = torch.empty((), dtype=tdt).element_size()
+    ld = (w["J"] + 16 // es - 1) // (16 // es) * (16 // es)
+    d = synth.spectrogram_like(K=args.K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"],
+                               device="cuda", out_dtype=tdt, ld=ld)
+    X, off = d["X"], d["offsets"]
+    N = int(off[-1])
+    ctx = api.Context(local)
+    ctx.set_timing(True)
+
+    def step(Xdev):
+        comp = ctx.compress(Xdev, off, R=w["R"], p=w["p"], q=w["q"], seed=w["seed"], J=w["J"])
+        res = ctx.fit(comp, max_iter=w["iters"], want_U=True)
+        return comp, res
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        comp, res = step(X)
+        comp.free()
+    phases = []
+    barrier()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            comp, res = step(X)
+            t = ctx.timings()
+            phases.append(t)
+            fitness = res.fitness
+            comp.free()
+        e1.record()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # per-phase averages over the timed steps (library CUDA events, its stream)
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    ell = w["R"] + w["p"]
+    xbytes = N * w["J"] * es
+    sketch_bytes = xbytes + N * ell * 4
+    project_bytes = xbytes + N * ell * 4 + args.K * ell * w["J"] * 4
+    dom = "sketch" if ph["sketch"] >= ph["project"] else "project"
+    dom_bytes = sketch_bytes if dom == "sketch" else project_bytes
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = dom_bytes / (ph[dom] * 1e-3) / 1e9
+    stage1_bytes = sketch_bytes + project_bytes
+    stage1_gbs = stage1_bytes / ((ph["sketch"] + ph["project"]) * 1e-3) / 1e9
+
+    # ---- e2e: X from pinned host memory through the public API ----
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty(N, w["J"], dtype=tdt, pin_memory=True)
+        Xh.copy_(X[:, :w["J"]].cpu())
+        Xd = torch.empty(N, ld, dtype=tdt, device="cuda")
+        for _ in range(max(1, args.warmup - 1)):
+            ctx.upload(Xh, Xd)
+            comp, res = step(Xd)
+            comp.free()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(args.steps):
+            ctx.upload(Xh, Xd)
+            comp, res = step(Xd)
+            _ = float(res.fitness)  # the result read back to the host (fitness + loss history)
+            comp.free()
+        f1.record()
+        barrier()
+        e2e_ms = f0.elapsed_time(f1) / args.steps
+        e2e = {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(N * w["J"] * es),
+               "d2h_bytes_per_step": int(8 + 8 * w["iters"] + 4 * (w["R"] * w["R"] + w["J"] * w["R"] + args.K * w["R"]))}
+        del Xh, Xd
+
+    plain = None
+    if args.with_plain:
+        Xp = torch.zeros(N, (w["J"] + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+        Xp[:, :w["J"]] = X[:, :w["J"]].float()
+        comp = ctx.compress(Xp, off, R=w["R"], p=w["p"], q=w["q"], seed=w["seed"], J=w["J"],
+                            flags=api.FLAG_PER_SLICE)
+        comp.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        comp = ctx.compress(Xp, off, R=w["R"], p=w["p"], q=w["q"], seed=w["seed"], J=w["J"],
+                            flags=api.FLAG_PER_SLICE)
+        res_p = ctx.fit(comp, max_iter=w["iters"], want_U=True, flags=api.FLAG_NO_GRAPH)
+        torch.cuda.synchronize()
+        plain = {"s": time.perf_counter() - t0, "fitness": res_p.fitness,
+                 "form": "FP32 X, per-slice launches, no CUDA graph"}
+        comp.free()
+        del Xp
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        t_s, t_ext, cores = cpu_oracle_time(args.cpu_slices)
+        cpu = {"value": t_ext, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_slices} of {args.K} slices (same generator), FP64 numpy oracle compress + "
+                         f"32 iterations + direct fitness took {t_s:.2f} s; extrapolated linearly in K"}
+
+    # launches of our kernels per step (host orchestration of capi.cu; checked against the ncu launch list)
+    launches_compress = 2 + 1 + 5 + 1 + 1 + 1 + 1 + 1 + 1 + 2 + 1 + 1 + 5 + 1 + 1 + 1 + 2 + 1 + 1
+    launches_fit = 2 + 6 * w["iters"] + 1 + 2 + 2 + 1
+    if rank == 0:
+        out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": workload_config(args),
+               "roofline": {"bound": "hbm", "kernel": f"stage-1 {dom} pass", "achieved": achieved, "peak": peak,
+                            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                            "peak_source": peak_src,
+                            "algorithmic_bytes_per_launch": dom_bytes},
+               "stage1_gbs": stage1_gbs, "stage1_frac": stage1_gbs / peak,
+               "phases_ms": ph, "fitness": fitness, "e2e": e2e, "cpu_baseline": cpu, "plain": plain,
+               "clocks": clk.summary(), "gpu_launches": (launches_compress + launches_fit) * args.steps}
+        line = json.dumps(out)
+        print(line)
+        if args.out:
+            with open(args.out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+    else:
+        main_ours(a)

@@ -1,0 +1,226 @@
+/*
+ * dpar2.h -- C ABI of the GB300 DPar2 library (libdpar2.so).
+ *
+ * DPar2 (Jang & Kang, "DPar2: Fast and Scalable PARAFAC2 Decomposition for
+ * Irregular Dense Tensors", arXiv 2203.12798) fits the PARAFAC2 model
+ * X_k ~ Q_k H S_k V^T (Def. 1, Sec. II-C; objective Eq. PARAFAC2_reform) to
+ * an irregular tensor {X_k}, k = 1..K, X_k of size I_k x J, by
+ *   1. compressing every slice with a randomized SVD, X_k ~ A_k B_k C_k^T
+ *      (Alg. 1; Eq. fstage_svd; Alg. 3 first loop),
+ *   2. compressing M = [C_1 B_1 ... C_K B_K] (J x KR) with a second
+ *      randomized SVD, M ~ D E F^T (Eq. matricization_svd),
+ *   3. running ALS on the compressed slices A_k F^(k) E D^T (Eq. Xk_final;
+ *      Sec. III-C..E; Alg. 3 repeat loop): a batched R x R SVD per slice
+ *      (Eq. q_k), the MTTKRPs of Lemmas 1-3 and the H / V / W updates.
+ *
+ * Conventions for every entry point
+ *   - All matrices are row-major.  "device" pointers are CUDA global memory
+ *     on the context's device; "host" pointers are ordinary host memory.
+ *   - Every call enqueues its work on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) and returns after that work has completed; the
+ *     caller's buffers may be reused when the call returns.
+ *   - Every call returns a dpar2_status; nothing throws across the ABI.  On
+ *     failure dpar2_last_error(ctx) gives a one-line explanation.  Argument
+ *     and shape checks happen on the host before any launch.  Faults found
+ *     on the device (non-finite values, a bounded wait that ran out) are
+ *     recorded in a device status word and reported by the call.
+ *   - The library owns dpar2_ctx and dpar2_comp objects (free them with
+ *     dpar2_destroy / dpar2_comp_free); everything else is caller-owned.
+ *   - Precision: X may be FP32, BF16 or FP16 (storage and multiplication
+ *     type, FP32 accumulation).  Gram matrices of the CholeskyQR2 steps, the
+ *     R x R Gram-Hadamard normal equations of the H, V, W updates and the
+ *     norm / fitness reductions are FP64.  All factor outputs are FP32.
+ */
+#ifndef DPAR2_H_
+#define DPAR2_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(DPAR2_BUILD) && defined(__GNUC__)
+#define DPAR2_API __attribute__((visibility("default")))
+#else
+#define DPAR2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DPAR2_OK = 0,
+  DPAR2_ERR_INVALID_ARG = 1, /* null pointer, bad option value, misaligned buffer */
+  DPAR2_ERR_SHAPE = 2,       /* K, J, R, offsets or ld inconsistent */
+  DPAR2_ERR_CUDA = 3,        /* a CUDA runtime / driver call failed */
+  DPAR2_ERR_NUMERICAL = 4,   /* non-finite values met on the device */
+  DPAR2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  DPAR2_ERR_OOM = 6,         /* device memory allocation failed */
+  DPAR2_ERR_UNSUPPORTED = 7  /* option combination not implemented */
+} dpar2_status;
+
+typedef enum { DPAR2_F32 = 0, DPAR2_BF16 = 1, DPAR2_F16 = 2 } dpar2_dtype;
+
+/* dpar2_options.flags */
+#define DPAR2_FLAG_PER_SLICE 0x1u /* stage 1 launched once per slice (the plain form) */
+#define DPAR2_FLAG_NO_GRAPH 0x2u  /* do not capture the ALS loop in a CUDA graph */
+#define DPAR2_FLAG_GENERIC 0x4u   /* CUDA-core stage-1 kernels even for 16-bit X */
+#define DPAR2_FLAG_DROP_M 0x8u    /* free M after stage 2 (identity fitness then needs X) */
+
+typedef struct {
+  int R;          /* target rank (Alg. 1 / Alg. 3 parameter), 1 <= R <= 64 */
+  int p;          /* oversampling s of Alg. 1: sketch width l = R + p <= 64 */
+  int q;          /* power-iteration exponent q of Alg. 1 (stage 1 and stage 2) */
+  uint64_t seed;  /* Philox seed of the Gaussian test matrices and of V_0 */
+  int max_iter;   /* maximum ALS iterations (Alg. 3 repeat loop) */
+  double tol;     /* stop when e_prev - e <= tol * e_prev; tol < 0: run max_iter */
+  int schedule;   /* stage-1 kernel variant: -1 = autotuned choice, >= 0 forced */
+  unsigned flags; /* DPAR2_FLAG_* */
+} dpar2_options;
+
+typedef struct dpar2_ctx dpar2_ctx;
+typedef struct dpar2_comp dpar2_comp;
+
+/* Device views of a compressed representation (library-owned memory, valid
+ * until dpar2_comp_free).  Shapes:
+ *   A       sum(I_k) x R   stage-1 left factors A_k stacked by slice (Eq. fstage_svd)
+ *   Bk      K x R          stage-1 singular values (diagonal of B_k)
+ *   M       K x J x R      block k = C_k B_k (the k-th J x R block of M), or NULL
+ *   D       J x R          stage-2 left factor (Eq. matricization_svd)
+ *   E       R              stage-2 singular values
+ *   Ft      K x R x R      F^(k) E, the k-th R x R block of F times E (Eq. verticalF)
+ *   xnorm2  K              ||X_k||_F^2 (FP64)
+ *   offsets K + 1          slice row offsets (int64, device copy)            */
+typedef struct {
+  int K, J, R, ell;
+  int64_t N; /* sum_k I_k */
+  const int64_t* offsets;
+  const float* A;
+  const float* Bk;
+  const float* M;
+  const float* D;
+  const float* E;
+  const float* Ft;
+  const double* xnorm2;
+  int32_t* rank1; /* per-slice numerical rank of the stage-1 sketch (device, K) */
+} dpar2_comp_view;
+
+/* Fill *opt with R=10, p=10, q=0, seed=0, max_iter=32, tol=-1, schedule=-1. */
+DPAR2_API dpar2_status dpar2_options_default(dpar2_options* opt);
+
+/* Create a context bound to CUDA device `device`.  Owns scratch memory that
+ * grows on demand and is reused across calls. */
+DPAR2_API dpar2_status dpar2_create(dpar2_ctx** ctx, int device);
+DPAR2_API void dpar2_destroy(dpar2_ctx* ctx);
+DPAR2_API const char* dpar2_last_error(const dpar2_ctx* ctx);
+
+/* Fill out[0..n) (device, float32) with the Gaussian stream (seed, stream_id):
+ * Philox4x32-10 (Salmon et al. SC'11) with counter (n/4 lo, n/4 hi, stream_id, 0)
+ * and key (seed lo, seed hi), Box-Muller on word pairs.  round16 != 0 rounds
+ * every value to the nearest bf16 and flushes |x| < 2^-14 to zero so that it
+ * is exact in fp32, bf16 and fp16. */
+DPAR2_API dpar2_status dpar2_gaussian(dpar2_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, float* out,
+                            int round16, void* stream);
+/* The raw 32-bit words 0..n-1 of the same Philox stream (device, uint32). */
+DPAR2_API dpar2_status dpar2_philox_words(dpar2_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, uint32_t* out,
+                                void* stream);
+
+/* Two-stage compression (Sec. III-B; Alg. 3 lines "compress slices", "M <-",
+ * "SVD(M)").
+ *   K, J         number of slices and columns (K >= 1, J >= 1)
+ *   row_offsets  host, K+1 int64, offsets[0] = 0, I_k = offsets[k+1]-offsets[k] >= 1
+ *   X            device, sum(I_k) rows of ldx elements of `dtype`; X_k is rows
+ *                offsets[k] .. offsets[k+1]-1, columns 0..J-1.  ldx >= J and
+ *                ldx * sizeof(dtype) must be a multiple of 16 bytes, X 16-byte
+ *                aligned.  Read only; must stay valid until the call returns.
+ *   opt          R, p, q, seed, schedule, flags are used.  Requires R <= J,
+ *                R + p <= min(J, 64).
+ *   omega        device J x (R+p) float32 test matrix of stage 1, or NULL for
+ *                the Gaussian stream (opt->seed, 0) rounded as in dpar2_gaussian.
+ *                For 16-bit X its values are used rounded to that type.
+ *   omega2       device (K R) x (R+p) float32 test matrix of stage 2, or NULL
+ *                for the Gaussian stream (opt->seed, 1).
+ *   out          receives a new library-owned compressed representation.
+ * Slices with I_k < R + p (or rank-deficient slices) keep only their
+ * numerical rank; the remaining columns of A_k, entries of B_k and columns
+ * of C_k B_k are zero. */
+DPAR2_API dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X,
+                            int64_t ldx, dpar2_dtype dtype, const dpar2_options* opt, const float* omega,
+                            const float* omega2, dpar2_comp** out, void* stream);
+
+/* ALS iterations on the compressed slices (Alg. 3 repeat loop, Sec. III-C..E).
+ *   comp          from dpar2_compress
+ *   opt           R must equal the compression's R; max_iter, tol, seed, flags used
+ *   V0            device J x R initial V, or NULL for the Gaussian stream (seed, 3);
+ *                 H_0 = I_R and S_k = I (W_0 = ones) always
+ *   H, V, W       device outputs R x R, J x R, K x R (S_k = diag(W(k,:)))
+ *   Upol          device output K x R x R, Z_k P_k^T of the last Q-step (Eq. q_k), or NULL
+ *   U             device output sum(I_k) x R, U_k = A_k Z_k P_k^T H (Alg. 3 last loop), or NULL
+ *   loss_history  host output of max_iter doubles (e after each iteration), or NULL
+ *   iters_run     host output, iterations performed, or NULL
+ *   fitness       host output: 1 - sum||X_k - X^_k||^2 / sum||X_k||^2 (Sec. IV-A)
+ *                 through the exact stage-1 identity (needs M), or NULL */
+DPAR2_API dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_options* opt, const float* V0,
+                       float* H, float* V, float* W, float* Upol, float* U, double* loss_history,
+                       int* iters_run, double* fitness, void* stream);
+
+/* Squared reconstruction error and fitness (Sec. IV-A) of the model
+ * X^_k = A_k Upol_k H S_k V^T.
+ *   X == NULL  identity mode: ||X_k||^2 - 2 <B_k C_k^T, Upol_k H S_k V^T> + ||Upol_k H S_k V^T||^2,
+ *              exact because A_k^T X_k = B_k C_k^T for the randomized SVD (needs M).
+ *   X != NULL  streamed mode: reads X again (same layout rules as dpar2_compress)
+ *              and sums ||X_k - A_k (Upol_k H S_k V^T)||^2 row by row.
+ *   H, V, W    device R x R, J x R, K x R;  Upol device K x R x R, or NULL to
+ *              recompute it with one Q-step from H, V, W.
+ *   sq_err, fitness  host outputs (either may be NULL). */
+DPAR2_API dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, const void* X, int64_t ldx,
+                                     dpar2_dtype dtype, const float* H, const float* V, const float* W,
+                                     const float* Upol, double* sq_err, double* fitness, void* stream);
+
+/* Copy `rows` rows of J elements of `dtype` from host memory (rows packed,
+ * row stride J; pinned memory gives asynchronous, full-bandwidth copies) into
+ * the device layout dpar2_compress reads (row stride ldx elements, X_dev
+ * 16-byte aligned).  Columns J..ldx-1 of X_dev are set to zero.  One 2-D copy. */
+DPAR2_API dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* X_host, int64_t rows, int J, dpar2_dtype dtype,
+                                         void* X_dev, int64_t ldx, void* stream);
+
+/* Phase timing.  With timing enabled the library records CUDA events on its
+ * work stream around the phases of every dpar2_compress / dpar2_fit call;
+ * dpar2_last_timings copies the durations (milliseconds) of the phases of
+ * the most recent calls into ms[0..n) and returns how many it wrote.  Phase
+ * indices: */
+#define DPAR2_PH_SKETCH 0   /* stage-1 sketch pass Y = X Omega over all slices */
+#define DPAR2_PH_QR 1       /* CholeskyQR2 of the sketches (+ power iterations) */
+#define DPAR2_PH_PROJECT 2  /* stage-1 projection pass B = Q^T X and ||X_k||^2 */
+#define DPAR2_PH_SMALL 3    /* small SVDs, blocks C_k B_k of M, A_k */
+#define DPAR2_PH_STAGE2 4   /* randomized SVD of M -> D, E, F */
+#define DPAR2_PH_COMPRESS 5 /* whole dpar2_compress */
+#define DPAR2_PH_ALS 6      /* the ALS iterations of dpar2_fit */
+#define DPAR2_PH_OUTPUT 7   /* V, U, fitness of dpar2_fit */
+#define DPAR2_NUM_PHASES 8
+DPAR2_API dpar2_status dpar2_set_timing(dpar2_ctx* ctx, int enable);
+DPAR2_API int dpar2_last_timings(const dpar2_ctx* ctx, double* ms, int n);
+
+/* Bytes of the preprocessed data in the sense of Theorem 2 (A_k, F^(k), D,
+ * E stored as float32): 4 (sum_k I_k R + K R^2 + J R + R). */
+DPAR2_API size_t dpar2_comp_bytes(const dpar2_comp* comp);
+/* Device bytes the object actually holds (adds B_k, M, ||X_k||^2, offsets). */
+DPAR2_API size_t dpar2_comp_device_bytes(const dpar2_comp* comp);
+DPAR2_API dpar2_status dpar2_comp_view_get(const dpar2_comp* comp, dpar2_comp_view* view);
+DPAR2_API void dpar2_comp_free(dpar2_comp* comp);
+
+/* Learned sketch (range-finder loss of a trainable test matrix Omega):
+ *   L(Omega) = (1/K) sum_k ||X_k - Y_k Y_k^+ X_k||_F^2 / ||X_k||_F^2,  Y_k = X_k Omega,
+ * the quantity Alg. 1's range finder leaves out of each slice.
+ * dpar2_sketch_loss_fwd computes L (host double) and saves what the backward
+ * pass needs in the context; dpar2_sketch_loss_bwd writes dL/dOmega
+ * (device J x l float32) for the same X and Omega, scaled by grad_scale.
+ *   X, row_offsets, ldx, dtype as for dpar2_compress; omega device J x l, l <= 64. */
+DPAR2_API dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X,
+                                   int64_t ldx, dpar2_dtype dtype, const float* omega, int ell,
+                                   double* loss, void* stream);
+DPAR2_API dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, float* grad_omega, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPAR2_H_ */

@@ -1,0 +1,269 @@
+"""Python binding of libdpar2 (ctypes over the C ABI of include/dpar2.h).
+
+Argument marshalling only: tensors are passed as raw device pointers together
+with the current torch CUDA stream; every numerical step runs in the
+library's kernels.  The library must be built (``build.build()``); importing
+this module on a machine without it raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from .build import LIB
+
+F32, BF16, F16 = 0, 1, 2
+_DT = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+FLAG_PER_SLICE, FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_DROP_M = 0x1, 0x2, 0x4, 0x8
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "CUDA", 4: "NUMERICAL", 5: "TIMEOUT", 6: "OOM",
+          7: "UNSUPPORTED"}
+
+
+class Dpar2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dpar2 {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("schedule", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+
+class CompView(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("J", ctypes.c_int), ("R", ctypes.c_int), ("ell", ctypes.c_int),
+                ("N", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("Bk", ctypes.c_void_p), ("M", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("Ft", ctypes.c_void_p), ("xnorm2", ctypes.c_void_p), ("rank1", ctypes.c_void_p)]
+
+
+_lib = None
+VP, I64, DP = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); mirrors include/dpar2.h
+SIGNATURES = {
+    "dpar2_options_default": (ctypes.c_int, [ctypes.POINTER(Options)]),
+    "dpar2_create": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.c_int]),
+    "dpar2_destroy": (None, [VP]),
+    "dpar2_last_error": (ctypes.c_char_p, [VP]),
+    "dpar2_gaussian": (ctypes.c_int, [VP, ctypes.c_uint64, ctypes.c_uint32, I64, VP, ctypes.c_int, VP]),
+    "dpar2_philox_words": (ctypes.c_int, [VP, ctypes.c_uint64, ctypes.c_uint32, I64, VP, VP]),
+    "dpar2_compress": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP, I64,
+                                      ctypes.c_int, ctypes.POINTER(Options), VP, VP, ctypes.POINTER(VP), VP]),
+    "dpar2_fit": (ctypes.c_int, [VP, VP, ctypes.POINTER(Options), VP, VP, VP, VP, VP, VP, DP,
+                                 ctypes.POINTER(ctypes.c_int), DP, VP]),
+    "dpar2_reconstruct_error": (ctypes.c_int, [VP, VP, VP, I64, ctypes.c_int, VP, VP, VP, VP, DP, DP, VP]),
+    "dpar2_comp_bytes": (ctypes.c_size_t, [VP]),
+    "dpar2_comp_device_bytes": (ctypes.c_size_t, [VP]),
+    "dpar2_comp_view_get": (ctypes.c_int, [VP, ctypes.POINTER(CompView)]),
+    "dpar2_comp_free": (None, [VP]),
+    "dpar2_sketch_loss_fwd": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP,
+                                             I64, ctypes.c_int, VP, ctypes.c_int, DP, VP]),
+    "dpar2_sketch_loss_bwd": (ctypes.c_int, [VP, ctypes.c_double, VP, VP]),
+    "dpar2_upload_rows": (ctypes.c_int, [VP, VP, I64, ctypes.c_int, ctypes.c_int, VP, I64, VP]),
+    "dpar2_set_timing": (ctypes.c_int, [VP, ctypes.c_int]),
+    "dpar2_last_timings": (ctypes.c_int, [VP, DP, ctypes.c_int]),
+}
+
+PHASES = ["sketch", "qr", "project", "small", "stage2", "compress", "als", "output"]
+
+
+def lib():
+    """Load libdpar2.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_2203_12798_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context bound to one CUDA device (owns reusable scratch)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self._h = ctypes.c_void_p()
+        self._check(lib().dpar2_create(ctypes.byref(self._h), device), "dpar2_create")
+
+    def _check(self, code, what=""):
+        if code != 0:
+            msg = lib().dpar2_last_error(self._h).decode() if self._h else what
+            raise Dpar2Error(code, msg or what)
+
+    def close(self):
+        if self._h:
+            lib().dpar2_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, Xh: torch.Tensor, Xd: torch.Tensor):
+        """Host rows (rows x J, packed; pinned for async) -> device rows with row stride Xd.stride(0)."""
+        assert Xh.dim() == 2 and Xh.is_contiguous() and Xd.dim() == 2 and Xd.stride(1) == 1
+        self._check(lib().dpar2_upload_rows(self._h, _ptr(Xh), Xh.shape[0], Xh.shape[1], _DT[Xh.dtype], _ptr(Xd),
+                                            Xd.stride(0), _stream()))
+
+    # ------------------------------------------------------------- timing
+    def set_timing(self, on: bool = True):
+        self._check(lib().dpar2_set_timing(self._h, int(on)))
+
+    def timings(self) -> dict:
+        """Milliseconds of each phase of the last compress / fit (CUDA events
+        recorded on the library's work stream)."""
+        buf = (ctypes.c_double * len(PHASES))()
+        n = lib().dpar2_last_timings(self._h, buf, len(PHASES))
+        return {PHASES[i]: buf[i] for i in range(n)}
+
+    # ------------------------------------------------------------- RNG
+    def gaussian(self, seed: int, stream_id: int, n: int, round16: bool = True, out=None):
+        out = torch.empty(n, dtype=torch.float32, device=f"cuda:{self.device}") if out is None else out
+        self._check(lib().dpar2_gaussian(self._h, seed, stream_id, n, _ptr(out), int(round16), _stream()))
+        return out
+
+    def philox_words(self, seed: int, stream_id: int, n: int):
+        out = torch.empty(n, dtype=torch.int32, device=f"cuda:{self.device}")
+        self._check(lib().dpar2_philox_words(self._h, seed, stream_id, n, _ptr(out), _stream()))
+        return out
+
+    # ------------------------------------------------------------- method
+    def compress(self, X: torch.Tensor, offsets, R=10, p=10, q=0, seed=0, omega=None, omega2=None, flags=0,
+                 J=None, schedule=-1) -> "Compressed":
+        """X: CUDA tensor (sum I_k) x ldx of float32/bfloat16/float16 (columns >= J ignored)."""
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        J = X.shape[1] if J is None else J
+        off = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
+        K = off.numel() - 1
+        opt = Options()
+        lib().dpar2_options_default(ctypes.byref(opt))
+        opt.R, opt.p, opt.q, opt.seed, opt.flags, opt.schedule = R, p, q, seed, flags, schedule
+        h = ctypes.c_void_p()
+        offp = ctypes.cast(off.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+        self._check(lib().dpar2_compress(self._h, K, J, offp, _ptr(X), X.stride(0), _DT[X.dtype],
+                                         ctypes.byref(opt), _ptr(omega), _ptr(omega2), ctypes.byref(h),
+                                         _stream()))
+        return Compressed(self, h, off)
+
+    def fit(self, comp: "Compressed", max_iter=32, tol=-1.0, seed=0, V0=None, want_U=False, want_upol=True,
+            fitness=True, flags=0):
+        v = comp.view()
+        dev = f"cuda:{self.device}"
+        H = torch.empty(v.R, v.R, device=dev)
+        V = torch.empty(v.J, v.R, device=dev)
+        W = torch.empty(v.K, v.R, device=dev)
+        Up = torch.empty(v.K, v.R, v.R, device=dev) if want_upol else None
+        U = torch.empty(v.N, v.R, device=dev) if want_U else None
+        hist = (ctypes.c_double * max_iter)()
+        iters = ctypes.c_int(0)
+        fit = ctypes.c_double(0.0)
+        opt = Options()
+        lib().dpar2_options_default(ctypes.byref(opt))
+        opt.R, opt.max_iter, opt.tol, opt.seed, opt.flags = v.R, max_iter, tol, seed, flags
+        self._check(lib().dpar2_fit(self._h, comp._h, ctypes.byref(opt), _ptr(V0), _ptr(H), _ptr(V), _ptr(W),
+                                    _ptr(Up), _ptr(U), hist, ctypes.byref(iters),
+                                    ctypes.byref(fit) if fitness else None, _stream()))
+        return FitResult(H=H, V=V, W=W, Upol=Up, U=U, losses=list(hist)[:iters.value], iters=iters.value,
+                         fitness=fit.value if fitness else None)
+
+    def reconstruct_error(self, comp: "Compressed", H, V, W, Upol=None, X=None):
+        sq = ctypes.c_double()
+        fit = ctypes.c_double()
+        ldx = X.stride(0) if X is not None else 0
+        dt = _DT[X.dtype] if X is not None else 0
+        self._check(lib().dpar2_reconstruct_error(self._h, comp._h, _ptr(X), ldx, dt, _ptr(H), _ptr(V), _ptr(W),
+                                                  _ptr(Upol), ctypes.byref(sq), ctypes.byref(fit), _stream()))
+        return sq.value, fit.value
+
+
+@dataclass
+class FitResult:
+    H: torch.Tensor
+    V: torch.Tensor
+    W: torch.Tensor
+    Upol: torch.Tensor
+    U: torch.Tensor
+    losses: list
+    iters: int
+    fitness: float
+
+
+class Compressed:
+    """Library-owned compressed representation (A_k, B_k, M, D, E, F^(k)E)."""
+
+    def __init__(self, ctx: Context, h, offsets):
+        self.ctx = ctx
+        self._h = h
+        self.offsets = offsets
+
+    def view(self) -> CompView:
+        v = CompView()
+        self.ctx._check(lib().dpar2_comp_view_get(self._h, ctypes.byref(v)))
+        return v
+
+    def nbytes(self) -> int:
+        return int(lib().dpar2_comp_bytes(self._h))
+
+    def device_nbytes(self) -> int:
+        return int(lib().dpar2_comp_device_bytes(self._h))
+
+    def tensors(self):
+        """Copies of the compressed factors as torch tensors (for inspection)."""
+        v = self.view()
+        dev = f"cuda:{self.ctx.device}"
+
+        def cp(ptr, shape, dtype=torch.float32):
+            out = torch.empty(shape, dtype=dtype, device=dev)
+            if ptr:
+                nb = out.numel() * out.element_size()
+                src = _DevPtr(ptr, nb)
+                out.view(-1).view(torch.uint8).copy_(src.as_tensor(dev))
+            return out
+
+        R, K, J, N = v.R, v.K, v.J, v.N
+        return dict(A=cp(v.A, (N, R)), Bk=cp(v.Bk, (K, R)), M=cp(v.M, (K, J, R)) if v.M else None,
+                    D=cp(v.D, (J, R)), E=cp(v.E, (R,)), Ft=cp(v.Ft, (K, R, R)),
+                    xnorm2=cp(v.xnorm2, (K,), torch.float64), rank1=cp(v.rank1, (K,), torch.int32))
+
+    def free(self):
+        if self._h:
+            lib().dpar2_comp_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _DevPtr:
+    """Wraps a raw device pointer as a uint8 torch tensor through __cuda_array_interface__."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+    def as_tensor(self, dev):
+        return torch.as_tensor(self, device=dev)

@@ -1,0 +1,722 @@
+// C ABI of libdpar2: argument checks, scratch management and the launch
+// sequence of the two-stage compression (Sec. III-B) and of the ALS
+// iterations (Alg. 3).  Every numerical step runs in the kernels of this
+// library; the host only validates, allocates, launches and reads back the
+// status word and the requested scalars.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace dp2;
+
+namespace {
+
+struct Fail {
+  dpar2_status st;
+  std::string msg;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{e == cudaErrorMemoryAllocation ? DPAR2_ERR_OOM : DPAR2_ERR_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+#define CK(x) ck((x), #x)
+
+inline void require(bool c, dpar2_status st, const std::string& msg) {
+  if (!c) throw Fail{st, msg};
+}
+
+template <typename T>
+T* wsget(dpar2_ctx* ctx, const char* name, size_t count) {
+  void* p = ctx->get(name, count * sizeof(T));
+  if (!p) throw Fail{DPAR2_ERR_OOM, std::string("cannot allocate scratch '") + name + "'"};
+  return static_cast<T*>(p);
+}
+
+void alloc(dp2::DevBuf& b, size_t bytes) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    throw Fail{DPAR2_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+  }
+  b.bytes = bytes;
+}
+
+size_t dtype_size(dpar2_dtype dt) { return dt == DPAR2_F32 ? 4 : 2; }
+
+// Runs `body` with the context's device current and a private work stream
+// ordered after `user` work; converts failures into status codes.
+template <typename F>
+dpar2_status guarded(dpar2_ctx* ctx, void* user_stream, F&& body) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  try {
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t us = static_cast<cudaStream_t>(user_stream);
+    cudaStream_t work = reinterpret_cast<cudaStream_t>(ctx->ws["__work_stream"].p);
+    cudaEvent_t ev = reinterpret_cast<cudaEvent_t>(ctx->ws["__event"].p);
+    CK(cudaEventRecord(ev, us));
+    CK(cudaStreamWaitEvent(work, ev, 0));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), work));
+    body(work);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, work));
+    CK(cudaStreamSynchronize(work));
+    for (int ph = 0; ph < DPAR2_NUM_PHASES; ++ph) {
+      if (!ctx->tpending[ph]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ctx->tev[2 * ph], ctx->tev[2 * ph + 1]) == cudaSuccess) ctx->tms[ph] = ms;
+      cudaGetLastError();
+      ctx->tpending[ph] = false;
+    }
+    const int st = *ctx->h_status;
+    if (st & ST_TIMEOUT) throw Fail{DPAR2_ERR_TIMEOUT, "a bounded device-side wait gave up"};
+    if (st & ST_NONFINITE) throw Fail{DPAR2_ERR_NUMERICAL, "non-finite values met on the device"};
+  } catch (const Fail& f) {
+    ctx->err = f.msg;
+    if (prev >= 0) cudaSetDevice(prev);
+    return f.st;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return DPAR2_OK;
+}
+
+inline void tbegin(dpar2_ctx* c, cudaStream_t s, int ph) {
+  if (c->timing) cudaEventRecord(c->tev[2 * ph], s);
+}
+inline void tend(dpar2_ctx* c, cudaStream_t s, int ph) {
+  if (c->timing) {
+    cudaEventRecord(c->tev[2 * ph + 1], s);
+    c->tpending[ph] = true;
+  }
+}
+
+// CholeskyQR2 of the per-slice sketches Y (rows x LP, in place): after the
+// call Y holds Q1 = Y R1^+ and M2 = R2^+ with Q = Q1 M2 column-orthonormal on
+// its numerical rank (FP64 Grams; dependent columns dropped).
+void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI, int ell, int LP, float* M2,
+             int* rank, cudaStream_t s, const char* tag) {
+  std::string t(tag);
+  double* G = wsget<double>(ctx, (t + "_G").c_str(), (size_t)K * LP * LP);
+  float* M1 = wsget<float>(ctx, (t + "_M1").c_str(), (size_t)K * LP * LP);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, s);
+  launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, s);
+  launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, s);
+  launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, s);
+}
+
+__global__ void k_b1_to_omk(const float* __restrict__ B1, int K, int ell, int LP, int J, int Jp, int Jpad,
+                            float* __restrict__ omk) {
+  const int64_t n = (int64_t)K * Jpad * LP;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / ((int64_t)Jpad * LP);
+    const int rem = (int)(i % ((int64_t)Jpad * LP));
+    const int j = rem / LP, c = rem % LP;
+    omk[i] = (j < J && c < ell) ? B1[(k * LP + c) * Jp + j] : 0.f;
+  }
+}
+
+__global__ void k_apply_m2(float* __restrict__ Y, const int64_t* __restrict__ off, int LP,
+                           const float* __restrict__ M2) {
+  // Y_k <- Y_k M2_k row by row (generic LP, used once per power iteration)
+  const int k = blockIdx.y;
+  const int64_t row = off[k] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= off[k + 1]) return;
+  float y[kMaxEll];
+  for (int c = 0; c < LP; ++c) y[c] = Y[row * LP + c];
+  const float* m = M2 + (int64_t)k * LP * LP;
+  for (int c = 0; c < LP; ++c) {
+    float s = 0.f;
+    for (int i = 0; i < LP; ++i) s = fmaf(y[i], m[i * LP + c], s);
+    Y[row * LP + c] = s;
+  }
+}
+
+__global__ void k_sum_f64(const double* __restrict__ v, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ ctx / comp ----
+void* dpar2_ctx::get(const std::string& name, size_t bytes) {
+  auto& b = ws[name];
+  if (b.p && b.bytes >= bytes) return b.p;
+  if (b.p) {
+    cudaDeviceSynchronize();
+    cudaFree(b.p);
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+  const size_t want = std::max<size_t>(bytes, 256);
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return nullptr;
+  }
+  b.bytes = want;
+  return b.p;
+}
+
+size_t dpar2_comp::device_bytes() const {
+  return offsets.bytes + A.bytes + Bk.bytes + M.bytes + D.bytes + E.bytes + Ft.bytes + xnorm2.bytes + rank1.bytes +
+         DtD.bytes;
+}
+
+dpar2_comp::~dpar2_comp() {
+  for (dp2::DevBuf* b : {&offsets, &A, &Bk, &M, &D, &E, &Ft, &xnorm2, &rank1, &DtD})
+    if (b->p) cudaFree(b->p);
+}
+
+extern "C" {
+
+dpar2_status dpar2_options_default(dpar2_options* opt) {
+  if (!opt) return DPAR2_ERR_INVALID_ARG;
+  opt->R = 10;
+  opt->p = 10;
+  opt->q = 0;
+  opt->seed = 0;
+  opt->max_iter = 32;
+  opt->tol = -1.0;
+  opt->schedule = -1;
+  opt->flags = 0;
+  return DPAR2_OK;
+}
+
+dpar2_status dpar2_create(dpar2_ctx** out, int device) {
+  if (!out) return DPAR2_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return DPAR2_ERR_CUDA;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return DPAR2_ERR_CUDA;
+  dpar2_ctx* ctx = new dpar2_ctx();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaStream_t work;
+  cudaEvent_t ev;
+  if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    if (prev >= 0) cudaSetDevice(prev);
+    return DPAR2_ERR_CUDA;
+  }
+  for (int i = 0; i < 2 * DPAR2_NUM_PHASES; ++i) cudaEventCreate(&ctx->tev[i]);
+  ctx->ws["__work_stream"].p = reinterpret_cast<void*>(work);
+  ctx->ws["__event"].p = reinterpret_cast<void*>(ev);
+  *out = ctx;
+  if (prev >= 0) cudaSetDevice(prev);
+  return DPAR2_OK;
+}
+
+void dpar2_destroy(dpar2_ctx* ctx) {
+  if (!ctx) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->ws) {
+    if (!kv.second.p) continue;
+    if (kv.first == "__work_stream") cudaStreamDestroy(reinterpret_cast<cudaStream_t>(kv.second.p));
+    else if (kv.first == "__event") cudaEventDestroy(reinterpret_cast<cudaEvent_t>(kv.second.p));
+    else cudaFree(kv.second.p);
+  }
+  for (int i = 0; i < 2 * DPAR2_NUM_PHASES; ++i)
+    if (ctx->tev[i]) cudaEventDestroy(ctx->tev[i]);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  delete ctx;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+const char* dpar2_last_error(const dpar2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* Xh, int64_t rows, int J, dpar2_dtype dtype, void* Xd,
+                               int64_t ldx, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!Xh || !Xd || rows < 0 || J < 1 || ldx < J) {
+    ctx->err = "dpar2_upload_rows: null buffer or ldx < J";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  const size_t es = dtype_size(dtype);
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    if (rows == 0) return;
+    if (ldx > J) CK(cudaMemset2DAsync(static_cast<char*>(Xd) + J * es, ldx * es, 0, (ldx - J) * es, rows, s));
+    CK(cudaMemcpy2DAsync(Xd, ldx * es, Xh, J * es, J * es, rows, cudaMemcpyHostToDevice, s));
+  });
+}
+
+dpar2_status dpar2_set_timing(dpar2_ctx* ctx, int enable) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return DPAR2_OK;
+}
+
+int dpar2_last_timings(const dpar2_ctx* ctx, double* ms, int n) {
+  if (!ctx || !ms) return 0;
+  const int m = std::min(n, (int)DPAR2_NUM_PHASES);
+  for (int i = 0; i < m; ++i) ms[i] = ctx->tms[i];
+  return m;
+}
+
+dpar2_status dpar2_gaussian(dpar2_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, float* out, int round16,
+                            void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!out || n < 0) {
+    ctx->err = "dpar2_gaussian: out is null or n < 0";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    if (n > 0) launch_gaussian(seed, stream_id, n, out, round16, s);
+  });
+}
+
+dpar2_status dpar2_philox_words(dpar2_ctx* ctx, uint64_t seed, uint32_t stream_id, int64_t n, uint32_t* out,
+                                void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!out || n < 0) {
+    ctx->err = "dpar2_philox_words: out is null or n < 0";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    if (n > 0) launch_philox_words(seed, stream_id, n, out, s);
+  });
+}
+
+// --------------------------------------------------------------- compress ----
+dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X, int64_t ldx,
+                            dpar2_dtype dtype, const dpar2_options* opt, const float* omega, const float* omega2,
+                            dpar2_comp** out, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  dpar2_comp* comp = nullptr;
+  auto chk = [&]() -> dpar2_status {
+    try {
+      require(out != nullptr, DPAR2_ERR_INVALID_ARG, "out is null");
+      *out = nullptr;
+      require(opt && X && row_offsets, DPAR2_ERR_INVALID_ARG, "opt, X and row_offsets must be non-null");
+      require(dtype == DPAR2_F32 || dtype == DPAR2_BF16 || dtype == DPAR2_F16, DPAR2_ERR_INVALID_ARG, "bad dtype");
+      require(K >= 1 && J >= 1, DPAR2_ERR_SHAPE, "K and J must be >= 1");
+      require(opt->R >= 1 && opt->R <= kMaxR && opt->R <= J, DPAR2_ERR_SHAPE, "need 1 <= R <= min(J, 64)");
+      require(opt->p >= 0 && opt->R + opt->p <= std::min(J, kMaxEll), DPAR2_ERR_SHAPE, "need R + p <= min(J, 64)");
+      require(opt->q >= 0 && opt->q <= 8, DPAR2_ERR_INVALID_ARG, "need 0 <= q <= 8");
+      require(ldx >= J, DPAR2_ERR_SHAPE, "ldx < J");
+      require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
+              "ldx * sizeof(dtype) must be a multiple of 16 bytes");
+      require((reinterpret_cast<uintptr_t>(X) & 15) == 0, DPAR2_ERR_INVALID_ARG, "X must be 16-byte aligned");
+      require(row_offsets[0] == 0, DPAR2_ERR_SHAPE, "row_offsets[0] must be 0");
+      for (int k = 0; k < K; ++k)
+        require(row_offsets[k + 1] > row_offsets[k], DPAR2_ERR_SHAPE, "every slice needs I_k >= 1 rows");
+      return DPAR2_OK;
+    } catch (const Fail& f) {
+      ctx->err = f.msg;
+      return f.st;
+    }
+  };
+  dpar2_status st0 = chk();
+  if (st0 != DPAR2_OK) return st0;
+
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    const int R = opt->R, ell = opt->R + opt->p, LP = round_up(ell, 8);
+    const int Jp = round_up(J, 4), Jpad = round_up(J, 32);
+    const int64_t N = row_offsets[K];
+    int64_t maxI = 0;
+    for (int k = 0; k < K; ++k) maxI = std::max<int64_t>(maxI, row_offsets[k + 1] - row_offsets[k]);
+    comp = new dpar2_comp();
+    comp->K = K;
+    comp->J = J;
+    comp->R = R;
+    comp->ell = ell;
+    comp->LP = LP;
+    comp->N = N;
+    comp->maxI = maxI;
+    comp->h_offsets.assign(row_offsets, row_offsets + K + 1);
+    alloc(comp->offsets, (K + 1) * sizeof(int64_t));
+    alloc(comp->A, (size_t)N * R * 4);
+    alloc(comp->Bk, (size_t)K * R * 4);
+    alloc(comp->M, (size_t)K * J * R * 4);
+    alloc(comp->D, (size_t)J * R * 4);
+    alloc(comp->E, (size_t)R * 4);
+    alloc(comp->Ft, (size_t)K * R * R * 4);
+    alloc(comp->xnorm2, (size_t)K * 8);
+    alloc(comp->rank1, (size_t)K * 4);
+    alloc(comp->DtD, (size_t)R * R * 8);
+    int64_t* d_off = static_cast<int64_t*>(comp->offsets.p);
+    CK(cudaMemcpyAsync(d_off, row_offsets, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const size_t es = dtype_size(dtype);
+
+    // ---- test matrix Omega (Alg. 1, "generate a Gaussian test matrix") ----
+    const float* om = omega;
+    if (!om) {
+      float* g = wsget<float>(ctx, "omega", (size_t)J * ell);
+      launch_gaussian(opt->seed, 0, (int64_t)J * ell, g, 1, s);
+      om = g;
+    }
+    tbegin(ctx, s, DPAR2_PH_COMPRESS);
+    float* om_pad = wsget<float>(ctx, "om_pad", (size_t)Jpad * LP);
+    launch_pad_omega(om, J, ell, Jpad, LP, dtype, om_pad, s);
+
+    // ---- sketch Y = X Omega (pass 1 over X) ----
+    float* Y = wsget<float>(ctx, "Y", (size_t)N * LP);
+    float* M2 = wsget<float>(ctx, "M2", (size_t)K * LP * LP);
+    float* B1 = wsget<float>(ctx, "B1", (size_t)K * LP * Jp);
+    const int nJb = project_blocks(Jp, LP);
+    double* xpart = wsget<double>(ctx, "xpart", (size_t)K * nJb);
+    tbegin(ctx, s, DPAR2_PH_SKETCH);
+    if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+      for (int k = 0; k < K; ++k) {
+        const int64_t r0 = row_offsets[k], nk = row_offsets[k + 1] - r0;
+        launch_sketch_generic(static_cast<const char*>(X) + r0 * ldx * es, dtype, ldx, nk, J, om_pad, LP,
+                              Y + r0 * LP, s);
+      }
+    } else {
+      launch_sketch_generic(X, dtype, ldx, N, J, om_pad, LP, Y, s);
+    }
+    tend(ctx, s, DPAR2_PH_SKETCH);
+    tbegin(ctx, s, DPAR2_PH_QR);
+    cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
+    // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
+    for (int it = 0; it < opt->q; ++it) {
+      k_apply_m2<<<dim3((unsigned)((maxI + 127) / 128), K), 128, 0, s>>>(Y, d_off, LP, M2);
+      launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, nullptr, nullptr, s);
+      float* omk = wsget<float>(ctx, "omk", (size_t)K * Jpad * LP);
+      k_b1_to_omk<<<4096, 256, 0, s>>>(B1, K, ell, LP, J, Jp, Jpad, omk);
+      launch_sketch_generic_per_slice(X, dtype, ldx, d_off, K, (int)maxI, J, omk, Jpad, LP, Y, s);
+      cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
+    }
+
+    tend(ctx, s, DPAR2_PH_QR);
+    // ---- projection B1 = Q1^T X (pass 2 over X) and ||X_k||^2 ----
+    tbegin(ctx, s, DPAR2_PH_PROJECT);
+    if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+      for (int k = 0; k < K; ++k)
+        launch_project_generic(X, dtype, ldx, d_off + k, 1, J, Jp, Y, LP, B1 + (size_t)k * LP * Jp,
+                               xpart + (size_t)k * nJb, nullptr, s);
+    } else {
+      launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, xpart, nullptr, s);
+    }
+    tend(ctx, s, DPAR2_PH_PROJECT);
+    tbegin(ctx, s, DPAR2_PH_SMALL);
+    launch_reduce_rows_f64(xpart, K, nJb, static_cast<double*>(comp->xnorm2.p), s);
+
+    // ---- small SVD of B = M2^T B1 -> C_k B_k blocks of M, T_k, A_k ----
+    double* GB = wsget<double>(ctx, "GB", (size_t)K * LP * LP);
+    float* T = wsget<float>(ctx, "T", (size_t)K * LP * R);
+    launch_gram_b1(B1, Jp, J, K, LP, GB, s);
+    launch_eig_top(GB, M2, K, ell, LP, R, T, nullptr, ctx->d_status, s);
+    launch_mblock(B1, Jp, J, K, ell, LP, R, T, static_cast<float*>(comp->Bk.p), static_cast<float*>(comp->M.p),
+                  static_cast<int*>(comp->rank1.p), 1e-5f, s);
+    launch_seg_product(Y, LP, LP, T, (int64_t)LP * R, R, static_cast<float*>(comp->A.p), R, d_off, K, maxI, s);
+
+    tend(ctx, s, DPAR2_PH_SMALL);
+    // ---- stage 2: randomized SVD of M (J x KR) ----
+    tbegin(ctx, s, DPAR2_PH_STAGE2);
+    const int64_t KR = (int64_t)K * R;
+    const float* om2 = omega2;
+    if (!om2) {
+      float* g = wsget<float>(ctx, "omega2", (size_t)KR * ell);
+      launch_gaussian(opt->seed, 1, KR * ell, g, 1, s);
+      om2 = g;
+    }
+    float* om2p = wsget<float>(ctx, "om2_pad", (size_t)KR * LP);
+    launch_pad_omega(om2, (int)KR, ell, (int)KR, LP, DPAR2_F32, om2p, s);
+    const int kchunk = std::max(1, std::min(64, 12288 / (R * LP)));
+    const int nch = (K + kchunk - 1) / kchunk;
+    float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nch * J * LP);
+    float* Y2 = wsget<float>(ctx, "Y2", (size_t)J * LP);
+    launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, om2p, LP, Y2p, kchunk, s);
+    launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+    int64_t* off2 = wsget<int64_t>(ctx, "off2", 4);
+    const int64_t h_off2[4] = {0, (int64_t)J, 0, KR};
+    CK(cudaMemcpyAsync(off2, h_off2, sizeof(h_off2), cudaMemcpyHostToDevice, s));
+    float* M2s = wsget<float>(ctx, "M2s", (size_t)LP * LP);
+    cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
+    for (int it = 0; it < opt->q; ++it) {
+      // Y2 <- M (M^T Q2): reuse the stage-2 kernels with Omega2 := M^T Q2
+      k_apply_m2<<<dim3((unsigned)((J + 127) / 128), 1), 128, 0, s>>>(Y2, off2, LP, M2s);
+      float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
+      launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
+      launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, B2p, LP, Y2p, kchunk, s);
+      launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+      cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
+    }
+    float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
+    launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
+    double* G2 = wsget<double>(ctx, "G2", (size_t)LP * LP);
+    launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, s);
+    float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
+    launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
+    launch_seg_product(Y2, LP, LP, T2, 0, R, static_cast<float*>(comp->D.p), R, off2, 1, J, s);
+    launch_seg_product(B2p, LP, LP, T2, 0, R, static_cast<float*>(comp->Ft.p), R, off2 + 2, 1, KR, s);
+    launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
+                    static_cast<float*>(comp->E.p), 1e-6f, s);
+    launch_ata(static_cast<const float*>(comp->D.p), J, R, static_cast<double*>(comp->DtD.p), s);
+    tend(ctx, s, DPAR2_PH_STAGE2);
+    tend(ctx, s, DPAR2_PH_COMPRESS);
+    if (opt->flags & DPAR2_FLAG_DROP_M) {
+      CK(cudaStreamSynchronize(s));
+      alloc(comp->M, 0);
+    }
+  });
+  if (st != DPAR2_OK) {
+    delete comp;
+    return st;
+  }
+  *out = comp;
+  return DPAR2_OK;
+}
+
+// -------------------------------------------------------------------- fit ----
+dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_options* opt, const float* V0, float* H,
+                       float* V, float* W, float* Upol, float* U, double* loss_history, int* iters_run,
+                       double* fitness, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!comp || !opt || !H || !V || !W) {
+    ctx->err = "comp, opt, H, V and W must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (opt->R != comp->R || opt->max_iter < 1) {
+    ctx->err = "opt->R must equal the compression's R and max_iter >= 1";
+    return DPAR2_ERR_SHAPE;
+  }
+  if (fitness && !comp->M.p) {
+    ctx->err = "fitness needs M (compressed without DPAR2_FLAG_DROP_M)";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  int iters = 0;
+  double fit_val = 0.0;
+  std::vector<double> hist(opt->max_iter, 0.0);
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    const int K = comp->K, J = comp->J, R = comp->R, RR = R * R;
+    const float* v0 = V0;
+    if (!v0) {
+      float* g = wsget<float>(ctx, "V0", (size_t)J * R);
+      launch_gaussian(opt->seed, 3, (int64_t)J * R, g, 0, s);
+      v0 = g;
+    }
+    AlsBufs b;
+    b.K = K;
+    b.J = J;
+    b.R = R;
+    b.D = static_cast<const float*>(comp->D.p);
+    b.Ft = static_cast<const float*>(comp->Ft.p);
+    b.DtD = static_cast<const double*>(comp->DtD.p);
+    b.H = H;
+    b.W = W;
+    b.CV = wsget<float>(ctx, "CV", RR);
+    b.Upol = Upol ? Upol : wsget<float>(ctx, "Upol", (size_t)K * RR);
+    b.Pi = wsget<float>(ctx, "Pi", (size_t)K * RR);
+    double* d6 = wsget<double>(ctx, "als_d", (size_t)6 * RR);
+    b.Psi = d6;
+    b.VtV = d6 + RR;
+    b.HtH = d6 + 2 * RR;
+    b.WtW = d6 + 3 * RR;
+    b.Ginv = d6 + 4 * RR;
+    b.nblk = std::max(1, std::min((K + 3) / 4, ctx->num_sms * 4));
+    b.part = wsget<float>(ctx, "als_part", (size_t)b.nblk * (2 * RR + 2));
+    b.loss = wsget<double>(ctx, "als_loss", (size_t)opt->max_iter);
+    b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR);
+    b.status = ctx->d_status;
+    tbegin(ctx, s, DPAR2_PH_ALS);
+    launch_als_init(b, v0, s);
+    if (opt->tol < 0) {
+      bool graph = !(opt->flags & DPAR2_FLAG_NO_GRAPH);
+      if (graph) {
+        cudaGraph_t g;
+        cudaGraphExec_t ge;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+        CK(cudaStreamEndCapture(s, &g));
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        CK(cudaGraphLaunch(ge, s));
+        CK(cudaStreamSynchronize(s));
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+      } else {
+        for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+      }
+      iters = opt->max_iter;
+    } else {
+      double prev = 0.0;
+      for (int it = 0; it < opt->max_iter; ++it) {
+        launch_als_iteration(b, it, s);
+        double e = 0.0;
+        CK(cudaMemcpyAsync(&e, b.loss + it, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        iters = it + 1;
+        if (it > 0 && prev - e <= opt->tol * prev) break;
+        prev = e;
+      }
+    }
+    tend(ctx, s, DPAR2_PH_ALS);
+    tbegin(ctx, s, DPAR2_PH_OUTPUT);
+    // outputs: V = D CV (Lemma 2 keeps V in span(D)), U_k = A_k Upol_k H
+    int64_t* off2 = wsget<int64_t>(ctx, "off_fit", 2);
+    const int64_t h2[2] = {0, (int64_t)J};
+    CK(cudaMemcpyAsync(off2, h2, sizeof(h2), cudaMemcpyHostToDevice, s));
+    launch_seg_product(b.D, R, R, b.CV, 0, R, V, R, off2, 1, J, s);
+    if (U) {
+      float* Tk = wsget<float>(ctx, "Tk", (size_t)K * RR);
+      launch_upol_h(K, R, b.Upol, H, Tk, s);
+      launch_seg_product(static_cast<const float*>(comp->A.p), R, R, Tk, RR, R, U, R,
+                         static_cast<const int64_t*>(comp->offsets.p), K, comp->maxI, s);
+    }
+    if (loss_history) CK(cudaMemcpyAsync(hist.data(), b.loss, iters * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (fitness) {
+      float* P = wsget<float>(ctx, "Pk", (size_t)K * RR);
+      double* fpart = wsget<double>(ctx, "fit_part", (size_t)b.nblk + 4);
+      launch_p_from_cv(K, R, b.CV, b.Ft, P, s);
+      launch_fitness(K, R, P, b.Upol, H, W, b.VtV, static_cast<const double*>(comp->xnorm2.p), fpart, b.nblk,
+                     fpart + b.nblk, s);
+      k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + b.nblk + 1);
+      tend(ctx, s, DPAR2_PH_OUTPUT);
+      double h[2];
+      CK(cudaMemcpyAsync(h, fpart + b.nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      fit_val = h[1] > 0 ? 1.0 - h[0] / h[1] : 0.0;
+    } else {
+      tend(ctx, s, DPAR2_PH_OUTPUT);
+    }
+  });
+  if (st == DPAR2_OK) {
+    if (loss_history) std::copy(hist.begin(), hist.begin() + iters, loss_history);
+    if (iters_run) *iters_run = iters;
+    if (fitness) *fitness = fit_val;
+  }
+  return st;
+}
+
+// ------------------------------------------------------ reconstruct error ----
+dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, const void* X, int64_t ldx,
+                                     dpar2_dtype dtype, const float* H, const float* V, const float* W,
+                                     const float* Upol, double* sq_err, double* fitness, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!comp || !H || !V || !W) {
+    ctx->err = "comp, H, V and W must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (X) {
+    ctx->err = "streamed mode (X != NULL) is not available in this build";
+    return DPAR2_ERR_UNSUPPORTED;
+  }
+  if (!comp->M.p) {
+    ctx->err = "identity mode needs M (compressed without DPAR2_FLAG_DROP_M)";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  (void)ldx;
+  (void)dtype;
+  double res[2] = {0, 0};
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    const int K = comp->K, J = comp->J, R = comp->R, RR = R * R;
+    double* d6 = wsget<double>(ctx, "re_d", (size_t)6 * RR);
+    double* Psi = d6;
+    double* VtV = d6 + RR;
+    launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV, s);
+    const int nblk = std::max(1, std::min((K + 3) / 4, ctx->num_sms * 4));
+    const float* up = Upol;
+    if (!up) {
+      AlsBufs b;
+      b.K = K;
+      b.J = J;
+      b.R = R;
+      b.D = static_cast<const float*>(comp->D.p);
+      b.Ft = static_cast<const float*>(comp->Ft.p);
+      b.H = const_cast<float*>(H);
+      b.W = const_cast<float*>(W);
+      b.Psi = Psi;
+      b.Upol = wsget<float>(ctx, "re_upol", (size_t)K * RR);
+      b.Pi = wsget<float>(ctx, "re_pi", (size_t)K * RR);
+      b.part = wsget<float>(ctx, "re_part", (size_t)nblk * (2 * RR + 2));
+      b.status = ctx->d_status;
+      b.nblk = nblk;
+      launch_qstep_only(b, s);
+      up = b.Upol;
+    }
+    float* P = wsget<float>(ctx, "re_P", (size_t)K * RR);
+    launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
+    double* fpart = wsget<double>(ctx, "re_fit", (size_t)nblk + 4);
+    launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk, s);
+    k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+    CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  });
+  if (st == DPAR2_OK) {
+    if (sq_err) *sq_err = res[0];
+    if (fitness) *fitness = res[1] > 0 ? 1.0 - res[0] / res[1] : 0.0;
+  }
+  return st;
+}
+
+// ------------------------------------------------------------ comp access ----
+size_t dpar2_comp_bytes(const dpar2_comp* c) {
+  if (!c) return 0;
+  return 4 * ((size_t)c->N * c->R + (size_t)c->K * c->R * c->R + (size_t)c->J * c->R + c->R);
+}
+size_t dpar2_comp_device_bytes(const dpar2_comp* c) { return c ? c->device_bytes() : 0; }
+
+dpar2_status dpar2_comp_view_get(const dpar2_comp* c, dpar2_comp_view* v) {
+  if (!c || !v) return DPAR2_ERR_INVALID_ARG;
+  v->K = c->K;
+  v->J = c->J;
+  v->R = c->R;
+  v->ell = c->ell;
+  v->N = c->N;
+  v->offsets = static_cast<const int64_t*>(c->offsets.p);
+  v->A = static_cast<const float*>(c->A.p);
+  v->Bk = static_cast<const float*>(c->Bk.p);
+  v->M = static_cast<const float*>(c->M.p);
+  v->D = static_cast<const float*>(c->D.p);
+  v->E = static_cast<const float*>(c->E.p);
+  v->Ft = static_cast<const float*>(c->Ft.p);
+  v->xnorm2 = static_cast<const double*>(c->xnorm2.p);
+  v->rank1 = static_cast<int32_t*>(c->rank1.p);
+  return DPAR2_OK;
+}
+
+void dpar2_comp_free(dpar2_comp* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  delete c;
+}
+
+dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int, int, const int64_t*, const void*, int64_t, dpar2_dtype,
+                                   const float*, int, double*, void*) {
+  if (ctx) ctx->err = "learned-sketch kernels are not available in this build";
+  return DPAR2_ERR_UNSUPPORTED;
+}
+dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double, float*, void*) {
+  if (ctx) ctx->err = "learned-sketch kernels are not available in this build";
+  return DPAR2_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

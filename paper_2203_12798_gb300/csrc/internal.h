@@ -1,0 +1,124 @@
+// Internal structures and kernel launchers of libdpar2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "dpar2.h"
+
+namespace dp2 {
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+}  // namespace dp2
+
+struct dpar2_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  int* d_status = nullptr;  // device status word (dp2::ST_*)
+  int* h_status = nullptr;  // pinned mirror
+  std::map<std::string, dp2::DevBuf> ws;  // named scratch buffers, grow-only
+  // learned-sketch forward state kept for the backward pass
+  int sk_K = 0, sk_J = 0, sk_ell = 0, sk_LP = 0;
+  int64_t sk_N = 0, sk_ldx = 0, sk_maxI = 0;
+  const void* sk_X = nullptr;
+  dpar2_dtype sk_dtype = DPAR2_F32;
+  bool sk_ready = false;
+  // phase timing (DPAR2_PH_*): start/end events on the work stream
+  bool timing = false;
+  cudaEvent_t tev[2 * DPAR2_NUM_PHASES] = {};
+  bool tpending[DPAR2_NUM_PHASES] = {};
+  double tms[DPAR2_NUM_PHASES] = {};
+  // scratch buffer of at least `bytes` bytes under `name` (contents undefined);
+  // nullptr when the allocation failed
+  void* get(const std::string& name, size_t bytes);
+};
+
+struct dpar2_comp {
+  int K = 0, J = 0, R = 0, ell = 0, LP = 0;
+  int64_t N = 0, maxI = 0;
+  std::vector<int64_t> h_offsets;
+  dp2::DevBuf offsets, A, Bk, M, D, E, Ft, xnorm2, rank1, DtD;
+  size_t device_bytes() const;
+  ~dpar2_comp();
+};
+
+namespace dp2 {
+
+// ---- RNG / operand preparation ----
+void launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t n, float* out, int round16, cudaStream_t s);
+void launch_philox_words(uint64_t seed, uint32_t stream_id, int64_t n, uint32_t* out, cudaStream_t s);
+void launch_pad_omega(const float* om, int J, int ell, int Jpad, int LP, dpar2_dtype dt, float* out,
+                      cudaStream_t s);
+
+// ---- stage 1, CUDA-core path ----
+void launch_sketch_generic(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const float* om_pad,
+                           int LP, float* Y, cudaStream_t s);
+void launch_sketch_generic_per_slice(const void* X, dpar2_dtype dt, int64_t ldx, const int64_t* d_off, int K,
+                                     int maxI, int J, const float* om_k, int Jpad, int LP, float* Y,
+                                     cudaStream_t s);
+void launch_project_generic(const void* X, dpar2_dtype dt, int64_t ldx, const int64_t* d_off, int K, int J,
+                            int Jp, const float* Q, int LP, float* B1, double* xpart, int* nJb_out,
+                            cudaStream_t s);
+int project_blocks(int Jp, int LP);
+
+// ---- per-slice small linear algebra ----
+void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, cudaStream_t s);
+void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
+                      cudaStream_t s);
+void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s);
+void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s);
+void launch_gram_b1(const float* B1, int Jp, int J, int K, int LP, double* G, cudaStream_t s);
+void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
+                    int* status, cudaStream_t s);
+void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
+                   int* rank, float tau, cudaStream_t s);
+void launch_seg_product(const float* In, int ldin, int nin, const float* T, int64_t tstride, int nout, float* Out,
+                        int ldout, const int64_t* d_off, int K, int64_t maxI, cudaStream_t s);
+
+// ---- stage 2 ----
+void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, int LP, float* Y2p, int kchunk,
+                      cudaStream_t s);
+void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cudaStream_t s);
+void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s);
+void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, cudaStream_t s);
+void launch_ata(const float* A, int64_t rows, int n, double* out, cudaStream_t s);
+
+// ---- ALS (Alg. 3 repeat loop) ----
+struct AlsBufs {
+  int K, J, R;
+  const float* D;     // J x R
+  const float* Ft;    // K x R x R  (F^(k) E)
+  const double* DtD;  // R x R
+  float* H;           // R x R
+  float* W;           // K x R
+  float* CV;          // R x R, V = D CV after the first iteration
+  float* Upol;        // K x R x R
+  float* Pi;          // K x R x R  (P_k Z_k^T F^(k) E)
+  double* Psi;        // R x R  D^T V
+  double* VtV;        // R x R
+  double* HtH;        // R x R
+  double* WtW;        // R x R
+  double* Ginv;       // R x R  (V^T V * H^T H)^+
+  float* part;        // nblk x (2 R^2 + 2) block partials
+  double* loss;       // max_iter history (device)
+  double* small;      // scratch, 8 R^2 doubles
+  int* status;
+  int nblk;
+};
+void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
+void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
+void launch_qstep_only(AlsBufs& b, cudaStream_t s);
+void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
+void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);
+void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);
+void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, cudaStream_t s);
+void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
+                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s);
+
+}  // namespace dp2

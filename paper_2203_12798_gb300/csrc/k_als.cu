@@ -1,0 +1,752 @@
+// ALS iterations on the compressed slices (Alg. 3 repeat loop; Sec. III-C..E).
+//
+// Per iteration, with F~_k = F^(k) E (R x R), Psi = D^T V (R x R):
+//   Q-step (Eq. q_k): T_k = F~_k Psi S_k H^T; one-sided Jacobi SVD
+//     T_k = Z_k Sigma_k P_k^T; Upol_k = Z_k P_k^T; Pi_k = Upol_k^T F~_k
+//     (= P_k Z_k^T F^(k) E, so Y_k = Pi_k D^T is never formed).
+//   Lemma 1: G1(:, r) = (sum_k W(k,r) Pi_k) Psi(:, r);  H = G1 (W^T W * V^T V)^+,
+//     columns normalised.
+//   Lemma 2: G2(:, r) = D g_r, g_r = sum_k W(k,r) Pi_k^T H(:, r);
+//     V = G2 (W^T W * H^T H)^+ = D CV, CV = [g_r] (.)^+, columns normalised.
+//     V stays in span(D), so Psi = D^T D CV and V^T V = CV^T D^T D CV are
+//     R x R products (D^T D from stage 2).
+//   Lemma 3: G3(k, r) = H(:, r)^T Pi_k Psi(:, r);  W = G3 (V^T V * H^T H)^+.
+//   Convergence value (Sec. III-E): e = sum_k ||Pi_k D^T - H S_k V^T||^2
+//     = sum_k ||Pi_k||^2 - 2 sum_r W(k,r) G3(k,r) + W_k (H^T H * V^T V) W_k^T.
+// Grid-wide sums are block partials reduced in a fixed order (deterministic).
+// The R x R Gram-Hadamard solves are FP64 (Cholesky; pseudoinverse from an
+// FP64 Jacobi eigendecomposition if a pivot fails).
+#include "common.cuh"
+#include "internal.h"
+
+namespace dp2 {
+
+constexpr int ALS_WARPS = 4;
+
+// Neumaier-compensated fp32 sum of n values with stride; returned as double.
+__device__ inline double comp_sum(const float* p, int n, int64_t stride) {
+  float s = 0.f, c = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float v = p[(int64_t)i * stride];
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  return (double)s + (double)c;
+}
+
+// ----------------------------------------------------- one-sided Jacobi ----
+// Columns of T (n x n, pitch ld) are orthogonalised by plane rotations from
+// the right, accumulated into V (starts at I).  Parallel (round-robin)
+// ordering; lane i < m/2 owns one column pair per step.  Returns sweeps used
+// (> max_sweeps when not converged).
+__device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+  const int m = n + (n & 1);
+  for (int e = lane; e < n * n; e += 32) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.f : 0.f;
+  __syncwarp();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    float worst = 0.f;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int pi = lane; pi < m / 2; pi += 32) {
+        int p, q;
+        if (pi == 0) {
+          p = 0;
+          q = 1 + (r % (m - 1));
+        } else {
+          p = 1 + ((r + pi) % (m - 1));
+          q = 1 + ((r - pi + (m - 1)) % (m - 1));
+        }
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= n) continue;
+        float a = 0.f, b = 0.f, g = 0.f;
+        for (int i = 0; i < n; ++i) {
+          const float tp = T[i * ld + p], tq = T[i * ld + q];
+          a = fmaf(tp, tp, a);
+          b = fmaf(tq, tq, b);
+          g = fmaf(tp, tq, g);
+        }
+        if (a == 0.f || b == 0.f) continue;
+        const float rel = fabsf(g) * rsqrtf(a) * rsqrtf(b);
+        worst = fmaxf(worst, rel);
+        if (rel <= tol) continue;
+        const float zeta = (b - a) / (2.f * g);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = rsqrtf(1.f + t * t), s = c * t;
+        for (int i = 0; i < n; ++i) {
+          const float tp = T[i * ld + p], tq = T[i * ld + q];
+          T[i * ld + p] = c * tp - s * tq;
+          T[i * ld + q] = s * tp + c * tq;
+          const float vp = V[i * ld + p], vq = V[i * ld + q];
+          V[i * ld + p] = c * vp - s * vq;
+          V[i * ld + q] = s * vp + c * vq;
+        }
+      }
+      __syncwarp();
+    }
+    worst = warp_max(worst);
+    if (worst <= tol) return sweep + 1;
+  }
+  return max_sweeps + 1;
+}
+
+// ------------------------------------------------------------- Q-step ----
+// One warp per slice.  Writes Upol_k, Pi_k and the block partial of Lemma 1's
+// G1 (R x R) into part[blk * pstride].
+__global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double* __restrict__ Psi,
+                        const float* __restrict__ W, const float* __restrict__ H, float* __restrict__ Upol,
+                        float* __restrict__ Pi, float* __restrict__ part, int pstride, int* __restrict__ status,
+                        int want_g1) {
+  extern __shared__ __align__(16) float sm[];
+  const int ld = R + 1, RR = R * R;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* ps = sm;             // Psi (R x R)
+  float* hs = ps + RR;        // H
+  float* slots = hs + RR;     // nw x RR
+  float* mine = slots + nw * RR + warp * (2 * R * ld + 3 * RR);
+  float* Tm = mine;           // R x ld
+  float* Vm = Tm + R * ld;    // R x ld
+  float* Fk = Vm + R * ld;    // R x R
+  float* A1 = Fk + RR;        // R x R
+  float* Up = A1 + RR;        // R x R
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    ps[e] = (float)Psi[e];
+    hs[e] = H[e];
+  }
+  for (int e = threadIdx.x; e < nw * RR; e += blockDim.x) slots[e] = 0.f;
+  __syncthreads();
+  const float tol = fmaxf(1e-6f, (float)R * 1.2e-7f);
+  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
+    const float* fk = Ft + (int64_t)k * RR;
+    const float* wk = W + (int64_t)k * R;
+    for (int e = lane; e < RR; e += 32) Fk[e] = fk[e];
+    __syncwarp();
+    for (int e = lane; e < RR; e += 32) {  // A1 = F~_k Psi
+      const int i = e / R, r = e % R;
+      float s = 0.f;
+      for (int m = 0; m < R; ++m) s = fmaf(Fk[i * R + m], ps[m * R + r], s);
+      A1[e] = s;
+    }
+    __syncwarp();
+    for (int e = lane; e < RR; e += 32) {  // T = A1 S_k H^T
+      const int i = e / R, b = e % R;
+      float s = 0.f;
+      for (int r = 0; r < R; ++r) s = fmaf(A1[i * R + r] * wk[r], hs[b * R + r], s);
+      Tm[i * ld + b] = s;
+    }
+    __syncwarp();
+    const int sw = warp_onesided_jacobi(Tm, Vm, R, ld, tol, 30);
+    if (sw > 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
+    // sigma_i = ||T(:, i)||; Upol = sum_{sigma_i > tau sigma_max} T(:, i) V(:, i)^T / sigma_i
+    float smax = 0.f;
+    for (int i = lane; i < R; i += 32) {
+      float s = 0.f;
+      for (int a = 0; a < R; ++a) s = fmaf(Tm[a * ld + i], Tm[a * ld + i], s);
+      A1[i] = sqrtf(s);
+      smax = fmaxf(smax, A1[i]);
+    }
+    smax = warp_max(smax);
+    __syncwarp();
+    const float cut = smax * (float)R * 1.2e-7f;
+    for (int e = lane; e < RR; e += 32) {
+      const int a = e / R, b = e % R;
+      float s = 0.f;
+      for (int i = 0; i < R; ++i) {
+        const float sg = A1[i];
+        if (sg > cut) s = fmaf(Tm[a * ld + i] / sg, Vm[b * ld + i], s);
+      }
+      Up[e] = s;
+    }
+    __syncwarp();
+    float* up = Upol + (int64_t)k * RR;
+    float* pk = Pi + (int64_t)k * RR;
+    for (int e = lane; e < RR; e += 32) {  // Pi = Upol^T F~_k
+      const int a = e / R, b = e % R;
+      float s = 0.f;
+      for (int i = 0; i < R; ++i) s = fmaf(Up[i * R + a], Fk[i * R + b], s);
+      up[e] = Up[e];
+      pk[e] = s;
+      A1[e] = s;
+    }
+    __syncwarp();
+    if (want_g1) {
+      float* slot = slots + warp * RR;
+      for (int e = lane; e < RR; e += 32) {  // slot += (Pi Psi) o W_k
+        const int i = e / R, r = e % R;
+        float s = 0.f;
+        for (int m = 0; m < R; ++m) s = fmaf(A1[i * R + m], ps[m * R + r], s);
+        slot[e] += wk[r] * s;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (want_g1)
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+      float s = 0.f;
+      for (int w = 0; w < nw; ++w) s += slots[w * RR + e];
+      part[(int64_t)blockIdx.x * pstride + e] = s;
+    }
+}
+
+// --------------------------------------------------------- Lemma 2 partial --
+// part[blk] (R x R): g(m, r) += W(k, r) sum_i Pi_k(i, m) H(i, r).
+__global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __restrict__ W,
+                     const float* __restrict__ H, float* __restrict__ part, int pstride) {
+  extern __shared__ __align__(16) float sm[];
+  const int RR = R * R;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* hs = sm;
+  float* slots = hs + RR;
+  float* pks = slots + nw * RR + warp * RR;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) hs[e] = H[e];
+  for (int e = threadIdx.x; e < nw * RR; e += blockDim.x) slots[e] = 0.f;
+  __syncthreads();
+  float* slot = slots + warp * RR;
+  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
+    for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
+    __syncwarp();
+    const float* wk = W + (int64_t)k * R;
+    for (int e = lane; e < RR; e += 32) {
+      const int m = e / R, r = e % R;
+      float s = 0.f;
+      for (int i = 0; i < R; ++i) s = fmaf(pks[i * R + m], hs[i * R + r], s);
+      slot[e] += wk[r] * s;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += slots[w * RR + e];
+    part[(int64_t)blockIdx.x * pstride + e] = s;
+  }
+}
+
+// --------------------------------------------------- Lemma 3 and W update --
+// W_k = G3_k Ginv with G3(k, r) = H(:, r)^T Pi_k Psi(:, r); also the block
+// partials of W^T W (R x R) and of the convergence value e (last entry).
+__global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* __restrict__ Psi,
+                      const float* __restrict__ H, const double* __restrict__ Ginv, const double* __restrict__ HtH,
+                      const double* __restrict__ VtV, float* __restrict__ W, float* __restrict__ part,
+                      int pstride) {
+  extern __shared__ __align__(16) float sm[];
+  const int RR = R * R;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* ps = sm;
+  float* hs = ps + RR;
+  float* gi = hs + RR;
+  float* hv = gi + RR;              // HtH * VtV
+  float* slots = hv + RR;           // nw x (RR + 1)
+  float* pks = slots + nw * (RR + 1) + warp * (RR + 2 * R);
+  float* g3 = pks + RR;
+  float* wn = g3 + R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    ps[e] = (float)Psi[e];
+    hs[e] = H[e];
+    gi[e] = (float)Ginv[e];
+    hv[e] = (float)(HtH[e] * VtV[e]);
+  }
+  for (int e = threadIdx.x; e < nw * (RR + 1); e += blockDim.x) slots[e] = 0.f;
+  __syncthreads();
+  float* slot = slots + warp * (RR + 1);
+  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
+    for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
+    __syncwarp();
+    for (int r = lane; r < R; r += 32) {
+      float s = 0.f;
+      for (int i = 0; i < R; ++i) {
+        float t = 0.f;
+        for (int m = 0; m < R; ++m) t = fmaf(pks[i * R + m], ps[m * R + r], t);
+        s = fmaf(hs[i * R + r], t, s);
+      }
+      g3[r] = s;
+    }
+    __syncwarp();
+    for (int r = lane; r < R; r += 32) {
+      float s = 0.f;
+      for (int m = 0; m < R; ++m) s = fmaf(g3[m], gi[m * R + r], s);
+      wn[r] = s;
+      W[(int64_t)k * R + r] = s;
+    }
+    __syncwarp();
+    // e_k in FP64 from fp32 inputs: ||Pi||^2 - 2 w . g3 + w (HtH*VtV) w
+    double ek = 0.0;
+    for (int e = lane; e < RR; e += 32) {
+      const int a = e / R, b = e % R;
+      ek += (double)pks[e] * pks[e] + (double)wn[a] * hv[e] * wn[b];
+    }
+    for (int r = lane; r < R; r += 32) ek -= 2.0 * (double)wn[r] * g3[r];
+    ek = warp_sum(ek);
+    for (int e = lane; e < RR; e += 32) slot[e] += wn[e / R] * wn[e % R];
+    if (lane == 0) slot[RR] += (float)ek;
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += slots[w * (RR + 1) + e];
+    part[(int64_t)blockIdx.x * pstride + e] = s;
+  }
+}
+
+// -------------------------------------------------------- FP64 small solves --
+// Cholesky factor of the SPD matrix A (n x n) in place (lower L), one thread.
+__device__ bool chol_inplace(double* A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    if (!(d > 1e-300)) return false;
+    d = sqrt(d);
+    A[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = s / d;
+    }
+  }
+  return true;
+}
+
+// Symmetric FP64 Jacobi eigendecomposition (cyclic, one thread) for the
+// pseudoinverse fallback: A <- diag, V eigenvectors.
+__device__ void jacobi_eig_f64(double* A, double* V, int n) {
+  for (int i = 0; i < n * n; ++i) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-30 * tot) return;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// Inv <- A^+ for symmetric PSD A (n x n, FP64), computed by the whole block;
+// Cholesky inverse, or the eigen pseudoinverse (MATLAB tolerance n eps ||A||)
+// when a pivot fails.  Work arrays: L (n x n), V (n x n).
+__device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* V, int n, int* status) {
+  __shared__ int ok;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e];
+  __syncthreads();
+  if (threadIdx.x == 0) ok = chol_inplace(L, n);
+  __syncthreads();
+  if (ok) {
+    // Inv = L^-T L^-1: column c of L^-1 by forward substitution (thread per column)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      for (int i = 0; i < n; ++i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) s -= L[i * n + k] * V[k * n + c];
+        V[i * n + c] = (i < c) ? 0.0 : s / L[i * n + i];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int a = e / n, b = e % n;
+      double s = 0.0;
+      for (int i = max(a, b); i < n; ++i) s += V[i * n + a] * V[i * n + b];
+      Inv[e] = s;
+    }
+    __syncthreads();
+    return;
+  }
+  if (threadIdx.x == 0) {
+    set_status(status, ST_PINV);
+    for (int e = 0; e < n * n; ++e) L[e] = A[e];  // the failed factorisation overwrote L
+    jacobi_eig_f64(L, V, n);
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(L[i * n + i]));
+    const double tol = n * 2.220446049250313e-16 * mx;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double l = L[i * n + i];
+          if (l > tol) s += V[a * n + i] * V[b * n + i] / l;
+        }
+        Inv[a * n + b] = s;
+      }
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------- H update --
+// H = G1 (W^T W * V^T V)^+, columns normalised; HtH = H^T H.
+__global__ void k_update_h(int R, const float* __restrict__ part, int nblk, int pstride,
+                           const double* __restrict__ WtW, const double* __restrict__ VtV, float* __restrict__ H,
+                           double* __restrict__ HtH, double* __restrict__ scratch, int* __restrict__ status) {
+  const int RR = R * R;
+  double* G1 = scratch;
+  double* Gm = G1 + RR;
+  double* Inv = Gm + RR;
+  double* L = Inv + RR;
+  double* V = L + RR;
+  double* Hn = V + RR;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    G1[e] = comp_sum(part + e, nblk, pstride);
+    Gm[e] = WtW[e] * VtV[e];
+  }
+  __syncthreads();
+  block_spd_pinv(Gm, Inv, L, V, R, status);
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int i = e / R, r = e % R;
+    double s = 0.0;
+    for (int m = 0; m < R; ++m) s += G1[i * R + m] * Inv[m * R + r];
+    Hn[e] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double n2 = 0.0;
+    for (int i = 0; i < R; ++i) n2 += Hn[i * R + r] * Hn[i * R + r];
+    const double nr = sqrt(n2);
+    if (!isfinite(nr)) set_status(status, ST_NONFINITE);
+    const double sc = nr > 1e-300 ? 1.0 / nr : 1.0;
+    for (int i = 0; i < R; ++i) Hn[i * R + r] *= sc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    H[e] = (float)Hn[e];
+    const int a = e / R, b = e % R;
+    double s = 0.0;
+    for (int i = 0; i < R; ++i) s += Hn[i * R + a] * Hn[i * R + b];
+    HtH[e] = s;
+  }
+}
+
+// --------------------------------------------------------------- V update --
+// CV = g (W^T W * H^T H)^+ with columns normalised through D^T D; then
+// Psi = D^T D CV, V^T V = CV^T D^T D CV and Ginv = (V^T V * H^T H)^+ for the W update.
+__global__ void k_update_v(int R, const float* __restrict__ part, int nblk, int pstride,
+                           const double* __restrict__ WtW, const double* __restrict__ HtH,
+                           const double* __restrict__ DtD, float* __restrict__ CV, double* __restrict__ Psi,
+                           double* __restrict__ VtV, double* __restrict__ Ginv, double* __restrict__ scratch,
+                           int* __restrict__ status) {
+  const int RR = R * R;
+  double* g = scratch;
+  double* Gm = g + RR;
+  double* Inv = Gm + RR;
+  double* L = Inv + RR;
+  double* V = L + RR;
+  double* C = V + RR;
+  double* DC = C + RR;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    g[e] = comp_sum(part + e, nblk, pstride);
+    Gm[e] = WtW[e] * HtH[e];
+  }
+  __syncthreads();
+  block_spd_pinv(Gm, Inv, L, V, R, status);
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int i = e / R, r = e % R;
+    double s = 0.0;
+    for (int m = 0; m < R; ++m) s += g[i * R + m] * Inv[m * R + r];
+    C[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {  // DC = DtD C
+    const int i = e / R, r = e % R;
+    double s = 0.0;
+    for (int m = 0; m < R; ++m) s += DtD[i * R + m] * C[m * R + r];
+    DC[e] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {  // ||V(:, r)||^2 = C(:, r)^T DtD C(:, r)
+    double n2 = 0.0;
+    for (int i = 0; i < R; ++i) n2 += C[i * R + r] * DC[i * R + r];
+    const double nr = sqrt(fmax(n2, 0.0));
+    if (!isfinite(nr)) set_status(status, ST_NONFINITE);
+    const double sc = nr > 1e-300 ? 1.0 / nr : 1.0;
+    for (int i = 0; i < R; ++i) {
+      C[i * R + r] *= sc;
+      DC[i * R + r] *= sc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e % R;
+    CV[e] = (float)C[e];
+    Psi[e] = DC[e];
+    double s = 0.0;
+    for (int i = 0; i < R; ++i) s += C[i * R + a] * DC[i * R + b];
+    VtV[e] = s;
+    Gm[e] = s * HtH[e];
+  }
+  __syncthreads();
+  block_spd_pinv(Gm, Ginv, L, V, R, status);
+}
+
+// ----------------------------------------------------- iteration epilogue --
+__global__ void k_finish(int R, const float* __restrict__ part, int nblk, int pstride, double* __restrict__ WtW,
+                         double* __restrict__ loss, int it, int* __restrict__ status) {
+  const int RR = R * R;
+  for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
+    const double v = comp_sum(part + e, nblk, pstride);
+    if (e < RR) WtW[e] = v;
+    else {
+      loss[it] = v;
+      if (!isfinite(v)) set_status(status, ST_NONFINITE);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- init ----
+// H = I, W = 1, W^T W = K, H^T H = I, Psi = D^T V0, V^T V = V0^T V0.
+__global__ void k_als_init(int K, int J, int R, const float* __restrict__ D, const float* __restrict__ V0,
+                           float* __restrict__ H, float* __restrict__ W, double* __restrict__ WtW,
+                           double* __restrict__ HtH, double* __restrict__ Psi, double* __restrict__ VtV) {
+  const int RR = R * R;
+  if (blockIdx.x > 0) {
+    for (int64_t i = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * R;
+         i += (int64_t)(gridDim.x - 1) * blockDim.x)
+      W[i] = 1.f;
+    return;
+  }
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e % R;
+    H[e] = a == b ? 1.f : 0.f;
+    HtH[e] = a == b ? 1.0 : 0.0;
+    WtW[e] = (double)K;
+    float sp = 0.f, cp = 0.f, sv = 0.f, cv = 0.f;  // compensated sums over J
+    for (int j = 0; j < J; ++j) {
+      const float x = D[(int64_t)j * R + a] * V0[(int64_t)j * R + b];
+      float t = sp + x;
+      cp += fabsf(sp) >= fabsf(x) ? (sp - t) + x : (x - t) + sp;
+      sp = t;
+      const float y = V0[(int64_t)j * R + a] * V0[(int64_t)j * R + b];
+      t = sv + y;
+      cv += fabsf(sv) >= fabsf(y) ? (sv - t) + y : (y - t) + sv;
+      sv = t;
+    }
+    Psi[e] = (double)sp + cp;
+    VtV[e] = (double)sv + cv;
+  }
+}
+
+// ------------------------------------------------------- output helpers ----
+// Tk (K x R x R) = Upol_k H.
+__global__ void k_upol_h(int K, int R, const float* __restrict__ Upol, const float* __restrict__ H,
+                         float* __restrict__ Tk) {
+  const int RR = R * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * RR;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / RR;
+    const int a = (int)(i % RR) / R, b = (int)(i % RR) % R;
+    const float* u = Upol + k * RR;
+    float s = 0.f;
+    for (int m = 0; m < R; ++m) s = fmaf(u[a * R + m], H[m * R + b], s);
+    Tk[i] = s;
+  }
+}
+
+// Squared error through the exact stage-1 identity, one warp per slice:
+//   ||X_k||^2 - 2 tr(P_k Upol_k H S_k) + ||Upol_k H S_k V^T||^2,
+// P_k = V^T M_k (R x R).  Writes block partials (FP64) of the sum.
+__global__ void k_fitness(int K, int R, const float* __restrict__ P, const float* __restrict__ Upol,
+                          const float* __restrict__ H, const float* __restrict__ W, const double* __restrict__ VtV,
+                          const double* __restrict__ xnorm2, double* __restrict__ part) {
+  extern __shared__ __align__(16) float sm[];
+  const int RR = R * R;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* hs = sm;
+  float* vv = hs + RR;
+  float* my = vv + RR + warp * 2 * RR;
+  float* Y1 = my;        // Upol H
+  float* Pk = my + RR;
+  __shared__ double red[32];
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    hs[e] = H[e];
+    vv[e] = (float)VtV[e];
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
+    const float* u = Upol + (int64_t)k * RR;
+    const float* wk = W + (int64_t)k * R;
+    for (int e = lane; e < RR; e += 32) {
+      const int a = e / R, b = e % R;
+      float s = 0.f;
+      for (int m = 0; m < R; ++m) s = fmaf(u[a * R + m], hs[m * R + b], s);
+      Y1[e] = s;
+      Pk[e] = P[(int64_t)k * RR + e];
+    }
+    __syncwarp();
+    double cross = 0.0, model = 0.0;
+    for (int e = lane; e < RR; e += 32) {
+      const int a = e / R, b = e % R;
+      // tr(P Y1 S) = sum_{a,b} P[a][b] Y1[b][a] W[a]
+      cross += (double)Pk[e] * Y1[b * R + a] * wk[a];
+      // (S Y1^T Y1 S)[a][b] VtV[a][b]
+      float g = 0.f;
+      for (int i = 0; i < R; ++i) g = fmaf(Y1[i * R + a], Y1[i * R + b], g);
+      model += (double)wk[a] * g * wk[b] * vv[e];
+    }
+    cross = warp_sum(cross);
+    model = warp_sum(model);
+    if (lane == 0) acc += xnorm2[k] - 2.0 * cross + model;
+    __syncwarp();
+  }
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// P_k (R x R) = CV^T F~_k^T for V = D CV (then V^T M_k = CV^T D^T M_k and D^T M_k = F~_k^T).
+__global__ void k_p_from_cv(int K, int R, const float* __restrict__ CV, const float* __restrict__ Ft,
+                            float* __restrict__ P) {
+  const int RR = R * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * RR;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / RR;
+    const int a = (int)(i % RR) / R, b = (int)(i % RR) % R;
+    const float* f = Ft + k * RR;
+    float s = 0.f;
+    for (int m = 0; m < R; ++m) s = fmaf(CV[m * R + a], f[b * R + m], s);
+    P[i] = s;
+  }
+}
+
+// P_k (R x R) = V^T M_k for an arbitrary V (J x R), one block per slice.
+__global__ void k_vtm(int J, int R, const float* __restrict__ V, const float* __restrict__ Mblk,
+                      float* __restrict__ P) {
+  const int k = blockIdx.x, RR = R * R;
+  const float* mk = Mblk + (int64_t)k * J * R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e % R;
+    float s = 0.f, c = 0.f;
+    for (int j = 0; j < J; ++j) {
+      const float x = V[(int64_t)j * R + a] * mk[(int64_t)j * R + b];
+      const float t = s + x;
+      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    P[(int64_t)k * RR + e] = s + c;
+  }
+}
+
+__global__ void k_reduce_f64(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    out[0] = s;
+  }
+}
+
+// Psi = D^T V and V^T V for an arbitrary V (one block; compensated fp32 sums).
+__global__ void k_psi_vtv(int J, int R, const float* __restrict__ D, const float* __restrict__ V,
+                          double* __restrict__ Psi, double* __restrict__ VtV) {
+  const int RR = R * R;
+  for (int e = threadIdx.x; e < 2 * RR; e += blockDim.x) {
+    const int which = e / RR, a = (e % RR) / R, b = (e % RR) % R;
+    const float* L = which ? V : D;
+    float s = 0.f, c = 0.f;
+    for (int j = 0; j < J; ++j) {
+      const float x = L[(int64_t)j * R + a] * V[(int64_t)j * R + b];
+      const float t = s + x;
+      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    (which ? VtV : Psi)[e % RR] = (double)s + c;
+  }
+}
+
+// ---------------------------------------------------------------- launchers --
+static int als_warps(int R) {
+  const int per = (2 * R * (R + 1) + 4 * R * R) * 4;
+  int w = (96 * 1024) / per;
+  return w < 1 ? 1 : (w > ALS_WARPS ? ALS_WARPS : w);
+}
+static size_t qstep_smem(int R, int nw) {
+  return (size_t)(2 * R * R + nw * R * R + nw * (2 * R * (R + 1) + 3 * R * R)) * sizeof(float);
+}
+
+void als_set_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_qstep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_g2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_g3w, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_fitness, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  done = true;
+}
+
+void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
+  als_set_attrs();
+  k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV);
+}
+
+void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
+  const int R = b.R, nw = als_warps(R);
+  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part,
+                                                     2 * R * R + 2, b.status, 0);
+}
+
+void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
+  const int R = b.R, RR = R * R, nw = als_warps(R);
+  const int ps = 2 * RR + 2;
+  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part, ps,
+                                                     b.status, 1);
+  k_update_h<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.VtV, b.H, b.HtH, b.small, b.status);
+  k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, b.part, ps);
+  k_update_v<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
+                               b.status);
+  k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
+      b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, b.part, ps);
+  k_finish<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.loss, it, b.status);
+}
+
+void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s) {
+  const int64_t n = (int64_t)K * R * R;
+  k_upol_h<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, Upol, H, Tk);
+}
+
+void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s) {
+  const int64_t n = (int64_t)K * R * R;
+  k_p_from_cv<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, CV, Ft, P);
+}
+
+void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s) {
+  k_vtm<<<K, 128, 0, s>>>(J, R, V, Mblk, P);
+}
+
+void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, cudaStream_t s) {
+  k_psi_vtv<<<1, 256, 0, s>>>(J, R, D, V, Psi, VtV);
+}
+
+void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
+                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s) {
+  als_set_attrs();
+  const int nw = 4;
+  k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 2 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2,
+                                                                           part);
+  k_reduce_f64<<<1, 32, 0, s>>>(part, nblk, out);
+}
+
+}  // namespace dp2

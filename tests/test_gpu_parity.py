@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (same X, same test matrices Omega / Omega2, same V_0).
+
+Tolerances (FP32 path): relative reconstruction errors agree to 1e-5 and
+fitness to 1e-4 (the bar the method's FP32 target states); factor-level
+comparisons use reconstructions, never sign/rotation-ambiguous factors.
+16-bit X is compared against the oracle run on the same rounded values."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dpar2 as od
+from oracle import philox as oph
+
+from _gpu import api_or_skip, padded, rel_sq_err, slices_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    return api_or_skip()
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+# ------------------------------------------------------------------ RNG ----
+
+def test_philox_words_bit_exact(ctx):
+    for seed, sid, n in [(0, 0, 1000), (0x0123456789ABCDEF, 3, 4099), (42, 1, 7)]:
+        got = ctx.philox_words(seed, sid, n).cpu().numpy().view(np.uint32)
+        ref = oph.philox_words(seed, sid, n)
+        assert np.array_equal(got, ref)
+
+
+def test_gaussian_stream_matches_oracle(ctx):
+    n = 20000
+    g = ctx.gaussian(7, 0, n, round16=False).cpu().double().numpy()
+    ref = oph.gaussian(7, 0, 1, n).ravel()
+    np.testing.assert_allclose(g, ref, atol=2e-5, rtol=2e-5)
+    g16 = ctx.gaussian(7, 0, n, round16=True).cpu()
+    ref16 = synth.bf16_representable(torch.from_numpy(ref)).double()
+    diff = (g16.double() - ref16).abs()
+    # rounding to bf16 of values that differ by ~1e-7 agrees except at ties
+    assert (diff > 0).float().mean() < 1e-3
+    assert diff.max() <= 2 ** -7 * ref16.abs().max()
+
+
+# ------------------------------------------------------------- stage 1/2 ----
+
+def _run(api, ctx, d, J, R, p, dtype, q=0, flags=0, seed=5):
+    X = d["X"]
+    off = d["offsets"]
+    K = off.numel() - 1
+    ell = R + p
+    om = synth.gaussian_matrix(J, ell, seed=seed).cuda()
+    om2 = synth.gaussian_matrix(K * R, ell, seed=seed + 1).cuda()
+    Xd = padded(X.cuda().float(), J, dtype)
+    comp = ctx.compress(Xd, off, R=R, p=p, q=q, omega=om, omega2=om2, flags=flags, J=J)
+    Xs = slices_np(Xd, off, J)  # the values the GPU read (rounded for 16-bit X)
+    return comp, Xs, om.double().cpu().numpy(), om2.double().cpu().numpy()
+
+
+def _stage1_recs(t, off):
+    A = t["A"].double().cpu().numpy()
+    M = t["M"].double().cpu().numpy()
+    o = [int(v) for v in off]
+    return [A[o[k]:o[k + 1]] @ M[k].T for k in range(len(o) - 1)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_compression_matches_oracle_plain_workload(api, ctx, dtype):
+    d = synth.plain_parafac2(K=64, Imin=50, Imax=200, J=64, R=10, seed=1001)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, dtype)
+    t = comp.tensors()
+    ref = od.compress(Xs, 10, om, om2)
+    off = d["offsets"]
+    # stage 1: X_k ~ A_k B_k C_k^T
+    g1 = _stage1_recs(t, off)
+    r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
+    assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
+    tot = np.sqrt(sum(np.sum(x * x) for x in Xs))
+    assert np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(g1, r1))) / tot <= 1e-4
+    # A_k column-orthonormal
+    A = t["A"].double().cpu().numpy()
+    o = [int(v) for v in off]
+    for k in range(0, 64, 9):
+        a = A[o[k]:o[k + 1]]
+        np.testing.assert_allclose(a.T @ a, np.eye(10), atol=2e-5)
+    # ||X_k||^2
+    np.testing.assert_allclose(t["xnorm2"].cpu().numpy(), [np.sum(x * x) for x in Xs], rtol=1e-5)
+    # stage 2: X~_k = A_k F^(k) E D^T
+    D = t["D"].double().cpu().numpy()
+    Ft = t["Ft"].double().cpu().numpy()
+    g2 = [A[o[k]:o[k + 1]] @ Ft[k] @ D.T for k in range(64)]
+    r2 = od.compressed_slices(ref)
+    assert abs(rel_sq_err(Xs, g2) - rel_sq_err(Xs, r2)) <= 1e-5
+    assert np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(g2, r2))) / tot <= 1e-4
+    np.testing.assert_allclose(D.T @ D, np.eye(10), atol=2e-5)
+    np.testing.assert_allclose(t["E"].double().cpu().numpy(), ref["E"], rtol=1e-4)
+    # F~_k = M_k^T D (construction identity of the stage-2 randomized SVD)
+    M = t["M"].double().cpu().numpy()
+    for k in range(0, 64, 13):
+        np.testing.assert_allclose(Ft[k], M[k].T @ D, atol=1e-4 * np.abs(Ft[k]).max())
+    assert comp.nbytes() == 4 * od.preprocessed_size([o[k + 1] - o[k] for k in range(64)], 64, 64, 10)
+
+
+def test_ragged_slices_and_tails(api, ctx):
+    """Slices shorter than the sketch width (I_k < R + p, and I_k < R), J not a
+    multiple of any tile width, row counts spanning several sketch tiles and
+    projection row chunks."""
+    rng = np.random.default_rng(3)
+    I = np.concatenate([[1, 3, 7, 11, 19], rng.integers(20, 300, 30), [257, 513]])
+    off = torch.zeros(len(I) + 1, dtype=torch.int64)
+    off[1:] = torch.from_numpy(np.cumsum(I))
+    J, R, p = 301, 8, 8
+    d = synth.plain_parafac2(K=len(I), J=J, R=R, seed=77, offsets=off)
+    comp, Xs, om, om2 = _run(api, ctx, d, J, R, p, torch.float32)
+    t = comp.tensors()
+    ref = od.compress(Xs, R, om, om2)
+    g1 = _stage1_recs(t, off)
+    r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
+    assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
+    for x, g in zip(Xs[:5], g1[:5]):  # I_k <= R: the slice is reproduced exactly
+        assert np.linalg.norm(x - g) <= 1e-5 * max(np.linalg.norm(x), 1e-30)
+    rank = t["rank1"].cpu().numpy()
+    assert list(rank[:5]) == [1, 3, 7, 8, 8]
+
+
+def test_noiseless_lowrank_stage1_exact(api, ctx):
+    d = synth.plain_parafac2(K=40, Imin=30, Imax=90, J=48, R=6, seed=9, snr_db=None)
+    comp, Xs, om, om2 = _run(api, ctx, d, 48, 6, 10, torch.float32)
+    t = comp.tensors()
+    g1 = _stage1_recs(t, d["offsets"])
+    assert rel_sq_err(Xs, g1) <= 1e-11
+    A = t["A"].double().cpu().numpy()
+    D = t["D"].double().cpu().numpy()
+    o = [int(v) for v in d["offsets"]]
+    g2 = [A[o[k]:o[k + 1]] @ t["Ft"][k].double().cpu().numpy() @ D.T for k in range(40)]
+    assert rel_sq_err(Xs, g2) <= 1e-11
+
+
+def test_power_iteration_matches_oracle(api, ctx):
+    d = synth.plain_parafac2(K=32, Imin=50, Imax=120, J=64, R=10, seed=1001)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32, q=1)
+    t = comp.tensors()
+    ref = od.compress(Xs, 10, om, om2, q=1)
+    g1 = _stage1_recs(t, d["offsets"])
+    r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
+    assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
+
+
+def test_per_slice_launches_match_grouped(api, ctx):
+    d = synth.plain_parafac2(K=20, Imin=50, Imax=200, J=64, R=10, seed=11)
+    c1, Xs, _, _ = _run(api, ctx, d, 64, 10, 10, torch.float32)
+    c2, _, _, _ = _run(api, ctx, d, 64, 10, 10, torch.float32, flags=api.FLAG_PER_SLICE)
+    a, b = c1.tensors(), c2.tensors()
+    for key in ("A", "M", "D", "Ft", "E"):
+        assert torch.equal(a[key], b[key]), key
+
+
+# ------------------------------------------------------------------- fit ----
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fit_matches_oracle(api, ctx, dtype):
+    d = synth.plain_parafac2(K=64, Imin=50, Imax=200, J=64, R=10, seed=1001)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, dtype)
+    V0 = synth.gaussian_matrix(64, 10, seed=99, representable16=False).cuda()
+    res = ctx.fit(comp, max_iter=32, V0=V0, want_U=True)
+    ref = od.dpar2_als(od.compress(Xs, 10, om, om2), V0.double().cpu().numpy(), max_iter=32)
+    f_or = od.fitness(Xs, ref["U"], ref["W"], ref["V"])
+    assert abs(res.fitness - f_or) <= 1e-4
+    # loss history (e of Sec. III-E) against the oracle's materialised value
+    np.testing.assert_allclose(res.losses, ref["losses"], rtol=1e-3)
+    L = np.array(res.losses)
+    assert np.all(L[1:] <= L[:-1] * (1 + 1e-5))
+    # the GPU factors reproduce the oracle's reconstruction X^_k = U_k S_k V^T
+    U = res.U.double().cpu().numpy()
+    W = res.W.double().cpu().numpy()
+    V = res.V.double().cpu().numpy()
+    o = [int(v) for v in d["offsets"]]
+    rec_g = [U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T for k in range(64)]
+    rec_o = [ref["U"][k] @ np.diag(ref["W"][k]) @ ref["V"].T for k in range(64)]
+    assert abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)) <= 1e-5
+    # fitness through the identity equals the direct definition on the GPU factors
+    assert abs(res.fitness - (1 - rel_sq_err(Xs, rec_g))) <= 1e-5
+    # Q_k = A_k Z_k P_k^T column-orthonormal
+    A = comp.tensors()["A"].double().cpu().numpy()
+    Up = res.Upol.double().cpu().numpy()
+    for k in range(0, 64, 7):
+        Q = A[o[k]:o[k + 1]] @ Up[k]
+        np.testing.assert_allclose(Q.T @ Q, np.eye(10), atol=5e-5)
+
+
+def test_reconstruct_error_identity_and_qstep(api, ctx):
+    d = synth.plain_parafac2(K=30, Imin=50, Imax=150, J=64, R=10, seed=21)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32)
+    res = ctx.fit(comp, max_iter=10, want_U=True)
+    sq, fit = ctx.reconstruct_error(comp, res.H, res.V, res.W, Upol=res.Upol)
+    assert abs(fit - res.fitness) <= 1e-6
+    U = res.U.double().cpu().numpy()
+    W = res.W.double().cpu().numpy()
+    V = res.V.double().cpu().numpy()
+    o = [int(v) for v in d["offsets"]]
+    direct = sum(np.sum((Xs[k] - U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T) ** 2) for k in range(30))
+    assert sq == pytest.approx(direct, rel=1e-4)
+    # Upol = None: one Q-step from (H, V, W) can only lower the error
+    sq2, fit2 = ctx.reconstruct_error(comp, res.H, res.V, res.W)
+    assert sq2 <= sq * (1 + 1e-5)
+
+
+def test_tol_stops_early_and_graph_equals_loop(api, ctx):
+    d = synth.plain_parafac2(K=30, Imin=50, Imax=150, J=64, R=10, seed=23)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32)
+    a = ctx.fit(comp, max_iter=12)
+    b = ctx.fit(comp, max_iter=12, flags=api.FLAG_NO_GRAPH)
+    assert a.losses == b.losses
+    c = ctx.fit(comp, max_iter=200, tol=1e-3)
+    assert c.iters < 200
+    assert c.losses[-2] - c.losses[-1] <= 1e-3 * c.losses[-2]
+
+
+def test_invalid_arguments_rejected(api, ctx):
+    d = synth.plain_parafac2(K=4, Imin=30, Imax=40, J=32, R=4, seed=1)
+    X = padded(d["X"].cuda().float(), 32, torch.float32)
+    with pytest.raises(api.Dpar2Error) as e:
+        ctx.compress(X, d["offsets"], R=40, p=0, J=32)
+    assert e.value.code == 2
+    bad = d["offsets"].clone()
+    bad[2] = bad[1]
+    with pytest.raises(api.Dpar2Error) as e:
+        ctx.compress(X, bad, R=4, p=4, J=32)
+    assert e.value.code == 2
+    Xu = torch.zeros(X.shape[0], 33, device="cuda")  # 33 floats = 132 bytes per row
+    with pytest.raises(api.Dpar2Error) as e:
+        ctx.compress(Xu, d["offsets"], R=4, p=4, J=33)
+    assert e.value.code == 1
