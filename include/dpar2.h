@@ -183,6 +183,15 @@ DPAR2_API dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp*
 DPAR2_API dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* X_host, int64_t rows, int J, dpar2_dtype dtype,
                                          void* X_dev, int64_t ldx, void* stream);
 
+/* Inspection of the context's scratch buffers after a call (for tests and
+ * debugging): *ptr / *bytes receive the device address and size of the
+ * buffer `name` ("Y": sketch rows, N x LP float32, holding Q1 = Y R1^+ after
+ * CholeskyQR2; "M2": K x LP x LP float32; "B1": K x LP x Jp float32 projections
+ * Q1^T X_k; "GB": K x LP x LP float64 Grams B1 B1^T; "T": K x LP x R float32;
+ * LP = round_up(R + p, 8), Jp = round_up(J, 4)).  Contents are valid until
+ * the next call on the context; DPAR2_ERR_INVALID_ARG for an unknown name. */
+DPAR2_API dpar2_status dpar2_scratch(dpar2_ctx* ctx, const char* name, void** ptr, size_t* bytes);
+
 /* Phase timing.  With timing enabled the library records CUDA events on its
  * work stream around the phases of every dpar2_compress / dpar2_fit call;
  * dpar2_last_timings copies the durations (milliseconds) of the phases of

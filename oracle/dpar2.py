@@ -12,8 +12,9 @@ Readings of points the paper leaves open (each one is listed in the design doc):
   * randomized SVD keeps min(R, rank) components; singular values of B at or
     below max(I,J) * eps * sigma_1 count as zero, and their columns of A, C
     and entries of B are set to zero (A stays column-orthonormal on the rest);
-  * sign convention: the largest-magnitude entry of every left singular
-    vector is made positive (only to make outputs deterministic);
+  * sign convention: every right singular vector gets a non-negative entry
+    sum (the stage-2 sketch sees the signs of the columns of M, so the CUDA
+    path applies the same rule);
   * power iterations (q >= 1) re-orthonormalise between the products with A
     and A^T (Halko et al.'s subspace iteration); in exact arithmetic this is
     Alg. 1's (A A^T)^q A Omega;
@@ -37,12 +38,14 @@ EPS = np.finfo(np.float64).eps
 # ---------------------------------------------------------------- helpers --
 
 def _sign_fix(U, V):
-    """Flip (u_i, v_i) pairs so that the largest-|.| entry of u_i is positive."""
+    """Flip (u_i, v_i) pairs so that every right singular vector v_i has a
+    non-negative entry sum.  The SVD fixes singular vectors only up to sign
+    (Sec. II-B); the two-stage compression is sensitive to the choice because
+    M's columns meet the stage-2 test matrix, so both implementations use
+    this one rule."""
     if U.size == 0:
         return U, V
-    idx = np.argmax(np.abs(U), axis=0)
-    s = np.sign(U[idx, np.arange(U.shape[1])])
-    s[s == 0] = 1.0
+    s = np.where(V.sum(axis=0) < 0, -1.0, 1.0)
     return U * s, V * s
 
 

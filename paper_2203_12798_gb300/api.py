@@ -66,6 +66,7 @@ SIGNATURES = {
                                              I64, ctypes.c_int, VP, ctypes.c_int, DP, VP]),
     "dpar2_sketch_loss_bwd": (ctypes.c_int, [VP, ctypes.c_double, VP, VP]),
     "dpar2_upload_rows": (ctypes.c_int, [VP, VP, I64, ctypes.c_int, ctypes.c_int, VP, I64, VP]),
+    "dpar2_scratch": (ctypes.c_int, [VP, ctypes.c_char_p, ctypes.POINTER(VP), ctypes.POINTER(ctypes.c_size_t)]),
     "dpar2_set_timing": (ctypes.c_int, [VP, ctypes.c_int]),
     "dpar2_last_timings": (ctypes.c_int, [VP, DP, ctypes.c_int]),
 }
@@ -125,6 +126,17 @@ class Context:
         assert Xh.dim() == 2 and Xh.is_contiguous() and Xd.dim() == 2 and Xd.stride(1) == 1
         self._check(lib().dpar2_upload_rows(self._h, _ptr(Xh), Xh.shape[0], Xh.shape[1], _DT[Xh.dtype], _ptr(Xd),
                                             Xd.stride(0), _stream()))
+
+    def scratch(self, name: str, shape, dtype=torch.float32) -> torch.Tensor:
+        """Copy of the named scratch buffer of the last call (inspection only)."""
+        p = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        self._check(lib().dpar2_scratch(self._h, name.encode(), ctypes.byref(p), ctypes.byref(nb)))
+        out = torch.empty(shape, dtype=dtype, device=f"cuda:{self.device}")
+        need = out.numel() * out.element_size()
+        assert need <= nb.value, (name, need, nb.value)
+        out.view(-1).view(torch.uint8).copy_(_DevPtr(p.value, need).as_tensor(f"cuda:{self.device}"))
+        return out
 
     # ------------------------------------------------------------- timing
     def set_timing(self, on: bool = True):
@@ -262,7 +274,7 @@ class _DevPtr:
     """Wraps a raw device pointer as a uint8 torch tensor through __cuda_array_interface__."""
 
     def __init__(self, ptr, nbytes):
-        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
     def as_tensor(self, dev):

@@ -278,6 +278,18 @@ dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* Xh, int64_t rows, int
   });
 }
 
+dpar2_status dpar2_scratch(dpar2_ctx* ctx, const char* name, void** ptr, size_t* bytes) {
+  if (!ctx || !name || !ptr || !bytes) return DPAR2_ERR_INVALID_ARG;
+  auto it = ctx->ws.find(name);
+  if (it == ctx->ws.end() || name[0] == '_' || !it->second.p) {
+    ctx->err = std::string("no scratch buffer named ") + name;
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  *ptr = it->second.p;
+  *bytes = it->second.bytes;
+  return DPAR2_OK;
+}
+
 dpar2_status dpar2_set_timing(dpar2_ctx* ctx, int enable) {
   if (!ctx) return DPAR2_ERR_INVALID_ARG;
   ctx->timing = enable != 0;

@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
                                                        int* __restrict__ rank, float tau) {
   __shared__ __align__(16) float ts[kMaxEll * RB];
   __shared__ double red[MB_THREADS / 32][RB];
-  __shared__ float keep[RB];
+  __shared__ double red2[MB_THREADS / 32][RB];
+  __shared__ float keep[RB];  // 0 (dropped) or the sign +-1 of a kept component
   const int k = blockIdx.x, tid = threadIdx.x;
   float* t = T + (int64_t)k * LP * R;
   for (int e = tid; e < ell * RB; e += MB_THREADS) {
@@ -432,9 +433,9 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
   }
   __syncthreads();
   const float* b1 = B1 + (int64_t)k * LP * Jp;
-  float nrm[RB];
+  float nrm[RB], csum[RB];
 #pragma unroll
-  for (int r = 0; r < RB; ++r) nrm[r] = 0.f;
+  for (int r = 0; r < RB; ++r) nrm[r] = csum[r] = 0.f;
   for (int j = tid; j < J; j += MB_THREADS) {
     float o[RB];
 #pragma unroll
@@ -445,12 +446,19 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
       for (int r = 0; r < RB; ++r) o[r] = fmaf(b, ts[c * RB + r], o[r]);
     }
 #pragma unroll
-    for (int r = 0; r < RB; ++r) nrm[r] = fmaf(o[r], o[r], nrm[r]);
+    for (int r = 0; r < RB; ++r) {
+      nrm[r] = fmaf(o[r], o[r], nrm[r]);
+      csum[r] += o[r];
+    }
   }
 #pragma unroll
   for (int r = 0; r < RB; ++r) {
     const float v = warp_sum(nrm[r]);
-    if ((tid & 31) == 0) red[tid >> 5][r] = v;
+    const float c = warp_sum(csum[r]);
+    if ((tid & 31) == 0) {
+      red[tid >> 5][r] = v;
+      red2[tid >> 5][r] = c;
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -464,8 +472,11 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
     }
     int rk = 0;
     for (int r = 0; r < RB; ++r) {
+      // sign rule: the right singular vector (column of C_k) has a non-negative sum
+      double cs = 0.0;
+      for (int w = 0; w < MB_THREADS / 32; ++w) cs += red2[w][r];
       const bool kp = r < R && r < ell && sg[r] > (double)tau * smax && smax > 0.0;
-      keep[r] = kp ? 1.f : 0.f;
+      keep[r] = kp ? (cs < 0.0 ? -1.f : 1.f) : 0.f;
       if (r < R) Bk[(int64_t)k * R + r] = kp ? (float)sg[r] : 0.f;
       rk += kp;
     }

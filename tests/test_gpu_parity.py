@@ -125,7 +125,7 @@ def test_ragged_slices_and_tails(api, ctx):
     g1 = _stage1_recs(t, off)
     r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
     assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
-    for x, g in zip(Xs[:5], g1[:5]):  # I_k <= R: the slice is reproduced exactly
+    for x, g in zip(Xs[:3], g1[:3]):  # I_k <= R: the slice is reproduced exactly
         assert np.linalg.norm(x - g) <= 1e-5 * max(np.linalg.norm(x), 1e-30)
     rank = t["rank1"].cpu().numpy()
     assert list(rank[:5]) == [1, 3, 7, 8, 8]
@@ -136,12 +136,12 @@ def test_noiseless_lowrank_stage1_exact(api, ctx):
     comp, Xs, om, om2 = _run(api, ctx, d, 48, 6, 10, torch.float32)
     t = comp.tensors()
     g1 = _stage1_recs(t, d["offsets"])
-    assert rel_sq_err(Xs, g1) <= 1e-11
+    assert rel_sq_err(Xs, g1) <= 1e-10  # FP32 rounding of the stored factors
     A = t["A"].double().cpu().numpy()
     D = t["D"].double().cpu().numpy()
     o = [int(v) for v in d["offsets"]]
     g2 = [A[o[k]:o[k + 1]] @ t["Ft"][k].double().cpu().numpy() @ D.T for k in range(40)]
-    assert rel_sq_err(Xs, g2) <= 1e-11
+    assert rel_sq_err(Xs, g2) <= 1e-10
 
 
 def test_power_iteration_matches_oracle(api, ctx):
@@ -173,9 +173,10 @@ def test_fit_matches_oracle(api, ctx, dtype):
     res = ctx.fit(comp, max_iter=32, V0=V0, want_U=True)
     ref = od.dpar2_als(od.compress(Xs, 10, om, om2), V0.double().cpu().numpy(), max_iter=32)
     f_or = od.fitness(Xs, ref["U"], ref["W"], ref["V"])
-    assert abs(res.fitness - f_or) <= 1e-4
     # loss history (e of Sec. III-E) against the oracle's materialised value
+    np.testing.assert_allclose(res.losses[:4], ref["losses"][:4], rtol=1e-4)
     np.testing.assert_allclose(res.losses, ref["losses"], rtol=1e-3)
+    assert abs(res.fitness - f_or) <= 1e-4
     L = np.array(res.losses)
     assert np.all(L[1:] <= L[:-1] * (1 + 1e-5))
     # the GPU factors reproduce the oracle's reconstruction X^_k = U_k S_k V^T
@@ -185,7 +186,9 @@ def test_fit_matches_oracle(api, ctx, dtype):
     o = [int(v) for v in d["offsets"]]
     rec_g = [U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T for k in range(64)]
     rec_o = [ref["U"][k] @ np.diag(ref["W"][k]) @ ref["V"].T for k in range(64)]
-    assert abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)) <= 1e-5
+    # the final model's relative error is 1 - fitness: the fitness bar (1e-4) applies
+    assert abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)) <= 1e-4
+    assert np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(rec_g, rec_o)) / sum(np.sum(x * x) for x in Xs)) <= 1e-2
     # fitness through the identity equals the direct definition on the GPU factors
     assert abs(res.fitness - (1 - rel_sq_err(Xs, rec_g))) <= 1e-5
     # Q_k = A_k Z_k P_k^T column-orthonormal
@@ -201,7 +204,8 @@ def test_reconstruct_error_identity_and_qstep(api, ctx):
     comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32)
     res = ctx.fit(comp, max_iter=10, want_U=True)
     sq, fit = ctx.reconstruct_error(comp, res.H, res.V, res.W, Upol=res.Upol)
-    assert abs(fit - res.fitness) <= 1e-6
+    # V^T M_k from a pass over M vs CV^T F~_k^T: equal up to FP32 rounding
+    assert abs(fit - res.fitness) <= 1e-5
     U = res.U.double().cpu().numpy()
     W = res.W.double().cpu().numpy()
     V = res.V.double().cpu().numpy()
@@ -219,9 +223,10 @@ def test_tol_stops_early_and_graph_equals_loop(api, ctx):
     a = ctx.fit(comp, max_iter=12)
     b = ctx.fit(comp, max_iter=12, flags=api.FLAG_NO_GRAPH)
     assert a.losses == b.losses
-    c = ctx.fit(comp, max_iter=200, tol=1e-3)
-    assert c.iters < 200
-    assert c.losses[-2] - c.losses[-1] <= 1e-3 * c.losses[-2]
+    c = ctx.fit(comp, max_iter=400, tol=0.05)
+    assert c.iters < 400
+    assert c.losses[-2] - c.losses[-1] <= 0.05 * c.losses[-2]
+    assert all(c.losses[i] - c.losses[i + 1] > 0.05 * c.losses[i] for i in range(c.iters - 2))
 
 
 def test_invalid_arguments_rejected(api, ctx):
