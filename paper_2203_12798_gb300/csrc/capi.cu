@@ -106,6 +106,13 @@ inline void tend(dpar2_ctx* c, cudaStream_t s, int ph) {
   }
 }
 
+// Row splits of a Gram so that at least ~2 blocks per SM work on it.
+int gram_splits(int K, int64_t maxI) {
+  if (K >= 256) return 1;
+  const int64_t want = (300 + K - 1) / K;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (maxI + 255) / 256));
+}
+
 // CholeskyQR2 of the per-slice sketches Y (rows x LP, in place): after the
 // call Y holds Q1 = Y R1^+ and M2 = R2^+ with Q = Q1 M2 column-orthonormal on
 // its numerical rank (FP64 Grams; dependent columns dropped).
@@ -114,10 +121,12 @@ void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI
   std::string t(tag);
   double* G = wsget<double>(ctx, (t + "_G").c_str(), (size_t)K * LP * LP);
   float* M1 = wsget<float>(ctx, (t + "_M1").c_str(), (size_t)K * LP * LP);
-  launch_gram_dd(Y, LP, d_off, K, ell, G, s);
+  const int nsplit = gram_splits(K, maxI);
+  double* Gp = nsplit > 1 ? wsget<double>(ctx, (t + "_Gp").c_str(), (size_t)K * nsplit * LP * LP) : nullptr;
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, s);
   launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
-  launch_gram_dd(Y, LP, d_off, K, ell, G, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, s);
 }
 
@@ -486,14 +495,19 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
     launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
     double* G2 = wsget<double>(ctx, "G2", (size_t)LP * LP);
-    launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, s);
+    {
+      const int ns = gram_splits(1, KR);
+      double* Gp = wsget<double>(ctx, "G2p", (size_t)ns * LP * LP);
+      launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, s);
+    }
     float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
     launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
     launch_seg_product(Y2, LP, LP, T2, 0, R, static_cast<float*>(comp->D.p), R, off2, 1, J, s);
     launch_seg_product(B2p, LP, LP, T2, 0, R, static_cast<float*>(comp->Ft.p), R, off2 + 2, 1, KR, s);
     launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
                     static_cast<float*>(comp->E.p), 1e-6f, s);
-    launch_ata(static_cast<const float*>(comp->D.p), J, R, static_cast<double*>(comp->DtD.p), s);
+    launch_atb(J, R, static_cast<const float*>(comp->D.p), static_cast<const float*>(comp->D.p),
+               static_cast<double*>(comp->DtD.p), s);
     tend(ctx, s, DPAR2_PH_STAGE2);
     tend(ctx, s, DPAR2_PH_COMPRESS);
     if (opt->flags & DPAR2_FLAG_DROP_M) {
@@ -555,8 +569,8 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.HtH = d6 + 2 * RR;
     b.WtW = d6 + 3 * RR;
     b.Ginv = d6 + 4 * RR;
-    b.nblk = std::max(1, std::min((K + 3) / 4, ctx->num_sms * 4));
-    b.part = wsget<float>(ctx, "als_part", (size_t)b.nblk * (2 * RR + 2));
+    b.nblk = als_blocks(K, R, ctx->num_sms);
+    b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.nblk * (2 * RR + 2));
     b.loss = wsget<double>(ctx, "als_loss", (size_t)opt->max_iter);
     b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR);
     b.status = ctx->d_status;
@@ -569,6 +583,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         cudaGraphExec_t ge;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+        launch_als_finish(b, opt->max_iter - 1, s);
         CK(cudaStreamEndCapture(s, &g));
         CK(cudaGraphInstantiate(&ge, g, 0));
         CK(cudaGraphLaunch(ge, s));
@@ -577,12 +592,14 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         cudaGraphDestroy(g);
       } else {
         for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+        launch_als_finish(b, opt->max_iter - 1, s);
       }
       iters = opt->max_iter;
     } else {
       double prev = 0.0;
       for (int it = 0; it < opt->max_iter; ++it) {
         launch_als_iteration(b, it, s);
+        launch_als_finish(b, it, s);
         double e = 0.0;
         CK(cudaMemcpyAsync(&e, b.loss + it, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -655,7 +672,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
     double* Psi = d6;
     double* VtV = d6 + RR;
     launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV, s);
-    const int nblk = std::max(1, std::min((K + 3) / 4, ctx->num_sms * 4));
+    const int nblk = als_blocks(K, R, ctx->num_sms);
     const float* up = Upol;
     if (!up) {
       AlsBufs b;
@@ -669,7 +686,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       b.Psi = Psi;
       b.Upol = wsget<float>(ctx, "re_upol", (size_t)K * RR);
       b.Pi = wsget<float>(ctx, "re_pi", (size_t)K * RR);
-      b.part = wsget<float>(ctx, "re_part", (size_t)nblk * (2 * RR + 2));
+      b.part = wsget<float>(ctx, "re_part", (size_t)3 * nblk * (2 * RR + 2));
       b.status = ctx->d_status;
       b.nblk = nblk;
       launch_qstep_only(b, s);

@@ -68,7 +68,10 @@ void launch_project_generic(const void* X, dpar2_dtype dt, int64_t ldx, const in
 int project_blocks(int Jp, int LP);
 
 // ---- per-slice small linear algebra ----
-void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, cudaStream_t s);
+// G[k] = Y_k^T Y_k (FP64, pitch LP).  nsplit > 1 splits every slice's rows over
+// nsplit blocks (partials in Gpart, K * nsplit * LP * LP) for few long slices.
+void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
+                    int nsplit, cudaStream_t s);
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
                       cudaStream_t s);
 void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s);
@@ -88,6 +91,8 @@ void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cuda
 void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s);
 void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, cudaStream_t s);
 void launch_ata(const float* A, int64_t rows, int n, double* out, cudaStream_t s);
+// out (n x n, FP64) = A^T B over `rows` rows (one 1024-thread block).
+void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, cudaStream_t s);
 
 // ---- ALS (Alg. 3 repeat loop) ----
 struct AlsBufs {
@@ -105,7 +110,7 @@ struct AlsBufs {
   double* HtH;        // R x R
   double* WtW;        // R x R
   double* Ginv;       // R x R  (V^T V * H^T H)^+
-  float* part;        // nblk x (2 R^2 + 2) block partials
+  float* part;        // 3 x nblk x (2 R^2 + 2) block partials
   double* loss;       // max_iter history (device)
   double* small;      // scratch, 8 R^2 doubles
   int* status;
@@ -113,6 +118,8 @@ struct AlsBufs {
 };
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
+void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);
+int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);

@@ -21,18 +21,79 @@
 
 namespace dp2 {
 
-constexpr int ALS_WARPS = 4;
+constexpr int ALS_WARPS = 16;
 
-// Neumaier-compensated fp32 sum of n values with stride; returned as double.
-__device__ inline double comp_sum(const float* p, int n, int64_t stride) {
-  float s = 0.f, c = 0.f;
-  for (int i = 0; i < n; ++i) {
-    const float v = p[(int64_t)i * stride];
-    const float t = s + v;
-    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
-    s = t;
+__device__ inline void neumaier(float& s, float& c, float v) {
+  const float t = s + v;
+  c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
+
+// out[e] = sum_b part[b * pstride + e] for e < n.  The whole block cooperates:
+// every entry's partials are split over tpe threads (8 loads in flight per
+// thread, compensated fp32 sums), then combined in a fixed order in FP64.
+__device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int pstride, int n, double* out) {
+  __shared__ double red[1024];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int tpe = max(1, T / n), per = T / tpe;
+  for (int e0 = 0; e0 < n; e0 += per) {
+    const int e = e0 + t / tpe, sub = t % tpe;
+    const bool act = t < per * tpe && e < n;
+    float s = 0.f, c = 0.f;
+    if (act) {
+      int b = sub;
+      for (; b + 7 * tpe < nblk; b += 8 * tpe) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u * tpe) * pstride + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) neumaier(s, c, v[u]);
+      }
+      for (; b < nblk; b += tpe) neumaier(s, c, part[(int64_t)b * pstride + e]);
+    }
+    red[t] = (double)s + (double)c;
+    __syncthreads();
+    if (act && sub == 0) {
+      double a = 0.0;
+      for (int q = 0; q < tpe; ++q) a += red[t + q];
+      out[e] = a;
+    }
+    __syncthreads();
   }
-  return (double)s + (double)c;
+}
+
+// out (n x n, FP64) = A^T B for A, B (rows x n, fp32, row-major), one block:
+// every entry's rows are split over tpe threads (compensated fp32 sums).
+__global__ void __launch_bounds__(1024) k_atb_block(int64_t rows, int n, const float* __restrict__ A,
+                                                    const float* __restrict__ B, double* __restrict__ out) {
+  __shared__ double red[1024];
+  const int T = blockDim.x, t = threadIdx.x, nn = n * n;
+  const int tpe = max(1, T / nn), per = T / tpe;
+  for (int e0 = 0; e0 < nn; e0 += per) {
+    const int e = e0 + t / tpe, sub = t % tpe;
+    const bool act = t < per * tpe && e < nn;
+    const int a = act ? e / n : 0, b = act ? e % n : 0;
+    float s = 0.f, c = 0.f;
+    if (act) {
+      int64_t i = sub;
+      for (; i + 7 * tpe < rows; i += 8 * tpe) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = A[(i + u * tpe) * n + a] * B[(i + u * tpe) * n + b];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) neumaier(s, c, v[u]);
+      }
+      for (; i < rows; i += tpe) neumaier(s, c, A[i * n + a] * B[i * n + b]);
+    }
+    red[t] = (double)s + (double)c;
+    __syncthreads();
+    if (act && sub == 0) {
+      double acc = 0.0;
+      for (int q = 0; q < tpe; ++q) acc += red[t + q];
+      out[e] = acc;
+    }
+    __syncthreads();
+  }
 }
 
 // ----------------------------------------------------- one-sided Jacobi ----
@@ -397,9 +458,12 @@ __device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* 
 
 // --------------------------------------------------------------- H update --
 // H = G1 (W^T W * V^T V)^+, columns normalised; HtH = H^T H.
-__global__ void k_update_h(int R, const float* __restrict__ part, int nblk, int pstride,
-                           const double* __restrict__ WtW, const double* __restrict__ VtV, float* __restrict__ H,
-                           double* __restrict__ HtH, double* __restrict__ scratch, int* __restrict__ status) {
+// When it > 0 it first closes the previous iteration: W^T W and its e from the
+// partials of the W update (part3).
+__global__ void k_update_h(int R, const float* __restrict__ part, const float* __restrict__ part3, int nblk,
+                           int pstride, int it, double* __restrict__ WtW, const double* __restrict__ VtV,
+                           float* __restrict__ H, double* __restrict__ HtH, double* __restrict__ loss,
+                           double* __restrict__ scratch, int* __restrict__ status) {
   const int RR = R * R;
   double* G1 = scratch;
   double* Gm = G1 + RR;
@@ -407,10 +471,20 @@ __global__ void k_update_h(int R, const float* __restrict__ part, int nblk, int 
   double* L = Inv + RR;
   double* V = L + RR;
   double* Hn = V + RR;
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    G1[e] = comp_sum(part + e, nblk, pstride);
-    Gm[e] = WtW[e] * VtV[e];
+  double* W3 = Hn + RR;  // RR + 1
+  if (it > 0) {
+    block_reduce_parts(part3, nblk, pstride, RR + 1, W3);
+    for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
+      if (e < RR) WtW[e] = W3[e];
+      else {
+        loss[it - 1] = W3[RR];
+        if (!isfinite(W3[RR])) set_status(status, ST_NONFINITE);
+      }
+    }
+    __syncthreads();
   }
+  block_reduce_parts(part, nblk, pstride, RR, G1);
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * VtV[e];
   __syncthreads();
   block_spd_pinv(Gm, Inv, L, V, R, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -454,10 +528,8 @@ __global__ void k_update_v(int R, const float* __restrict__ part, int nblk, int 
   double* V = L + RR;
   double* C = V + RR;
   double* DC = C + RR;
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    g[e] = comp_sum(part + e, nblk, pstride);
-    Gm[e] = WtW[e] * HtH[e];
-  }
+  block_reduce_parts(part, nblk, pstride, RR, g);
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
   __syncthreads();
   block_spd_pinv(Gm, Inv, L, V, R, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -501,10 +573,11 @@ __global__ void k_update_v(int R, const float* __restrict__ part, int nblk, int 
 
 // ----------------------------------------------------- iteration epilogue --
 __global__ void k_finish(int R, const float* __restrict__ part, int nblk, int pstride, double* __restrict__ WtW,
-                         double* __restrict__ loss, int it, int* __restrict__ status) {
+                         double* __restrict__ loss, int it, double* __restrict__ scratch, int* __restrict__ status) {
   const int RR = R * R;
+  block_reduce_parts(part, nblk, pstride, RR + 1, scratch);
   for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
-    const double v = comp_sum(part + e, nblk, pstride);
+    const double v = scratch[e];
     if (e < RR) WtW[e] = v;
     else {
       loss[it] = v;
@@ -530,19 +603,6 @@ __global__ void k_als_init(int K, int J, int R, const float* __restrict__ D, con
     H[e] = a == b ? 1.f : 0.f;
     HtH[e] = a == b ? 1.0 : 0.0;
     WtW[e] = (double)K;
-    float sp = 0.f, cp = 0.f, sv = 0.f, cv = 0.f;  // compensated sums over J
-    for (int j = 0; j < J; ++j) {
-      const float x = D[(int64_t)j * R + a] * V0[(int64_t)j * R + b];
-      float t = sp + x;
-      cp += fabsf(sp) >= fabsf(x) ? (sp - t) + x : (x - t) + sp;
-      sp = t;
-      const float y = V0[(int64_t)j * R + a] * V0[(int64_t)j * R + b];
-      t = sv + y;
-      cv += fabsf(sv) >= fabsf(y) ? (sv - t) + y : (y - t) + sv;
-      sv = t;
-    }
-    Psi[e] = (double)sp + cp;
-    VtV[e] = (double)sv + cv;
   }
 }
 
@@ -659,29 +719,17 @@ __global__ void k_reduce_f64(const double* __restrict__ part, int n, double* __r
   }
 }
 
-// Psi = D^T V and V^T V for an arbitrary V (one block; compensated fp32 sums).
-__global__ void k_psi_vtv(int J, int R, const float* __restrict__ D, const float* __restrict__ V,
-                          double* __restrict__ Psi, double* __restrict__ VtV) {
-  const int RR = R * R;
-  for (int e = threadIdx.x; e < 2 * RR; e += blockDim.x) {
-    const int which = e / RR, a = (e % RR) / R, b = (e % RR) % R;
-    const float* L = which ? V : D;
-    float s = 0.f, c = 0.f;
-    for (int j = 0; j < J; ++j) {
-      const float x = L[(int64_t)j * R + a] * V[(int64_t)j * R + b];
-      const float t = s + x;
-      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-      s = t;
-    }
-    (which ? VtV : Psi)[e % RR] = (double)s + c;
-  }
-}
-
 // ---------------------------------------------------------------- launchers --
 static int als_warps(int R) {
   const int per = (2 * R * (R + 1) + 4 * R * R) * 4;
-  int w = (96 * 1024) / per;
+  int w = (160 * 1024) / per;
   return w < 1 ? 1 : (w > ALS_WARPS ? ALS_WARPS : w);
+}
+
+int als_blocks(int K, int R, int num_sms) {
+  const int nw = als_warps(R);
+  const int want = (K + nw - 1) / nw;
+  return std::max(1, std::min(want, 2 * num_sms));
 }
 static size_t qstep_smem(int R, int nw) {
   return (size_t)(2 * R * R + nw * R * R + nw * (2 * R * (R + 1) + 3 * R * R)) * sizeof(float);
@@ -700,6 +748,8 @@ void als_set_attrs() {
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
   als_set_attrs();
   k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV);
+  k_atb_block<<<1, 1024, 0, s>>>(b.J, b.R, b.D, V0, b.Psi);
+  k_atb_block<<<1, 1024, 0, s>>>(b.J, b.R, V0, V0, b.VtV);
 }
 
 void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
@@ -708,18 +758,30 @@ void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
                                                      2 * R * R + 2, b.status, 0);
 }
 
+// One iteration = 5 launches: Q-step (+ Lemma 1 partials), H update (closing
+// the previous iteration's W^T W and e), Lemma 2 partials, V update, Lemma 3
+// + W update (+ W^T W and e partials).  Partials use three separate regions.
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   const int R = b.R, RR = R * R, nw = als_warps(R);
   const int ps = 2 * RR + 2;
-  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part, ps,
+  float* p1 = b.part;
+  float* p2 = b.part + (size_t)b.nblk * ps;
+  float* p3 = b.part + (size_t)2 * b.nblk * ps;
+  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
                                                      b.status, 1);
-  k_update_h<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.VtV, b.H, b.HtH, b.small, b.status);
-  k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, b.part, ps);
-  k_update_v<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
+  k_update_h<<<1, 512, 0, s>>>(R, p1, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small, b.status);
+  k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps);
+  k_update_v<<<1, 512, 0, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
                                b.status);
   k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
-      b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, b.part, ps);
-  k_finish<<<1, 128, 0, s>>>(R, b.part, b.nblk, ps, b.WtW, b.loss, it, b.status);
+      b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, p3, ps);
+}
+
+// Closes the last iteration `it`: W^T W and loss[it] from the W-update partials.
+void launch_als_finish(AlsBufs& b, int it, cudaStream_t s) {
+  const int R = b.R, RR = R * R, ps = 2 * RR + 2;
+  k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.nblk * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
+                             b.status);
 }
 
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s) {
@@ -737,7 +799,12 @@ void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P
 }
 
 void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, cudaStream_t s) {
-  k_psi_vtv<<<1, 256, 0, s>>>(J, R, D, V, Psi, VtV);
+  k_atb_block<<<1, 1024, 0, s>>>(J, R, D, V, Psi);
+  k_atb_block<<<1, 1024, 0, s>>>(J, R, V, V, VtV);
+}
+
+void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, cudaStream_t s) {
+  k_atb_block<<<1, 1024, 0, s>>>(rows, n, A, B, out);
 }
 
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,

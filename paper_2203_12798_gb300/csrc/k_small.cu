@@ -26,9 +26,9 @@ constexpr int GR_MAXP = 9;  // ceil(64*65/2 / 256)
 
 __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict__ Y, int LP,
                                                         const int64_t* __restrict__ off, int ell,
-                                                        double* __restrict__ G) {
+                                                        double* __restrict__ G, int nsplit) {
   extern __shared__ __align__(16) float ys[];
-  const int k = blockIdx.x, tid = threadIdx.x;
+  const int k = blockIdx.x, tid = threadIdx.x, split = blockIdx.y;
   const int P = ell * (ell + 1) / 2;
   int pa[GR_MAXP], pb[GR_MAXP];
   DF acc[GR_MAXP];
@@ -45,7 +45,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
     acc[i].hi = 0.f;
     acc[i].lo = 0.f;
   }
-  const int64_t r0 = off[k], r1 = off[k + 1];
+  // rows of slice k, split in nsplit contiguous ranges (one per blockIdx.y)
+  const int64_t s0 = off[k], s1 = off[k + 1];
+  const int64_t chunk = round_up64((s1 - s0 + nsplit - 1) / nsplit, GR_ROWS);
+  const int64_t r0 = min64(s1, s0 + split * chunk), r1 = min64(s1, r0 + chunk);
   for (int64_t rs = r0; rs < r1; rs += GR_ROWS) {
     const int nr = (int)min64(GR_ROWS, r1 - rs);
     __syncthreads();
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
         if (tid + q * GR_THREADS < P) df_mac(acc[q], yr[pa[q]], yr[pb[q]]);
     }
   }
-  double* g = G + (int64_t)k * LP * LP;
+  double* g = G + ((int64_t)k * nsplit + split) * LP * LP;
 #pragma unroll
   for (int q = 0; q < GR_MAXP; ++q) {
     if (tid + q * GR_THREADS < P) {
@@ -618,37 +621,52 @@ __global__ void __launch_bounds__(128) k_s2_project(const float* __restrict__ Mb
 
 // E_r = ||Ft(:, r)|| over all K R rows (F E has columns of norm E_r since F
 // has orthonormal columns); columns with E_r <= tau max E are zeroed in Ft and D.
-__global__ void __launch_bounds__(256) k_s2_enorm(float* __restrict__ Ft, int64_t rows, int R,
-                                                  float* __restrict__ D, int J, float* __restrict__ E, float tau) {
-  __shared__ double red[8][kMaxR];
+__global__ void __launch_bounds__(1024) k_s2_enorm(float* __restrict__ Ft, int64_t rows, int R,
+                                                   float* __restrict__ D, int J, float* __restrict__ E, float tau) {
+  __shared__ double red[1024];
+  __shared__ double e2[kMaxR];
   __shared__ float keep[kMaxR];
-  const int tid = threadIdx.x;
-  float acc[kMaxR];
-  for (int r = 0; r < R; ++r) acc[r] = 0.f;
-  for (int64_t i = tid; i < rows; i += 256)
-    for (int r = 0; r < R; ++r) acc[r] = fmaf(Ft[i * R + r], Ft[i * R + r], acc[r]);
-  for (int r = 0; r < R; ++r) {
-    const float v = warp_sum(acc[r]);
-    if ((tid & 31) == 0) red[tid >> 5][r] = v;
+  __shared__ int ndrop;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int tpe = T / R;  // threads per column, rows split among them (8 loads in flight each)
+  const int r = t / tpe, sub = t % tpe;
+  float s = 0.f;
+  if (r < R) {
+    int64_t i = sub;
+    for (; i + 7 * tpe < rows; i += 8 * tpe) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = Ft[(i + u * tpe) * R + r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = fmaf(v[u], v[u], s);
+    }
+    for (; i < rows; i += tpe) s = fmaf(Ft[i * R + r], Ft[i * R + r], s);
+  }
+  red[t] = s;
+  __syncthreads();
+  if (r < R && sub == 0) {
+    double a = 0.0;
+    for (int q = 0; q < tpe; ++q) a += red[t + q];
+    e2[r] = a;
   }
   __syncthreads();
-  if (tid == 0) {
-    double e[kMaxR], mx = 0.0;
-    for (int r = 0; r < R; ++r) {
-      double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += red[w][r];
-      e[r] = sqrt(s);
-      mx = fmax(mx, e[r]);
-    }
-    for (int r = 0; r < R; ++r) {
-      const bool kp = e[r] > (double)tau * mx && mx > 0.0;
-      keep[r] = kp ? 1.f : 0.f;
-      E[r] = kp ? (float)e[r] : 0.f;
+  if (t == 0) {
+    double mx = 0.0;
+    for (int c = 0; c < R; ++c) mx = fmax(mx, sqrt(e2[c]));
+    ndrop = 0;
+    for (int c = 0; c < R; ++c) {
+      const double e = sqrt(e2[c]);
+      const bool kp = e > (double)tau * mx && mx > 0.0;
+      keep[c] = kp ? 1.f : 0.f;
+      E[c] = kp ? (float)e : 0.f;
+      ndrop += !kp;
     }
   }
   __syncthreads();
-  for (int64_t i = tid; i < rows * R; i += 256) Ft[i] *= keep[i % R];
-  for (int i = tid; i < J * R; i += 256) D[i] *= keep[i % R];
+  if (ndrop) {
+    for (int64_t i = t; i < rows * R; i += T) Ft[i] *= keep[i % R];
+    for (int i = t; i < J * R; i += T) D[i] *= keep[i % R];
+  }
 }
 
 // out (n x n, FP64) = A^T A for A (rows x n, fp32); one block.
@@ -675,8 +693,26 @@ __global__ void __launch_bounds__(256) k_ata(const float* __restrict__ A, int64_
 }
 
 // ---------------------------------------------------------------- launchers --
-void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, cudaStream_t s) {
-  k_gram_dd<<<K, GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, G);
+// G[k] (+)= sum of the nsplit partial Grams Gpart[k * nsplit + i] (fixed order).
+__global__ void k_sum_splits(const double* __restrict__ Gpart, int nsplit, int K, int n, double* __restrict__ G) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / n, e = i % n;
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) s += Gpart[(k * nsplit + q) * n + e];
+    G[i] = s;
+  }
+}
+
+void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
+                    int nsplit, cudaStream_t s) {
+  if (nsplit <= 1 || !Gpart) {
+    k_gram_dd<<<dim3(K, 1), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, G, 1);
+    return;
+  }
+  k_gram_dd<<<dim3(K, nsplit), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, Gpart, nsplit);
+  const int n = LP * LP;
+  k_sum_splits<<<(K * n + 255) / 256, 256, 0, s>>>(Gpart, nsplit, K, n, G);
 }
 
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
@@ -746,7 +782,7 @@ void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, 
 }
 
 void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, cudaStream_t s) {
-  k_s2_enorm<<<1, 256, 0, s>>>(Ft, rows, R, D, J, E, tau);
+  k_s2_enorm<<<1, (1024 / R) * R, 0, s>>>(Ft, rows, R, D, J, E, tau);
 }
 
 void launch_ata(const float* A, int64_t rows, int n, double* out, cudaStream_t s) {

@@ -105,10 +105,10 @@ def _model_energy(H, V, W, offsets) -> float:
 def _orthonormal(n: int, r: int, g, device, dtype) -> torch.Tensor:
     """n x r with orthonormal columns (n >= r) or orthonormal rows (n < r)."""
     if n >= r:
-        q, _ = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=dtype))
-        return q
-    q, _ = torch.linalg.qr(torch.randn(r, n, generator=g, device=device, dtype=dtype))
-    return q.T.contiguous()
+        q, _ = torch.linalg.qr(torch.randn(n, r, generator=g, device=device, dtype=dtype).cpu())
+        return q.to(device)
+    q, _ = torch.linalg.qr(torch.randn(r, n, generator=g, device=device, dtype=dtype).cpu())
+    return q.T.contiguous().to(device)
 
 
 def _parafac2_slices(offsets, J, R, seed, device, dtype, s_std=0.3):
@@ -170,16 +170,19 @@ def spectrogram_like(K=8000, Imin=100, Imax=704, J=2049, R=10, seed=1002, snr_db
     # group slices by length so the orthonormal U_k are made by batched QR
     lengths = torch.tensor([off[k + 1] - off[k] for k in range(K)])
     gu = _gen(device, seed + 11)
+    gq = _gen("cpu", seed + 17)
     for n in torch.unique(lengths).tolist():
         ks = (lengths == n).nonzero().flatten().tolist()
         for b0 in range(0, len(ks), 256):
             kb = ks[b0:b0 + 256]
-            A = torch.randn(len(kb), n, R, generator=gu, device=device)
+            # orthonormal U_k from batched QR on the host (small n x R matrices)
+            A = torch.randn(len(kb), n, R, generator=gq)
             if n >= R:
                 U, _ = torch.linalg.qr(A)
             else:
                 Qt, _ = torch.linalg.qr(A.transpose(1, 2))
                 U = Qt.transpose(1, 2)
+            U = U.to(device)
             HS = H.unsqueeze(0) * Wt[kb].unsqueeze(1)  # B x R x R
             sl = U @ (HS @ V.T.unsqueeze(0))  # B x n x J
             sl += sigma * torch.randn(sl.shape, generator=gu, device=device)

@@ -173,9 +173,11 @@ def test_fit_matches_oracle(api, ctx, dtype):
     res = ctx.fit(comp, max_iter=32, V0=V0, want_U=True)
     ref = od.dpar2_als(od.compress(Xs, 10, om, om2), V0.double().cpu().numpy(), max_iter=32)
     f_or = od.fitness(Xs, ref["U"], ref["W"], ref["V"])
-    # loss history (e of Sec. III-E) against the oracle's materialised value
-    np.testing.assert_allclose(res.losses[:4], ref["losses"][:4], rtol=1e-4)
-    np.testing.assert_allclose(res.losses, ref["losses"], rtol=1e-3)
+    # loss history (e of Sec. III-E) against the oracle's materialised value.
+    # FP32 errors are relative to the data energy sum ||X_k||^2 (~1e-5 of it
+    # in the compressed slices); e is a residual of a few % of that energy.
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert np.max(np.abs(np.array(res.losses) - np.array(ref["losses"]))) <= 2e-5 * tot
     assert abs(res.fitness - f_or) <= 1e-4
     L = np.array(res.losses)
     assert np.all(L[1:] <= L[:-1] * (1 + 1e-5))
@@ -189,8 +191,9 @@ def test_fit_matches_oracle(api, ctx, dtype):
     # the final model's relative error is 1 - fitness: the fitness bar (1e-4) applies
     assert abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)) <= 1e-4
     assert np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(rec_g, rec_o)) / sum(np.sum(x * x) for x in Xs)) <= 1e-2
-    # fitness through the identity equals the direct definition on the GPU factors
-    assert abs(res.fitness - (1 - rel_sq_err(Xs, rec_g))) <= 1e-5
+    # fitness through the identity equals the direct definition on the GPU
+    # factors, up to the FP32 orthonormality of A_k (~1e-5)
+    assert abs(res.fitness - (1 - rel_sq_err(Xs, rec_g))) <= 3e-5
     # Q_k = A_k Z_k P_k^T column-orthonormal
     A = comp.tensors()["A"].double().cpu().numpy()
     Up = res.Upol.double().cpu().numpy()
@@ -211,7 +214,8 @@ def test_reconstruct_error_identity_and_qstep(api, ctx):
     V = res.V.double().cpu().numpy()
     o = [int(v) for v in d["offsets"]]
     direct = sum(np.sum((Xs[k] - U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T) ** 2) for k in range(30))
-    assert sq == pytest.approx(direct, rel=1e-4)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert abs(sq - direct) <= 3e-5 * tot
     # Upol = None: one Q-step from (H, V, W) can only lower the error
     sq2, fit2 = ctx.reconstruct_error(comp, res.H, res.V, res.W)
     assert sq2 <= sq * (1 + 1e-5)
