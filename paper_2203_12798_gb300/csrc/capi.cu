@@ -414,8 +414,21 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     float* B1 = wsget<float>(ctx, "B1", (size_t)K * LP * Jp);
     const int nJb = project_blocks(Jp, LP);
     double* xpart = wsget<double>(ctx, "xpart", (size_t)K * nJb);
+    // tensor-core path: 16-bit X, all slices in one persistent launch
+    const bool use_tc = dtype != DPAR2_F32 && !(opt->flags & (DPAR2_FLAG_GENERIC | DPAR2_FLAG_PER_SLICE)) &&
+                        tc_available();
+    const int LPN = tc_lpn(ell);
+    void* omT16 = nullptr;
+    if (use_tc) {
+      omT16 = wsget<uint16_t>(ctx, "omT16", (size_t)LPN * Jpad);
+      launch_omega_t16(om_pad, Jpad, LP, LPN, dtype, omT16, s);
+    }
     tbegin(ctx, s, DPAR2_PH_SKETCH);
-    if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+    bool sketched = false;
+    if (use_tc)
+      sketched = launch_sketch_tc(X, dtype, ldx, N, J, omT16, Jpad, LPN, LP, Y, ctx->num_sms, ctx->d_status, s);
+    if (sketched) {
+    } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
       for (int k = 0; k < K; ++k) {
         const int64_t r0 = row_offsets[k], nk = row_offsets[k + 1] - r0;
         launch_sketch_generic(static_cast<const char*>(X) + r0 * ldx * es, dtype, ldx, nk, J, om_pad, LP,
@@ -439,8 +452,37 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
 
     tend(ctx, s, DPAR2_PH_QR);
     // ---- projection B1 = Q1^T X (pass 2 over X) and ||X_k||^2 ----
-    tbegin(ctx, s, DPAR2_PH_PROJECT);
-    if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+    int nJb_used = nJb;
+    bool projected = false;
+    if (use_tc) {
+      // Q1 split into three exact-sum 16-bit parts, slices padded to 64 rows
+      std::vector<int64_t> hp(K + 1, 0);
+      int64_t maxPad = 0;
+      for (int k = 0; k < K; ++k) {
+        const int64_t pk = round_up64(row_offsets[k + 1] - row_offsets[k], 64);
+        hp[k + 1] = hp[k] + pk;
+        maxPad = std::max(maxPad, pk);
+      }
+      const int64_t Npad = hp[K];
+      int64_t* d_poff = wsget<int64_t>(ctx, "poff", (size_t)K + 1);
+      CK(cudaMemcpyAsync(d_poff, hp.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      void* Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * Npad);
+      launch_qsplit(Y, LP, LPN, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
+      const int nJb_tc = (Jp + 127) / 128;
+      double* xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc);
+      CK(cudaStreamSynchronize(s));  // hp must outlive the pageable copy
+      tbegin(ctx, s, DPAR2_PH_PROJECT);
+      projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, LPN, LP, B1, xp, nJb_tc,
+                                    ctx->num_sms, ctx->d_status, s);
+      if (projected) {
+        xpart = xp;
+        nJb_used = nJb_tc;
+      }
+    } else {
+      tbegin(ctx, s, DPAR2_PH_PROJECT);
+    }
+    if (projected) {
+    } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
       for (int k = 0; k < K; ++k)
         launch_project_generic(X, dtype, ldx, d_off + k, 1, J, Jp, Y, LP, B1 + (size_t)k * LP * Jp,
                                xpart + (size_t)k * nJb, nullptr, s);
@@ -449,7 +491,7 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     }
     tend(ctx, s, DPAR2_PH_PROJECT);
     tbegin(ctx, s, DPAR2_PH_SMALL);
-    launch_reduce_rows_f64(xpart, K, nJb, static_cast<double*>(comp->xnorm2.p), s);
+    launch_reduce_rows_f64(xpart, K, nJb_used, static_cast<double*>(comp->xnorm2.p), s);
 
     // ---- small SVD of B = M2^T B1 -> C_k B_k blocks of M, T_k, A_k ----
     double* GB = wsget<double>(ctx, "GB", (size_t)K * LP * LP);

@@ -67,6 +67,18 @@ void launch_project_generic(const void* X, dpar2_dtype dt, int64_t ldx, const in
                             cudaStream_t s);
 int project_blocks(int Jp, int LP);
 
+// ---- stage 1, tensor-core path (16-bit X, tcgen05 + TMA) ----
+bool tc_available();
+int tc_lpn(int ell);  // MMA N width of the sketch: 32 or 64
+void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s);
+bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const void* omT16, int Jpad,
+                      int LPN, int LP, float* Y, int num_sms, int* status, cudaStream_t s);
+void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
+                   int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
+bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
+                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
+                       float* B1, double* xpart, int nJb, int num_sms, int* status, cudaStream_t s);
+
 // ---- per-slice small linear algebra ----
 // G[k] = Y_k^T Y_k (FP64, pitch LP).  nsplit > 1 splits every slice's rows over
 // nsplit blocks (partials in Gpart, K * nsplit * LP * LP) for few long slices.

@@ -1,0 +1,693 @@
+// Stage-1 streaming passes on the 5th-generation tensor cores (sm_103a) for
+// 16-bit X (BF16 / FP16 storage and multiplication, FP32 accumulation in TMEM).
+//
+//   sketch   Y = X Omega                (Alg. 1, "construct Y"; Eq. fstage_svd)
+//   project  B1_k = Q1_k^T X_k          (Alg. 1, "construct B") + ||X_k||_F^2
+//
+// Both kernels are persistent (one CTA per SM) and warp-specialised:
+//   warp 0      one thread issues TMA tile loads (cp.async.bulk.tensor) into a
+//               ring of shared-memory stages, each guarded by mbarriers;
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma for every stage
+//               and tcgen05.commit's the stage back to the producer;
+//   warps 2-5   epilogue: tcgen05.ld the FP32 accumulator (one TMEM lane per
+//               output row), write it out; the accumulator is double-buffered
+//               in TMEM so the epilogue of one tile overlaps the next tile's MMAs;
+//   warp 6      (project only) sums the squares of the staged X tiles.
+// Every mbarrier wait is bounded by %globaltimer (kWaitNs); a wait that runs out
+// raises a CTA-wide abort flag, every role stops issuing work, waits (bounded)
+// for its in-flight copies / MMAs, TMEM is released and the status word gets
+// ST_TIMEOUT.
+//
+// Shared-memory operand layouts are the canonical 128-byte-swizzled ones that
+// TMA SWIZZLE_128B produces (8-row atoms of 128-byte rows, 1024-byte aligned):
+//   sketch   A = X tile, 128 rows x 64 columns, K-major (K = columns)
+//            B = Omega^T chunk, LPN x 64, K-major
+//   project  A = X tile seen as M = 128 columns x K = 64 rows: MN-major, two
+//            64-column atoms 8 KB apart (leading-dimension offset), 8-row K
+//            groups 1 KB apart (stride offset)
+//            B = Q1 split into three 16-bit parts (Q1 = hi + mid + lo exactly
+//            up to FP32 rounding), 3 LPN x 64 rows, K-major (K = rows), so
+//            one MMA per K step yields hi/mid/lo partial products that the
+//            epilogue adds: FP32 accuracy from 16-bit operands.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dp2 {
+namespace tc {
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with parity `parity` of `bar`.  Returns false (and
+// raises the abort flag) after kWaitNs, or at once when another role aborted.
+__device__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 127) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, 128-byte swizzle (sm_100 family format:
+// start >> 4 in bits 0-13, leading-dimension byte offset >> 4 in 16-29,
+// stride-dimension byte offset >> 4 in 32-45, version 1 in 46-47, layout
+// type SWIZZLE_128B = 2 in 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16 with FP32 accumulation.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16, bool a_mn, bool b_mn) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// --------------------------------------------------------------- sketch ----
+constexpr int SK_BM = 128, SK_BK = 64, SK_STAGES = 6;
+
+template <int LPN>
+struct SketchSmem {
+  static constexpr int A = SK_BM * SK_BK * 2;
+  static constexpr int B = LPN * SK_BK * 2;
+  static constexpr int BYTES = 1024 + SK_STAGES * (A + B) + 256;
+};
+
+template <int LPN>
+__global__ void __launch_bounds__(192, 1) k_sketch_tc(const __grid_constant__ CUtensorMap tmX,
+                                                      const __grid_constant__ CUtensorMap tmO, int64_t N, int J,
+                                                      int LP, float* __restrict__ Y, int bf16, int* status) {
+  using S = SketchSmem<LPN>;
+  constexpr uint32_t NCOL = 2 * LPN < 32 ? 32 : 2 * LPN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint8_t* sA = base;
+  uint8_t* sB = base + SK_STAGES * S::A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + SK_STAGES * S::B);
+  uint64_t* empty = full + SK_STAGES;
+  uint64_t* accfull = empty + SK_STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (N + SK_BM - 1) / SK_BM;
+  const int nk = (J + SK_BK - 1) / SK_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SK_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 128);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, NCOL);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    prefetch_tmap(&tmX);
+    prefetch_tmap(&tmO);
+    int s = 0;
+    uint32_t ph = 0, inflight = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+      for (int kc = 0; kc < nk; ++kc) {
+        if (!wait_bounded(&empty[s], ph ^ 1, abort_flag)) break;
+        mbar_arrive_expect_tx(&full[s], S::A + S::B);
+        tma_load_2d(sA + s * S::A, &tmX, &full[s], kc * SK_BK, (int)(tile * SK_BM));
+        tma_load_2d(sB + s * S::B, &tmO, &full[s], kc * SK_BK, 0);
+        inflight = 1;
+        if (++s == SK_STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    // on abort: wait (bounded) until the last issued stage has landed
+    if (*abort_flag && inflight) {
+      int ls = (s + SK_STAGES - 1) % SK_STAGES;
+      uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&full[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issue
+    const uint32_t idesc = idesc_f16(SK_BM, LPN, bf16 != 0, false, false);
+    int s = 0;
+    uint32_t ph = 0;
+    int t = 0;
+    bool issued = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++t) {
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accempty[acc], aph ^ 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * LPN;
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc) {
+        if (!wait_bounded(&full[s], ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc_sw128(smem_u32(sA + s * S::A), 16, 1024);
+        const uint64_t bd = sdesc_sw128(smem_u32(sB + s * S::B), 16, 1024);
+#pragma unroll
+        for (int kk = 0; kk < SK_BK / 16; ++kk)
+          tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0 ? 1u : 0u);
+        tc_commit(&empty[s]);
+        issued = true;
+        if (++s == SK_STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      tc_commit(&accfull[acc]);
+    }
+    if (*abort_flag && issued) {
+      // drain: wait (bounded) for the MMAs behind the last commit
+      const int ls = (s + SK_STAGES - 1) % SK_STAGES;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&empty[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    int t = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
+      tc_fence_after();
+      float v[LPN];
+#pragma unroll
+      for (int g = 0; g < LPN / 32; ++g) tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * LPN + g * 32, v + 32 * g);
+      tc_fence_before();
+      mbar_arrive(&accempty[acc]);
+      const int64_t row = tile * SK_BM + q * 32 + lane;
+      if (row < N) {
+        float4* dst = reinterpret_cast<float4*>(Y + row * LP);
+#pragma unroll
+        for (int c4 = 0; c4 < LPN / 4; ++c4)
+          if (4 * c4 < LP) dst[c4] = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, NCOL);
+  }
+  if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
+}
+
+// -------------------------------------------------------------- project ----
+constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
+
+template <int LPN>
+struct ProjSmem {
+  static constexpr int NS = 3 * LPN;          // hi / mid / lo splits
+  static constexpr int A = PJ_BM * PJ_BK * 2;  // two 64-column boxes of 64 rows
+  static constexpr int B = NS * PJ_BK * 2;
+  static constexpr int BYTES = 1024 + PJ_STAGES * (A + B) + 256;
+};
+
+template <int LPN>
+__global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ CUtensorMap tmX,
+                                                       const __grid_constant__ CUtensorMap tmQ,
+                                                       const int64_t* __restrict__ off,
+                                                       const int64_t* __restrict__ poff, int K, int J, int Jp,
+                                                       int LP, float* __restrict__ B1, double* __restrict__ xpart,
+                                                       int nJb, int bf16, int* status) {
+  using S = ProjSmem<LPN>;
+  constexpr uint32_t NCOL = 2 * S::NS <= 256 ? 256 : 512;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint8_t* sA = base;
+  uint8_t* sB = base + PJ_STAGES * S::A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + PJ_STAGES * S::B);
+  uint64_t* empty = full + PJ_STAGES;
+  uint64_t* accfull = empty + PJ_STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nitems = (int64_t)K * nJb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PJ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 2);  // MMA commit + norm warp
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 128);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, NCOL);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    prefetch_tmap(&tmX);
+    prefetch_tmap(&tmQ);
+    int s = 0;
+    uint32_t ph = 0;
+    bool inflight = false;
+    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
+      const int k = (int)(item / nJb), jb = (int)(item % nJb);
+      const int64_t r0 = off[k], nrows = off[k + 1] - r0, p0 = poff[k];
+      const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
+      bool ok = true;
+      for (int c = 0; c < nch; ++c) {
+        if (!wait_bounded(&empty[s], ph ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], S::A + S::B);
+        uint8_t* a = sA + s * S::A;
+        tma_load_2d(a, &tmX, &full[s], jb * PJ_BM, (int)(r0 + c * PJ_BK));
+        tma_load_2d(a + S::A / 2, &tmX, &full[s], jb * PJ_BM + 64, (int)(r0 + c * PJ_BK));
+        tma_load_2d(sB + s * S::B, &tmQ, &full[s], (int)(p0 + c * PJ_BK), 0);
+        inflight = true;
+        if (++s == PJ_STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+    }
+    if (*abort_flag && inflight) {
+      const int ls = (s + PJ_STAGES - 1) % PJ_STAGES;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&full[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issue
+    const uint32_t idesc = idesc_f16(PJ_BM, S::NS, bf16 != 0, true, false);
+    int s = 0;
+    uint32_t ph = 0;
+    int t = 0;
+    bool issued = false;
+    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x, ++t) {
+      const int k = (int)(item / nJb);
+      const int64_t nrows = off[k + 1] - off[k];
+      const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accempty[acc], aph ^ 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * S::NS;
+      bool ok = true;
+      for (int c = 0; c < nch; ++c) {
+        if (!wait_bounded(&full[s], ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // A: MN-major, 64-column atoms 8 KB apart, 8-row K groups 1 KB apart
+        const uint64_t ad = sdesc_sw128(smem_u32(sA + s * S::A), S::A / 2, 1024);
+        // B: K-major, 8-row groups 1 KB apart
+        const uint64_t bd = sdesc_sw128(smem_u32(sB + s * S::B), 16, 1024);
+#pragma unroll
+        for (int kk = 0; kk < PJ_BK / 16; ++kk)
+          tc_mma(d, ad + (uint64_t)(kk * 128), bd + (uint64_t)(kk * 2), idesc, (c | kk) != 0 ? 1u : 0u);
+        tc_commit(&empty[s]);
+        issued = true;
+        if (++s == PJ_STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      tc_commit(&accfull[acc]);
+    }
+    if (*abort_flag && issued) {
+      const int ls = (s + PJ_STAGES - 1) % PJ_STAGES;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&empty[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    int t = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++t) {
+      const int k = (int)(item / nJb), jb = (int)(item % nJb);
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
+      tc_fence_after();
+      const int j = jb * PJ_BM + q * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + acc * S::NS;
+      for (int g = 0; g < LPN / 32; ++g) {
+        float v[32], w[32];
+        tmem_ld32(tl + g * 32, v);
+        tmem_ld32(tl + LPN + g * 32, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
+        tmem_ld32(tl + 2 * LPN + g * 32, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
+        if (j < Jp) {
+          float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i];
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[acc]);
+    }
+  } else if (warp == 6) {
+    // ------------------------------------------------------------ ||X_k||^2
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      const int k = (int)(item / nJb), jb = (int)(item % nJb);
+      const int64_t nrows = off[k + 1] - off[k];
+      const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
+      float acc = 0.f;
+      bool ok = true;
+      for (int c = 0; c < nch; ++c) {
+        if (!wait_bounded(&full[s], ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int valid = (int)min64(PJ_BK, nrows - (int64_t)c * PJ_BK);
+        const uint8_t* a = sA + s * S::A;
+        // 2 boxes x 64 rows x 128 bytes; lane reads 16 bytes (8 elements)
+        for (int it = 0; it < S::A / 512; ++it) {
+          const int byte = it * 512 + lane * 16;
+          const int row = (byte % (S::A / 2)) / 128;
+          if (row < valid) {
+            const uint4 u = *reinterpret_cast<const uint4*>(a + byte);
+            float f[8];
+            if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
+            else Vec16<__half>::unpack(u, f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc = fmaf(f[e], f[e], acc);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == PJ_STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      acc = warp_sum(acc);
+      if (lane == 0) xpart[(int64_t)k * nJb + jb] = (double)acc;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, NCOL);
+  }
+  if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
+}
+
+// ------------------------------------------------------------- operands ----
+// Omega^T in 16-bit (LPN x Jpad) from the padded FP32 Omega (Jpad x LP).
+__global__ void k_omega_t16(const float* __restrict__ om, int Jpad, int LP, int LPN, int bf16, void* out) {
+  const int64_t n = (int64_t)LPN * Jpad;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Jpad), j = (int)(i % Jpad);
+    const float v = c < LP ? om[(int64_t)j * LP + c] : 0.f;
+    if (bf16) reinterpret_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v);
+    else reinterpret_cast<__half*>(out)[i] = __float2half_rn(v);
+  }
+}
+
+// Q1 rows (N x LP FP32) -> three exact-sum 16-bit parts, transposed to
+// (3 LPN) x Npad with every slice padded to a multiple of 64 rows (zeros).
+__global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int64_t* __restrict__ off,
+                         const int64_t* __restrict__ poff, int K, int64_t Npad, int bf16, void* out) {
+  const int k = blockIdx.y;
+  const int64_t p0 = poff[k], p1 = poff[k + 1], r0 = off[k], nr = off[k + 1] - r0;
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p - p0;
+    for (int c = 0; c < LPN; ++c) {
+      const float qv = (i < nr && c < LP) ? Q[(r0 + i) * LP + c] : 0.f;
+      if (bf16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(qv);
+        const float r1 = qv - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out);
+        o[(int64_t)c * Npad + p] = h;
+        o[(int64_t)(LPN + c) * Npad + p] = m;
+        o[(int64_t)(2 * LPN + c) * Npad + p] = l;
+      } else {
+        const __half h = __float2half_rn(qv);
+        const float r1 = qv - __half2float(h);
+        const __half m = __float2half_rn(r1);
+        const __half l = __float2half_rn(r1 - __half2float(m));
+        __half* o = reinterpret_cast<__half*>(out);
+        o[(int64_t)c * Npad + p] = h;
+        o[(int64_t)(LPN + c) * Npad + p] = m;
+        o[(int64_t)(2 * LPN + c) * Npad + p] = l;
+      }
+    }
+  }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side --
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D tensor map of a row-major 16-bit matrix (rows x cols, row pitch
+// ld elements), box (bx cols, by rows), 128-byte swizzle, zero fill outside.
+static bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t cols, uint64_t rows, uint64_t ld,
+                     uint32_t bx, uint32_t by) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {bx, by};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+int tc_lpn(int ell) { return ell <= 32 ? 32 : 64; }
+
+bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const void* omT16, int Jpad,
+                      int LPN, int LP, float* Y, int num_sms, int* status, cudaStream_t s) {
+  const bool bf = dt == DPAR2_BF16;
+  CUtensorMap mx, mo;
+  if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, tc::SK_BK, tc::SK_BM)) return false;
+  if (!make_map(&mo, omT16, bf, (uint64_t)Jpad, (uint64_t)LPN, (uint64_t)Jpad, tc::SK_BK, (uint32_t)LPN)) return false;
+  const int64_t ntiles = (N + tc::SK_BM - 1) / tc::SK_BM;
+  const int grid = (int)std::min<int64_t>(ntiles, num_sms);
+  if (LPN == 32) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_sketch_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SketchSmem<32>::BYTES);
+      attr = true;
+    }
+    tc::k_sketch_tc<32><<<grid, 192, tc::SketchSmem<32>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_sketch_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SketchSmem<64>::BYTES);
+      attr = true;
+    }
+    tc::k_sketch_tc<64><<<grid, 192, tc::SketchSmem<64>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status);
+  }
+  return true;
+}
+
+bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
+                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
+                       float* B1, double* xpart, int nJb, int num_sms, int* status, cudaStream_t s) {
+  const bool bf = dt == DPAR2_BF16;
+  CUtensorMap mx, mq;
+  if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, 64, tc::PJ_BK)) return false;
+  if (!make_map(&mq, Qs, bf, (uint64_t)Npad, (uint64_t)(3 * LPN), (uint64_t)Npad, tc::PJ_BK, (uint32_t)(3 * LPN)))
+    return false;
+  const int64_t nitems = (int64_t)K * nJb;
+  const int grid = (int)std::min<int64_t>(nitems, num_sms);
+  if (LPN == 32) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_project_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<32>::BYTES);
+      attr = true;
+    }
+    tc::k_project_tc<32><<<grid, 224, tc::ProjSmem<32>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
+                                                                      nJb, bf ? 1 : 0, status);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_project_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<64>::BYTES);
+      attr = true;
+    }
+    tc::k_project_tc<64><<<grid, 224, tc::ProjSmem<64>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
+                                                                      nJb, bf ? 1 : 0, status);
+  }
+  return true;
+}
+
+void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s) {
+  const int64_t n = (int64_t)LPN * Jpad;
+  tc::k_omega_t16<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(om_pad, Jpad, LP, LPN,
+                                                                                     dt == DPAR2_BF16 ? 1 : 0, out);
+}
+
+void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
+                   int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s) {
+  dim3 grid((unsigned)std::max<int64_t>(1, (maxPad + 127) / 128), K);
+  tc::k_qsplit<<<grid, 128, 0, s>>>(Q, LP, LPN, d_off, d_poff, K, Npad, dt == DPAR2_BF16 ? 1 : 0, out);
+}
+
+}  // namespace dp2

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("dtype,K,J,R,p", [(torch.float32, 12, 80, 6, 10), (torch.bfloat16, 12, 80, 6, 10),
                                            (torch.float32, 12, 64, 10, 10), (torch.float32, 64, 64, 10, 10),
-                                           (torch.float32, 10, 300, 20, 10), (torch.bfloat16, 10, 130, 30, 20)])
+                                           (torch.float32, 10, 300, 20, 10), (torch.bfloat16, 10, 130, 30, 20),
+                                           (torch.float16, 12, 257, 10, 10), (torch.bfloat16, 6, 200, 30, 20),
+                                           (torch.bfloat16, 40, 2049, 10, 10)])
 def test_stage1_intermediates(dtype, K, J, R, p):
     api = api_or_skip()
     ctx = api.Context(0)
