@@ -469,14 +469,15 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
       void* Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * Npad);
       launch_qsplit(Y, LP, LPN, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
       const int nJb_tc = (Jp + 127) / 128;
-      double* xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc);
+      // one partial ||X_k||^2 per (slice, column block, norm warp)
+      double* xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
       CK(cudaStreamSynchronize(s));  // hp must outlive the pageable copy
       tbegin(ctx, s, DPAR2_PH_PROJECT);
       projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, LPN, LP, B1, xp, nJb_tc,
                                     ctx->num_sms, ctx->d_status, s);
       if (projected) {
         xpart = xp;
-        nJb_used = nJb_tc;
+        nJb_used = nJb_tc * kProjNormWarps;
       }
     } else {
       tbegin(ctx, s, DPAR2_PH_PROJECT);

@@ -69,6 +69,7 @@ int project_blocks(int Jp, int LP);
 
 // ---- stage 1, tensor-core path (16-bit X, tcgen05 + TMA) ----
 bool tc_available();
+constexpr int kProjNormWarps = 8;  // partial ||X_k||^2 per column block of the tensor-core projection
 int tc_lpn(int ell);  // MMA N width of the sketch: 32 or 64
 void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s);
 bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const void* omT16, int Jpad,
@@ -133,6 +134,8 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);
 int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
+// register-resident Q-step (lane = column); false when R has no instantiation (R > 32)
+bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);
 void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);

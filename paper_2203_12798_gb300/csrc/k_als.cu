@@ -754,6 +754,7 @@ void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
 
 void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
   const int R = b.R, nw = als_warps(R);
+  if (launch_qstep_reg(b, b.part, 2 * R * R + 2, 0, s)) return;
   k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part,
                                                      2 * R * R + 2, b.status, 0);
 }
@@ -767,8 +768,9 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   float* p1 = b.part;
   float* p2 = b.part + (size_t)b.nblk * ps;
   float* p3 = b.part + (size_t)2 * b.nblk * ps;
-  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
-                                                     b.status, 1);
+  if (!launch_qstep_reg(b, p1, ps, 1, s))
+    k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
+                                                       b.status, 1);
   k_update_h<<<1, 512, 0, s>>>(R, p1, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small, b.status);
   k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps);
   k_update_v<<<1, 512, 0, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,

@@ -1,0 +1,261 @@
+// Q-step of the ALS iterations (Alg. 3 first inner loop; Eq. q_k), register
+// resident: for every slice k
+//   T_k = F~_k Psi S_k H^T  (R x R),  T_k = Z_k Sigma_k P_k^T  (one-sided Jacobi),
+//   Upol_k = Z_k P_k^T,  Pi_k = Upol_k^T F~_k,
+// plus the Lemma 1 partial sum  G1 += (Pi_k Psi) diag(W(k,:)).
+//
+// Layout: one problem per group of R lanes (floor(32 / R) problems per warp);
+// lane c of a group holds column c of T and column c of the accumulated right
+// rotations V in registers.  Each Jacobi step pairs columns by the cyclic
+// round-robin ordering; the two lanes of a pair exchange their columns with
+// shuffles and compute the same rotation (same operands, same operation order)
+// so no shared state is needed.  Small products go through per-group shared
+// memory.  R is a compile-time constant; ranks that are not instantiated run
+// padded with zero rows / columns (zero columns are never rotated and get
+// zero singular values, so the padded problem's polar factor restricted to
+// the first R_actual rows / columns is the actual one).
+#include "common.cuh"
+#include "internal.h"
+
+namespace dp2 {
+
+template <int R>
+__global__ void __launch_bounds__(256) k_qstep_reg(int K, int Ra, const float* __restrict__ Ft,
+                                                   const double* __restrict__ Psi, const float* __restrict__ W,
+                                                   const float* __restrict__ H, float* __restrict__ Upol,
+                                                   float* __restrict__ Pi, float* __restrict__ part, int pstride,
+                                                   int* __restrict__ status, int want_g1) {
+  constexpr int G = 32 / R;  // problems per warp
+  constexpr int RR = R * R;
+  constexpr int M = R + (R & 1);  // round-robin players (one dummy when R is odd)
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ float ps[RR], hs[RR];
+  extern __shared__ float sm[];  // [nw][G][3 RR] group scratch, then [nw][G][RR] G1 slots
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / R, c = lane - g * R;
+  const bool lane_act = g < G;
+  float* gs = sm + (size_t)(warp * G + (lane_act ? g : 0)) * 3 * RR;
+  float* Fs = gs;
+  float* Ts = gs + RR;
+  float* Ps = gs + 2 * RR;
+  float* slots = sm + (size_t)nw * G * 3 * RR;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e % R;
+    const bool in = a < Ra && b < Ra;
+    ps[e] = in ? (float)Psi[a * Ra + b] : 0.f;
+    hs[e] = in ? H[a * Ra + b] : 0.f;
+  }
+  __syncthreads();
+  const float tol = fmaxf(1e-6f, (float)Ra * 1.2e-7f);
+  const int RaRa = Ra * Ra;
+  float acc[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) acc[i] = 0.f;
+
+  for (int64_t kb = ((int64_t)blockIdx.x * nw + warp) * G; kb < K; kb += (int64_t)gridDim.x * nw * G) {
+    const int64_t k = kb + g;
+    const bool act = lane_act && k < K;
+    // F~_k, column c
+    if (lane_act) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) Fs[i * R + c] = (act && i < Ra && c < Ra) ? Ft[k * RaRa + i * Ra + c] : 0.f;
+    }
+    float wk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) wk[r] = (act && r < Ra) ? W[k * Ra + r] : 0.f;
+    __syncwarp();
+    // A1 = F~_k Psi, column c
+    float t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < R; ++m) s = fmaf(Fs[i * R + m], ps[m * R + c], s);
+      t[i] = s;
+    }
+    if (lane_act) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) Ts[i * R + c] = t[i];
+    }
+    __syncwarp();
+    // T = A1 S_k H^T, column c:  T(i, c) = sum_r A1(i, r) W(k, r) H(c, r)
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s = fmaf(Ts[i * R + r], wk[r] * hs[c * R + r], s);
+      t[i] = s;
+    }
+    float v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = (i == c) ? 1.f : 0.f;
+
+    // ---- one-sided Jacobi, parallel round-robin ordering
+    int sweep = 0;
+    for (; sweep < 30; ++sweep) {
+      bool rotated = false;
+      for (int rr = 0; rr < M - 1; ++rr) {
+        int p;
+        if (c == 0) {
+          p = 1 + rr;
+        } else {
+          const int x = c - 1;
+          p = (x == rr) ? 0 : 1 + ((2 * rr - x + 2 * (M - 1)) % (M - 1));
+        }
+        const bool pair = lane_act && p < R;
+        const int src = pair ? g * R + p : lane;
+        float tp[R], vp[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          tp[i] = __shfl_sync(FULL, t[i], src);
+          vp[i] = __shfl_sync(FULL, v[i], src);
+        }
+        if (pair) {
+          const bool lo = c < p;
+          float a = 0.f, b = 0.f, gm = 0.f;
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const float tl = lo ? t[i] : tp[i], th = lo ? tp[i] : t[i];
+            a = fmaf(tl, tl, a);
+            b = fmaf(th, th, b);
+            gm = fmaf(tl, th, gm);
+          }
+          if (a > 0.f && b > 0.f) {
+            const float rel = fabsf(gm) * rsqrtf(a) * rsqrtf(b);
+            if (rel > tol) {
+              rotated = true;
+              const float zeta = (b - a) / (2.f * gm);
+              const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+              const float cs = rsqrtf(1.f + tt * tt), sn = cs * tt;
+#pragma unroll
+              for (int i = 0; i < R; ++i) {
+                const float tl = lo ? t[i] : tp[i], th = lo ? tp[i] : t[i];
+                t[i] = lo ? (cs * tl - sn * th) : (sn * tl + cs * th);
+                const float vl = lo ? v[i] : vp[i], vh = lo ? vp[i] : v[i];
+                v[i] = lo ? (cs * vl - sn * vh) : (sn * vl + cs * vh);
+              }
+            }
+          }
+        }
+      }
+      if (!__any_sync(FULL, rotated)) break;
+    }
+    if (sweep == 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
+
+    // ---- polar factor Upol = sum_i z_i v_i^T over sigma_i > cut
+    float s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < R; ++i) s2 = fmaf(t[i], t[i], s2);
+    const float sg = sqrtf(s2);
+    float smax = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) smax = fmaxf(smax, __shfl_sync(FULL, sg, lane_act ? g * R + j : lane));
+    const float inv = (sg > smax * (float)Ra * 1.2e-7f && sg > 0.f) ? 1.f / sg : 0.f;
+    __syncwarp();
+    if (lane_act) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        Ts[i * R + c] = t[i] * inv;  // Z column c
+        Ps[i * R + c] = v[i];        // P column c
+      }
+    }
+    __syncwarp();
+    float up[R];  // Upol column c: Upol(a, c) = sum_i Z(a, i) P(c, i)
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) s = fmaf(Ts[a * R + i], Ps[c * R + i], s);
+      up[a] = s;
+    }
+    if (act && c < Ra) {
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+        if (a < Ra) Upol[k * RaRa + a * Ra + c] = up[a];
+    }
+    __syncwarp();
+    if (lane_act) {
+#pragma unroll
+      for (int a = 0; a < R; ++a) Ts[a * R + c] = up[a];
+    }
+    __syncwarp();
+    float pc[R];  // Pi column c: Pi(a, c) = sum_i Upol(i, a) F~(i, c)
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) s = fmaf(Ts[i * R + a], Fs[i * R + c], s);
+      pc[a] = s;
+    }
+    if (act && c < Ra) {
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+        if (a < Ra) Pi[k * RaRa + a * Ra + c] = pc[a];
+    }
+    if (want_g1) {
+      __syncwarp();
+      if (lane_act) {
+#pragma unroll
+        for (int a = 0; a < R; ++a) Ps[a * R + c] = pc[a];
+      }
+      __syncwarp();
+      // Lemma 1: G1(i, c) += W(k, c) (Pi Psi)(i, c)
+      const float wc = act ? wk[c] : 0.f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < R; ++m) s = fmaf(Ps[i * R + m], ps[m * R + c], s);
+        acc[i] = fmaf(wc, s, acc[i]);
+      }
+    }
+    __syncwarp();
+  }
+  if (!want_g1) return;
+  if (lane_act) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) slots[(size_t)(warp * G + g) * RR + i * R + c] = acc[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RaRa; e += blockDim.x) {
+    const int i = e / Ra, cc = e % Ra;
+    float s = 0.f;
+    for (int q = 0; q < nw * G; ++q) s += slots[(size_t)q * RR + i * R + cc];
+    part[(int64_t)blockIdx.x * pstride + e] = s;
+  }
+}
+
+template <int R>
+static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+  constexpr int G = 32 / R;
+  const size_t per_warp = (size_t)G * 4 * R * R * sizeof(float);
+  int nw = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
+  const size_t smem = nw * per_warp;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_qstep_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    attr = true;
+  }
+  k_qstep_reg<R><<<b.nblk, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
+                                               b.status, want_g1);
+}
+
+// Launches the register-resident Q-step when the rank has an instantiation
+// (exact for R in {10, 20, 30}, zero-padded to 8, 16, 24 or 32 otherwise);
+// returns false for R > 32.
+bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+  switch (b.R) {
+    case 10: qreg<10>(b, part, pstride, want_g1, s); return true;
+    case 20: qreg<20>(b, part, pstride, want_g1, s); return true;
+    case 30: qreg<30>(b, part, pstride, want_g1, s); return true;
+    default: break;
+  }
+  if (b.R <= 8) qreg<8>(b, part, pstride, want_g1, s);
+  else if (b.R <= 16) qreg<16>(b, part, pstride, want_g1, s);
+  else if (b.R <= 24) qreg<24>(b, part, pstride, want_g1, s);
+  else if (b.R <= 32) qreg<32>(b, part, pstride, want_g1, s);
+  else return false;
+  return true;
+}
+
+}  // namespace dp2

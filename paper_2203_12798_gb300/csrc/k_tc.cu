@@ -12,7 +12,8 @@
 //   warps 2-5   epilogue: tcgen05.ld the FP32 accumulator (one TMEM lane per
 //               output row), write it out; the accumulator is double-buffered
 //               in TMEM so the epilogue of one tile overlaps the next tile's MMAs;
-//   warp 6      (project only) sums the squares of the staged X tiles.
+//   warps 6-13  (project only) sum the squares of the staged X tiles, each
+//               warp one eighth of every stage.
 // Every mbarrier wait is bounded by %globaltimer (kWaitNs); a wait that runs out
 // raises a CTA-wide abort flag, every role stops issuing work, waits (bounded)
 // for its in-flight copies / MMAs, TMEM is released and the status word gets
@@ -315,6 +316,8 @@ __global__ void __launch_bounds__(192, 1) k_sketch_tc(const __grid_constant__ CU
 
 // -------------------------------------------------------------- project ----
 constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
+constexpr int PJ_NORM_WARPS = kProjNormWarps;          // warps 6 .. 6 + PJ_NORM_WARPS - 1
+constexpr int PJ_THREADS = 32 * (6 + PJ_NORM_WARPS);
 
 template <int LPN>
 struct ProjSmem {
@@ -325,7 +328,7 @@ struct ProjSmem {
 };
 
 template <int LPN>
-__global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ CUtensorMap tmX,
+__global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_constant__ CUtensorMap tmX,
                                                        const __grid_constant__ CUtensorMap tmQ,
                                                        const int64_t* __restrict__ off,
                                                        const int64_t* __restrict__ poff, int K, int J, int Jp,
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ C
   if (threadIdx.x == 0) {
     for (int s = 0; s < PJ_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);  // MMA commit + norm warp
+      mbar_init(&empty[s], 1 + PJ_NORM_WARPS);  // MMA commit + one arrival per norm warp
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accfull[a], 1);
@@ -483,8 +486,14 @@ __global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ C
       tc_fence_before();
       mbar_arrive(&accempty[acc]);
     }
-  } else if (warp == 6) {
+  } else if (warp >= 6) {
     // ------------------------------------------------------------ ||X_k||^2
+    // Norm warp nw scans bytes [nw * BYTES_PER, (nw + 1) * BYTES_PER) of every
+    // staged X tile (two 8 KB boxes of 64 rows x 128 bytes), rows of the
+    // current slice only, and writes its own partial sum per work item
+    // (xpart is K x nJb x PJ_NORM_WARPS; a later kernel adds them in order).
+    constexpr int BYTES_PER = S::A / PJ_NORM_WARPS;
+    const int nw = warp - 6;
     int s = 0;
     uint32_t ph = 0;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -499,13 +508,13 @@ __global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ C
           break;
         }
         const int valid = (int)min64(PJ_BK, nrows - (int64_t)c * PJ_BK);
-        const uint8_t* a = sA + s * S::A;
-        // 2 boxes x 64 rows x 128 bytes; lane reads 16 bytes (8 elements)
-        for (int it = 0; it < S::A / 512; ++it) {
-          const int byte = it * 512 + lane * 16;
+        const uint8_t* a = sA + s * S::A + nw * BYTES_PER;
+#pragma unroll
+        for (int it = 0; it < BYTES_PER / 512; ++it) {
+          const int byte = nw * BYTES_PER + it * 512 + lane * 16;
           const int row = (byte % (S::A / 2)) / 128;
           if (row < valid) {
-            const uint4 u = *reinterpret_cast<const uint4*>(a + byte);
+            const uint4 u = *reinterpret_cast<const uint4*>(a + it * 512 + lane * 16);
             float f[8];
             if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
             else Vec16<__half>::unpack(u, f);
@@ -522,7 +531,7 @@ __global__ void __launch_bounds__(224, 1) k_project_tc(const __grid_constant__ C
       }
       if (!ok) break;
       acc = warp_sum(acc);
-      if (lane == 0) xpart[(int64_t)k * nJb + jb] = (double)acc;
+      if (lane == 0) xpart[((int64_t)k * nJb + jb) * PJ_NORM_WARPS + nw] = (double)acc;
     }
   }
   tc_fence_before();
@@ -664,7 +673,7 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
       cudaFuncSetAttribute(tc::k_project_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<32>::BYTES);
       attr = true;
     }
-    tc::k_project_tc<32><<<grid, 224, tc::ProjSmem<32>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
+    tc::k_project_tc<32><<<grid, tc::PJ_THREADS, tc::ProjSmem<32>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
                                                                       nJb, bf ? 1 : 0, status);
   } else {
     static bool attr = false;
@@ -672,7 +681,7 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
       cudaFuncSetAttribute(tc::k_project_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<64>::BYTES);
       attr = true;
     }
-    tc::k_project_tc<64><<<grid, 224, tc::ProjSmem<64>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
+    tc::k_project_tc<64><<<grid, tc::PJ_THREADS, tc::ProjSmem<64>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
                                                                       nJb, bf ? 1 : 0, status);
   }
   return true;
