@@ -115,7 +115,8 @@ int gram_splits(int K, int64_t maxI) {
 
 // CholeskyQR2 of the per-slice sketches Y (rows x LP, in place): after the
 // call Y holds Q1 = Y R1^+ and M2 = R2^+ with Q = Q1 M2 column-orthonormal on
-// its numerical rank (FP64 Grams; dependent columns dropped).
+// its numerical rank (FP64 Grams; FP64 Cholesky for the first step, FP32 for
+// the second, whose Gram is near the identity; dependent columns dropped).
 void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI, int ell, int LP, float* M2,
              int* rank, cudaStream_t s, const char* tag) {
   std::string t(tag);
@@ -124,10 +125,10 @@ void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI
   const int nsplit = gram_splits(K, maxI);
   double* Gp = nsplit > 1 ? wsget<double>(ctx, (t + "_Gp").c_str(), (size_t)K * nsplit * LP * LP) : nullptr;
   launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
-  launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, s);
+  launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, true, s);
   launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
   launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
-  launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, s);
+  launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, false, s);
 }
 
 __global__ void k_b1_to_omk(const float* __restrict__ B1, int K, int ell, int LP, int J, int Jp, int Jpad,
@@ -615,7 +616,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.nblk = als_blocks(K, R, ctx->num_sms);
     b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.nblk * (2 * RR + 2));
     b.loss = wsget<double>(ctx, "als_loss", (size_t)opt->max_iter);
-    b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR);
+    b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR + 8);
     b.status = ctx->d_status;
     tbegin(ctx, s, DPAR2_PH_ALS);
     launch_als_init(b, v0, s);

@@ -58,6 +58,87 @@ __device__ inline void df_mac(DF& s, float a, float b) {
 }
 __device__ inline double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
 
+// ------------------------------------------- warp-parallel small Cholesky ----
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this part, so
+// the small factorisations below avoid divisions and square roots (one
+// reciprocal square root per pivot) and spread every elimination step over
+// the 32 lanes of a warp.
+
+// 1/sqrt(d) for d > 0.  Float: the hardware estimate.  Double: the float
+// estimate refined by one Newton step for the reciprocal square root,
+// y <- y + y (1 - d y^2) / 2, which turns a relative error e into about
+// 1.5 e^2 (about 1e-14 here); outside the float range, 1 / sqrt(d) in double.
+__device__ inline float rsqrt_nr(float d) { return rsqrtf(d); }
+__device__ inline double rsqrt_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  const double y = (double)rsqrtf((float)d);
+  const double r = fma(-(d * y), y, 1.0);
+  return fma(0.5 * y, r, y);
+}
+
+// Upper-triangle index table of an n x n matrix (n <= 255), row-major: entry
+// tri_start(c, n) + (e - c) holds (c << 8) | e for c <= e < n.
+__host__ __device__ inline int tri_start(int c, int n) { return c * n - c * (c - 1) / 2; }
+__device__ inline void warp_pair_table(unsigned short* pairs, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < n; c += 32) {
+    const int b = tri_start(c, n);
+    for (int e = c; e < n; ++e) pairs[b + e - c] = (unsigned short)((c << 8) | e);
+  }
+  __syncwarp();
+}
+
+// Right-looking Cholesky A = R^T R by one warp.  A (n x n, row-major): the
+// upper triangle is read and overwritten by R.  The pivot d_j (A_jj after the
+// updates of steps < j) is kept when d_j > thr; otherwise (or for every pivot
+// when drop_all) row j of R is zero.  rinv[j] = 1 / R_jj, 0 for a dropped
+// pivot.  Returns the number of dropped pivots (the same in every lane).
+template <typename T>
+__device__ int warp_chol_upper(T* A, int n, T thr, bool drop_all, T* rinv, const unsigned short* pairs) {
+  const int lane = threadIdx.x & 31;
+  const int P = n * (n + 1) / 2;
+  int nd = 0;
+  for (int j = 0; j < n; ++j) {
+    const T d = A[j * n + j];
+    const bool drop = drop_all || !(d > thr);
+    const T y = drop ? T(0) : rsqrt_nr(d);
+    nd += drop;
+    for (int c = j + 1 + lane; c < n; c += 32) A[j * n + c] *= y;
+    __syncwarp();
+    if (lane == 0) {
+      A[j * n + j] = drop ? T(0) : d * y;
+      rinv[j] = y;
+    }
+    for (int t = tri_start(j + 1, n) + lane; t < P; t += 32) {
+      const int c = pairs[t] >> 8, e = pairs[t] & 255;
+      A[c * n + e] -= A[j * n + c] * A[j * n + e];
+    }
+    __syncwarp();
+  }
+  return nd;
+}
+
+// Mi = R^{-1} for the upper-triangular R of warp_chol_upper (rinv = its
+// reciprocal diagonal, 0 at dropped pivots) by back substitution: row m of
+// Mi is finished from the bottom up and its contribution pushed to the rows
+// above it.  Mi (n x n) must be zero on entry; rows and columns of dropped
+// pivots stay zero.
+template <typename T>
+__device__ void warp_tri_inv(const T* Rm, int n, const T* rinv, T* Mi) {
+  const int lane = threadIdx.x & 31;
+  for (int m = n - 1; m >= 0; --m) {
+    const T ym = rinv[m];
+    for (int c = m + lane; c < n; c += 32) Mi[m * n + c] = ((c == m ? T(1) : T(0)) - Mi[m * n + c]) * ym;
+    __syncwarp();
+    const int w = n - m;
+    for (int t = lane; t < m * w; t += 32) {
+      const int i = t / w, c = m + (t - i * w);
+      Mi[i * n + c] = fma(Rm[i * n + m], Mi[m * n + c], Mi[i * n + c]);
+    }
+    __syncwarp();
+  }
+}
+
 // 16-bit element conversions.
 template <typename T>
 __device__ inline float to_f(T v);

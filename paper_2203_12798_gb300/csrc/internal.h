@@ -85,8 +85,9 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
 // nsplit blocks (partials in Gpart, K * nsplit * LP * LP) for few long slices.
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
                     int nsplit, cudaStream_t s);
+// fp64: factorise in FP64 (first CholeskyQR step) or FP32 (second step).
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
-                      cudaStream_t s);
+                      bool fp64, cudaStream_t s);
 void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s);
 void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s);
 void launch_gram_b1(const float* B1, int Jp, int J, int K, int LP, double* G, cudaStream_t s);

@@ -287,12 +287,14 @@ __global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __
 
 // --------------------------------------------------- Lemma 3 and W update --
 // W_k = G3_k Ginv with G3(k, r) = H(:, r)^T Pi_k Psi(:, r); also the block
-// partials of W^T W (R x R) and of the convergence value e (last entry).
+// partials of W^T W (R x R) and of the convergence value e (entries RR and
+// RR + 1: the hi and lo floats of a double-float sum).
 __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* __restrict__ Psi,
                       const float* __restrict__ H, const double* __restrict__ Ginv, const double* __restrict__ HtH,
                       const double* __restrict__ VtV, float* __restrict__ W, float* __restrict__ part,
                       int pstride) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ float ered[32][2];
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* ps = sm;
@@ -312,6 +314,11 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
   for (int e = threadIdx.x; e < nw * (RR + 1); e += blockDim.x) slots[e] = 0.f;
   __syncthreads();
   float* slot = slots + warp * (RR + 1);
+  // e_k = ||Pi_k||^2 - 2 w . g3 + w (HtH*VtV) w, accumulated per lane as a
+  // double-float sum of exact products
+  DF ek;
+  ek.hi = 0.f;
+  ek.lo = 0.f;
   for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
     for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
     __syncwarp();
@@ -332,44 +339,36 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
       W[(int64_t)k * R + r] = s;
     }
     __syncwarp();
-    // e_k in FP64 from fp32 inputs: ||Pi||^2 - 2 w . g3 + w (HtH*VtV) w
-    double ek = 0.0;
     for (int e = lane; e < RR; e += 32) {
-      const int a = e / R, b = e % R;
-      ek += (double)pks[e] * pks[e] + (double)wn[a] * hv[e] * wn[b];
+      const int a = e / R, b = e - a * R;
+      df_mac(ek, pks[e], pks[e]);
+      df_mac(ek, wn[a] * wn[b], hv[e]);
+      slot[e] += wn[a] * wn[b];
     }
-    for (int r = lane; r < R; r += 32) ek -= 2.0 * (double)wn[r] * g3[r];
-    ek = warp_sum(ek);
-    for (int e = lane; e < RR; e += 32) slot[e] += wn[e / R] * wn[e % R];
-    if (lane == 0) slot[RR] += (float)ek;
+    for (int r = lane; r < R; r += 32) df_mac(ek, -2.f * wn[r], g3[r]);
     __syncwarp();
   }
+  // lane sums -> warp (hi, lo) in double, then per block
+  double ev = warp_sum(df_value(ek));
+  if (lane == 0) {
+    ered[warp][0] = (float)ev;
+    ered[warp][1] = (float)(ev - (double)(float)ev);
+  }
   __syncthreads();
-  for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     float s = 0.f;
     for (int w = 0; w < nw; ++w) s += slots[w * (RR + 1) + e];
     part[(int64_t)blockIdx.x * pstride + e] = s;
   }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)ered[w][0] + (double)ered[w][1];
+    part[(int64_t)blockIdx.x * pstride + RR] = (float)s;
+    part[(int64_t)blockIdx.x * pstride + RR + 1] = (float)(s - (double)(float)s);
+  }
 }
 
 // -------------------------------------------------------- FP64 small solves --
-// Cholesky factor of the SPD matrix A (n x n) in place (lower L), one thread.
-__device__ bool chol_inplace(double* A, int n) {
-  for (int j = 0; j < n; ++j) {
-    double d = A[j * n + j];
-    for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
-    if (!(d > 1e-300)) return false;
-    d = sqrt(d);
-    A[j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double s = A[i * n + j];
-      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
-      A[i * n + j] = s / d;
-    }
-  }
-  return true;
-}
-
 // Symmetric FP64 Jacobi eigendecomposition (cyclic, one thread) for the
 // pseudoinverse fallback: A <- diag, V eigenvectors.
 __device__ void jacobi_eig_f64(double* A, double* V, int n) {
@@ -408,29 +407,38 @@ __device__ void jacobi_eig_f64(double* A, double* V, int n) {
   }
 }
 
-// Inv <- A^+ for symmetric PSD A (n x n, FP64), computed by the whole block;
-// Cholesky inverse, or the eigen pseudoinverse (MATLAB tolerance n eps ||A||)
-// when a pivot fails.  Work arrays: L (n x n), V (n x n).
-__device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* V, int n, int* status) {
+// Inv <- A^+ for symmetric PSD A (n x n, FP64), computed by the whole block:
+// Cholesky A = R^T R by warp 0 and Inv = R^-1 R^-T, or the eigen
+// pseudoinverse (MATLAB tolerance n eps ||A||) when a pivot is not above
+// 1e-300.  sh: shared workspace of spd_pinv_smem(n) bytes; L, V: n x n work
+// arrays of the fallback.
+__host__ __device__ inline size_t spd_pinv_smem(int n) {
+  return (size_t)(2 * n * n + n) * sizeof(double) + (size_t)(n * (n + 1) / 2) * sizeof(unsigned short);
+}
+
+__device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* V, int n, double* sh,
+                               int* status) {
   __shared__ int ok;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e];
-  __syncthreads();
-  if (threadIdx.x == 0) ok = chol_inplace(L, n);
+  double* Rm = sh;
+  double* Mi = Rm + n * n;
+  double* rinv = Mi + n * n;
+  unsigned short* pairs = reinterpret_cast<unsigned short*>(rinv + n);
+  if (threadIdx.x < 32) {
+    for (int e = threadIdx.x; e < n * n; e += 32) {
+      Rm[e] = A[e];
+      Mi[e] = 0.0;
+    }
+    warp_pair_table(pairs, n);
+    const int nd = warp_chol_upper<double>(Rm, n, 1e-300, false, rinv, pairs);
+    if (nd == 0) warp_tri_inv<double>(Rm, n, rinv, Mi);
+    if (threadIdx.x == 0) ok = (nd == 0);
+  }
   __syncthreads();
   if (ok) {
-    // Inv = L^-T L^-1: column c of L^-1 by forward substitution (thread per column)
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      for (int i = 0; i < n; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int k = c; k < i; ++k) s -= L[i * n + k] * V[k * n + c];
-        V[i * n + c] = (i < c) ? 0.0 : s / L[i * n + i];
-      }
-    }
-    __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int a = e / n, b = e % n;
+      const int a = e / n, b = e - a * n;
       double s = 0.0;
-      for (int i = max(a, b); i < n; ++i) s += V[i * n + a] * V[i * n + b];
+      for (int i = max(a, b); i < n; ++i) s = fma(Mi[a * n + i], Mi[b * n + i], s);
       Inv[e] = s;
     }
     __syncthreads();
@@ -438,7 +446,7 @@ __device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* 
   }
   if (threadIdx.x == 0) {
     set_status(status, ST_PINV);
-    for (int e = 0; e < n * n; ++e) L[e] = A[e];  // the failed factorisation overwrote L
+    for (int e = 0; e < n * n; ++e) L[e] = A[e];
     jacobi_eig_f64(L, V, n);
     double mx = 0.0;
     for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(L[i * n + i]));
@@ -456,14 +464,25 @@ __device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* 
   __syncthreads();
 }
 
+// Scale factors 1 / ||column r|| for the R columns whose squared norms are
+// n2[r] (1 for a zero column); flags a non-finite norm.
+__device__ inline double inv_norm(double n2, int* status) {
+  if (!isfinite(n2)) set_status(status, ST_NONFINITE);
+  return n2 > 0.0 ? rsqrt_nr(n2) : 1.0;
+}
+
 // --------------------------------------------------------------- H update --
 // H = G1 (W^T W * V^T V)^+, columns normalised; HtH = H^T H.
 // When it > 0 it first closes the previous iteration: W^T W and its e from the
-// partials of the W update (part3).
-__global__ void k_update_h(int R, const float* __restrict__ part, const float* __restrict__ part3, int nblk,
-                           int pstride, int it, double* __restrict__ WtW, const double* __restrict__ VtV,
-                           float* __restrict__ H, double* __restrict__ HtH, double* __restrict__ loss,
-                           double* __restrict__ scratch, int* __restrict__ status) {
+// partials of the W update (part3; e as a (hi, lo) float pair).
+__global__ void __launch_bounds__(512) k_update_h(int R, const float* __restrict__ part,
+                                                  const float* __restrict__ part3, int nblk, int pstride, int it,
+                                                  double* __restrict__ WtW, const double* __restrict__ VtV,
+                                                  float* __restrict__ H, double* __restrict__ HtH,
+                                                  double* __restrict__ loss, double* __restrict__ scratch,
+                                                  int* __restrict__ status) {
+  extern __shared__ __align__(16) double ush[];
+  __shared__ double scl[kMaxR];
   const int RR = R * R;
   double* G1 = scratch;
   double* Gm = G1 + RR;
@@ -471,14 +490,15 @@ __global__ void k_update_h(int R, const float* __restrict__ part, const float* _
   double* L = Inv + RR;
   double* V = L + RR;
   double* Hn = V + RR;
-  double* W3 = Hn + RR;  // RR + 1
+  double* W3 = Hn + RR;  // RR + 2
   if (it > 0) {
-    block_reduce_parts(part3, nblk, pstride, RR + 1, W3);
+    block_reduce_parts(part3, nblk, pstride, RR + 2, W3);
     for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
       if (e < RR) WtW[e] = W3[e];
       else {
-        loss[it - 1] = W3[RR];
-        if (!isfinite(W3[RR])) set_status(status, ST_NONFINITE);
+        const double v = W3[RR] + W3[RR + 1];
+        loss[it - 1] = v;
+        if (!isfinite(v)) set_status(status, ST_NONFINITE);
       }
     }
     __syncthreads();
@@ -486,28 +506,27 @@ __global__ void k_update_h(int R, const float* __restrict__ part, const float* _
   block_reduce_parts(part, nblk, pstride, RR, G1);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * VtV[e];
   __syncthreads();
-  block_spd_pinv(Gm, Inv, L, V, R, status);
+  block_spd_pinv(Gm, Inv, L, V, R, ush, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const int i = e / R, r = e % R;
+    const int i = e / R, r = e - i * R;
     double s = 0.0;
-    for (int m = 0; m < R; ++m) s += G1[i * R + m] * Inv[m * R + r];
+    for (int m = 0; m < R; ++m) s = fma(G1[i * R + m], Inv[m * R + r], s);
     Hn[e] = s;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double n2 = 0.0;
-    for (int i = 0; i < R; ++i) n2 += Hn[i * R + r] * Hn[i * R + r];
-    const double nr = sqrt(n2);
-    if (!isfinite(nr)) set_status(status, ST_NONFINITE);
-    const double sc = nr > 1e-300 ? 1.0 / nr : 1.0;
-    for (int i = 0; i < R; ++i) Hn[i * R + r] *= sc;
+    for (int i = 0; i < R; ++i) n2 = fma(Hn[i * R + r], Hn[i * R + r], n2);
+    scl[r] = inv_norm(n2, status);
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) Hn[e] *= scl[e % R];
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     H[e] = (float)Hn[e];
-    const int a = e / R, b = e % R;
+    const int a = e / R, b = e - a * R;
     double s = 0.0;
-    for (int i = 0; i < R; ++i) s += Hn[i * R + a] * Hn[i * R + b];
+    for (int i = 0; i < R; ++i) s = fma(Hn[i * R + a], Hn[i * R + b], s);
     HtH[e] = s;
   }
 }
@@ -515,11 +534,14 @@ __global__ void k_update_h(int R, const float* __restrict__ part, const float* _
 // --------------------------------------------------------------- V update --
 // CV = g (W^T W * H^T H)^+ with columns normalised through D^T D; then
 // Psi = D^T D CV, V^T V = CV^T D^T D CV and Ginv = (V^T V * H^T H)^+ for the W update.
-__global__ void k_update_v(int R, const float* __restrict__ part, int nblk, int pstride,
-                           const double* __restrict__ WtW, const double* __restrict__ HtH,
-                           const double* __restrict__ DtD, float* __restrict__ CV, double* __restrict__ Psi,
-                           double* __restrict__ VtV, double* __restrict__ Ginv, double* __restrict__ scratch,
-                           int* __restrict__ status) {
+__global__ void __launch_bounds__(512) k_update_v(int R, const float* __restrict__ part, int nblk, int pstride,
+                                                  const double* __restrict__ WtW, const double* __restrict__ HtH,
+                                                  const double* __restrict__ DtD, float* __restrict__ CV,
+                                                  double* __restrict__ Psi, double* __restrict__ VtV,
+                                                  double* __restrict__ Ginv, double* __restrict__ scratch,
+                                                  int* __restrict__ status) {
+  extern __shared__ __align__(16) double ush[];
+  __shared__ double scl[kMaxR];
   const int RR = R * R;
   double* g = scratch;
   double* Gm = g + RR;
@@ -531,55 +553,55 @@ __global__ void k_update_v(int R, const float* __restrict__ part, int nblk, int 
   block_reduce_parts(part, nblk, pstride, RR, g);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
   __syncthreads();
-  block_spd_pinv(Gm, Inv, L, V, R, status);
+  block_spd_pinv(Gm, Inv, L, V, R, ush, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const int i = e / R, r = e % R;
+    const int i = e / R, r = e - i * R;
     double s = 0.0;
-    for (int m = 0; m < R; ++m) s += g[i * R + m] * Inv[m * R + r];
+    for (int m = 0; m < R; ++m) s = fma(g[i * R + m], Inv[m * R + r], s);
     C[e] = s;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {  // DC = DtD C
-    const int i = e / R, r = e % R;
+    const int i = e / R, r = e - i * R;
     double s = 0.0;
-    for (int m = 0; m < R; ++m) s += DtD[i * R + m] * C[m * R + r];
+    for (int m = 0; m < R; ++m) s = fma(DtD[i * R + m], C[m * R + r], s);
     DC[e] = s;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {  // ||V(:, r)||^2 = C(:, r)^T DtD C(:, r)
     double n2 = 0.0;
-    for (int i = 0; i < R; ++i) n2 += C[i * R + r] * DC[i * R + r];
-    const double nr = sqrt(fmax(n2, 0.0));
-    if (!isfinite(nr)) set_status(status, ST_NONFINITE);
-    const double sc = nr > 1e-300 ? 1.0 / nr : 1.0;
-    for (int i = 0; i < R; ++i) {
-      C[i * R + r] *= sc;
-      DC[i * R + r] *= sc;
-    }
+    for (int i = 0; i < R; ++i) n2 = fma(C[i * R + r], DC[i * R + r], n2);
+    scl[r] = inv_norm(fmax(n2, 0.0), status);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const int a = e / R, b = e % R;
+    const double sc = scl[e % R];
+    C[e] *= sc;
+    DC[e] *= sc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e - a * R;
     CV[e] = (float)C[e];
     Psi[e] = DC[e];
     double s = 0.0;
-    for (int i = 0; i < R; ++i) s += C[i * R + a] * DC[i * R + b];
+    for (int i = 0; i < R; ++i) s = fma(C[i * R + a], DC[i * R + b], s);
     VtV[e] = s;
     Gm[e] = s * HtH[e];
   }
   __syncthreads();
-  block_spd_pinv(Gm, Ginv, L, V, R, status);
+  block_spd_pinv(Gm, Ginv, L, V, R, ush, status);
 }
 
 // ----------------------------------------------------- iteration epilogue --
 __global__ void k_finish(int R, const float* __restrict__ part, int nblk, int pstride, double* __restrict__ WtW,
                          double* __restrict__ loss, int it, double* __restrict__ scratch, int* __restrict__ status) {
   const int RR = R * R;
-  block_reduce_parts(part, nblk, pstride, RR + 1, scratch);
+  block_reduce_parts(part, nblk, pstride, RR + 2, scratch);
   for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
-    const double v = scratch[e];
-    if (e < RR) WtW[e] = v;
+    if (e < RR) WtW[e] = scratch[e];
     else {
+      const double v = scratch[RR] + scratch[RR + 1];
       loss[it] = v;
       if (!isfinite(v)) set_status(status, ST_NONFINITE);
     }
@@ -742,6 +764,8 @@ void als_set_attrs() {
   cudaFuncSetAttribute(k_g2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g3w, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_fitness, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_update_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spd_pinv_smem(kMaxR));
+  cudaFuncSetAttribute(k_update_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spd_pinv_smem(kMaxR));
   done = true;
 }
 
@@ -771,9 +795,10 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   if (!launch_qstep_reg(b, p1, ps, 1, s))
     k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
                                                        b.status, 1);
-  k_update_h<<<1, 512, 0, s>>>(R, p1, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small, b.status);
+  const size_t psm = spd_pinv_smem(R);
+  k_update_h<<<1, 512, psm, s>>>(R, p1, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small, b.status);
   k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps);
-  k_update_v<<<1, 512, 0, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
+  k_update_v<<<1, 512, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
                                b.status);
   k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
       b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, p3, ps);

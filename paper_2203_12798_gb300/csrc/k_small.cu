@@ -22,8 +22,9 @@ __device__ inline double warp_max_d(double v) {
 // G_k (ell x ell, pitch LP, FP64) = Y_k^T Y_k over the rows of slice k.
 constexpr int GR_THREADS = 256;
 constexpr int GR_ROWS = 64;
-constexpr int GR_MAXP = 9;  // ceil(64*65/2 / 256)
 
+// GR_MAXP = pair slots per thread, ceil(ell (ell + 1) / 2 / 256) (1 for ell <= 22).
+template <int GR_MAXP>
 __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict__ Y, int LP,
                                                         const int64_t* __restrict__ off, int ell,
                                                         double* __restrict__ G, int nsplit) {
@@ -74,72 +75,48 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
 }
 
 // ------------------------------------------------------- Cholesky (drop) ----
-// G = R^T R column by column (R upper triangular, FP64).  A pivot
+// G = R^T R (R upper triangular) in precision T: FP64 for the first
+// CholeskyQR step (the Gram of the raw sketch squares its condition number),
+// FP32 for the second (the Gram of Q1 is close to the identity).  A pivot
 // d_j = G_jj - sum_i R_ij^2 <= tau * max_i G_ii marks column j as numerically
 // dependent on the columns before it: its row of R is zero and it is left
 // out of Q.  Output Minv (LP x LP float) = pseudo-inverse of R (zero rows and
 // columns at dropped indices), so that Q = Y Minv has orthonormal columns on
-// the kept index set and zero columns elsewhere.
+// the kept index set and zero columns elsewhere.  One warp per slice.
+template <typename T>
 __global__ void __launch_bounds__(32) k_chol_drop(const double* __restrict__ G, int ell, int LP, double tau,
                                                   float* __restrict__ Minv, int* __restrict__ rank,
                                                   int* __restrict__ status) {
-  extern __shared__ __align__(16) double sh[];
-  double* Rm = sh;              // ell x ell
-  double* Mi = sh + ell * ell;  // ell x ell
-  __shared__ int dropped[kMaxEll];
+  extern __shared__ __align__(16) unsigned char chol_sh[];
+  T* A = reinterpret_cast<T*>(chol_sh);  // ell x ell, becomes R
+  T* Mi = A + ell * ell;                  // ell x ell
+  __shared__ T rinv[kMaxEll];
+  __shared__ unsigned short pairs[kMaxEll * (kMaxEll + 1) / 2];
   const int k = blockIdx.x, lane = threadIdx.x;
   const double* g = G + (int64_t)k * LP * LP;
   double md = 0.0;
   bool bad = false;
-  for (int i = lane; i < ell; i += 32) {
-    const double v = g[i * LP + i];
-    if (!isfinite(v)) bad = true;
-    md = fmax(md, v);
+  for (int e = lane; e < ell * ell; e += 32) {
+    const int i = e / ell, c = e - i * ell;
+    const double v = g[i * LP + c];
+    if (i == c) {
+      if (!isfinite(v)) bad = true;
+      md = fmax(md, v);
+    }
+    A[e] = (T)v;
+    Mi[e] = T(0);
   }
   md = warp_max_d(md);
   bad = __any_sync(0xffffffffu, bad);
-  for (int j = 0; j < ell; ++j) {
-    double s = 0.0;
-    for (int i = lane; i < j; i += 32) s += Rm[i * ell + j] * Rm[i * ell + j];
-    s = warp_sum(s);
-    const double d = g[j * LP + j] - s;
-    const bool drop = !(d > tau * md) || bad;
-    const double rjj = drop ? 0.0 : sqrt(d);
-    if (lane == 0) {
-      dropped[j] = drop;
-      Rm[j * ell + j] = rjj;
-    }
-    for (int c = j + 1 + lane; c < ell; c += 32) {
-      double t = 0.0;
-      if (!drop) {
-        t = g[j * LP + c];
-        for (int i = 0; i < j; ++i) t -= Rm[i * ell + j] * Rm[i * ell + c];
-        t /= rjj;
-      }
-      Rm[j * ell + c] = t;
-    }
-    __syncwarp();
-  }
-  for (int c = lane; c < ell; c += 32) {
-    for (int i = ell - 1; i >= 0; --i) {
-      double v = 0.0;
-      if (i <= c && !dropped[c] && !dropped[i]) {
-        v = (i == c) ? 1.0 : 0.0;
-        for (int m = i + 1; m <= c; ++m) v -= Rm[i * ell + m] * Mi[m * ell + c];
-        v /= Rm[i * ell + i];
-      }
-      Mi[i * ell + c] = v;
-    }
-  }
-  __syncwarp();
+  warp_pair_table(pairs, ell);
+  const int nd = warp_chol_upper<T>(A, ell, (T)(tau * md), bad, rinv, pairs);
+  warp_tri_inv<T>(A, ell, rinv, Mi);
   float* out = Minv + (int64_t)k * LP * LP;
   for (int e = lane; e < LP * LP; e += 32) {
-    const int i = e / LP, c = e % LP;
-    out[e] = (i < ell && c < ell) ? (float)Mi[i * ell + c] : 0.f;
+    const int i = e / LP, c = e - i * LP;
+    const bool in = i < ell && c < ell && !bad && rinv[i] != T(0) && rinv[c] != T(0);
+    out[e] = in ? (float)Mi[i * ell + c] : 0.f;
   }
-  int nd = 0;
-  for (int j = lane; j < ell; j += 32) nd += dropped[j];
-  nd = __reduce_add_sync(0xffffffffu, nd);
   if (lane == 0) {
     if (rank) rank[k] = ell - nd;
     if (nd) set_status(status, ST_RANK_DROP);
@@ -185,7 +162,9 @@ __global__ void k_reduce_rows_f64(const double* __restrict__ part, int K, int n,
 
 // -------------------------------------------------------- Gram of B1 rows ----
 // G_k (LP x LP, FP64) = B1_k B1_k^T over columns j < J; B1_k is LP x Jp.
-// Threads own 4x4 tiles of the upper triangle; thread groups split the columns.
+// Threads own 4x4 tiles of the upper triangle; thread groups split the
+// columns.  The next 64-column chunk is loaded into registers while the
+// current one is consumed from shared memory.
 constexpr int GB_THREADS = 256;
 constexpr int GB_CJ = 64;
 
@@ -195,6 +174,7 @@ __global__ void __launch_bounds__(GB_THREADS) k_gram_b1(const float* __restrict_
   constexpr int T = LP / 4;
   constexpr int NT = T * (T + 1) / 2;
   constexpr int NG = GB_THREADS / NT > 0 ? GB_THREADS / NT : 1;
+  constexpr int PER = LP * GB_CJ / GB_THREADS;  // chunk elements per thread
   __shared__ __align__(16) float bs[GB_CJ][LP + 4];
   __shared__ float red[NG > 1 ? NG : 1][LP][LP + 1];
   const int k = blockIdx.x, tid = threadIdx.x;
@@ -212,13 +192,25 @@ __global__ void __launch_bounds__(GB_THREADS) k_gram_b1(const float* __restrict_
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   const float* src = B1 + (int64_t)k * LP * Jp;
+  float pre[PER];
+  auto fetch = [&](int j0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * GB_THREADS;
+      const int c = e / GB_CJ, jj = e % GB_CJ;
+      pre[u] = (j0 + jj < J) ? __ldg(src + (int64_t)c * Jp + j0 + jj) : 0.f;
+    }
+  };
+  fetch(0);
   for (int j0 = 0; j0 < J; j0 += GB_CJ) {
     __syncthreads();
-    for (int e = tid; e < LP * GB_CJ; e += GB_THREADS) {
-      const int c = e / GB_CJ, jj = e % GB_CJ;
-      bs[jj][c] = (j0 + jj < J) ? src[(int64_t)c * Jp + j0 + jj] : 0.f;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * GB_THREADS;
+      bs[e % GB_CJ][e / GB_CJ] = pre[u];
     }
     __syncthreads();
+    if (j0 + GB_CJ < J) fetch(j0 + GB_CJ);
     if (act) {
       for (int jj = grp; jj < GB_CJ; jj += NG) {
         const float4 va = *reinterpret_cast<const float4*>(&bs[jj][4 * ta]);
@@ -243,48 +235,47 @@ __global__ void __launch_bounds__(GB_THREADS) k_gram_b1(const float* __restrict_
   double* g = G + (int64_t)k * LP * LP;
   for (int e = tid; e < LP * LP; e += GB_THREADS) {
     const int a = e / LP, b = e % LP;
-    const int ua = min(a, b), ub = max(a, b);
-    if ((ua / 4) > (ub / 4)) continue;
-    double s = 0.0;
-    for (int q = 0; q < NG; ++q) s += (double)red[q][ua][ub];
-    // tiles on the diagonal hold both orders; off-diagonal tiles only ua < ub rows
-    if ((ua / 4) == (ub / 4)) {
-      s = 0.0;
-      for (int q = 0; q < NG; ++q) s += (double)red[q][a][b];
-    }
-    g[a * LP + b] = s;
+    // off-diagonal tiles hold only the (ua, ub) order; diagonal tiles both
+    const bool diag = (a / 4) == (b / 4);
+    const int ra = diag ? a : min(a, b), rb = diag ? b : max(a, b);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) s += red[q][ra][rb];
+    g[e] = (double)s;
   }
 }
 
 // ------------------------------------------------------ Jacobi eigensolver ----
-// Symmetric n x n matrix A (smem, pitch n+1, overwritten by its eigenvalues on
-// the diagonal) and eigenvectors V (smem, pitch n+1), computed by one warp
-// with the cyclic parallel ordering (round-robin pairs, n padded to even).
-// Stops when the off-diagonal Frobenius norm is <= tol * ||A||_F or after
-// max_sweeps sweeps (then returns false).
-__device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sweeps) {
+// Two-sided Jacobi eigensolver for a symmetric n x n matrix A (shared memory,
+// pitch n + 1) by one warp: each round of the cyclic round-robin ordering
+// rotates up to n/2 disjoint (p, q) planes at once, with the rows of all
+// planes, then the columns, spread over the lanes.  A is overwritten by its
+// eigenvalues on the diagonal and V (pitch n + 1) by the eigenvectors.  A
+// plane is left alone when |a_pq| <= tol sqrt|a_pp| sqrt|a_qq| or
+// |a_pq| <= tol ||A||_F / n; a rotated a_pq is set to zero.  Stops after a
+// sweep without rotations (true) or after max_sweeps (false).
+struct JacobiRound {
+  int p[32], q[32];
+  float c[32], s[32];
+};
+
+__device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sweeps, JacobiRound& rd) {
   const int lane = threadIdx.x & 31;
   const int ld = n + 1;
   const int m = n + (n & 1);  // players (one dummy when n is odd)
+  const int half = m / 2;
   for (int e = lane; e < n * n; e += 32) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.f : 0.f;
-  __syncwarp();
   float fro = 0.f;
   for (int e = lane; e < n * n; e += 32) fro += A[(e / n) * ld + e % n] * A[(e / n) * ld + e % n];
   fro = warp_sum(fro);
-  const float thr = tol * tol * fro;
+  const float floor_abs = tol * sqrtf(fro) / (float)n;
+  __syncwarp();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    float off = 0.f;
-    for (int e = lane; e < n * n; e += 32) {
-      const int i = e / n, j = e % n;
-      if (i != j) off += A[i * ld + j] * A[i * ld + j];
-    }
-    off = warp_sum(off);
-    if (off <= thr || fro == 0.f) return true;
+    bool any = false;
     for (int r = 0; r < m - 1; ++r) {
-      // pair of this lane (lanes >= m/2 idle in the parameter phase)
-      int p = -1, q = -1;
-      float c = 1.f, s = 0.f;
-      if (lane < m / 2) {
+      bool rot = false;
+      if (lane < half) {
+        int p, q;
         if (lane == 0) {
           p = 0;
           q = 1 + (r % (m - 1));
@@ -292,57 +283,71 @@ __device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sw
           p = 1 + ((r + lane) % (m - 1));
           q = 1 + ((r - lane + (m - 1)) % (m - 1));
         }
-        if (p > q) { int t = p; p = q; q = t; }
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, s = 0.f;
         if (q < n) {
-          const float apq = A[p * ld + q];
-          if (apq != 0.f) {
-            const float app = A[p * ld + p], aqq = A[q * ld + q];
+          const float apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+          const float mag = fabsf(apq);
+          if (mag > floor_abs && mag > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
             const float th = (aqq - app) / (2.f * apq);
-            const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(1.f + th * th));
-            c = rsqrtf(1.f + t * t);
+            const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+            c = rsqrtf(fmaf(t, t, 1.f));
             s = t * c;
+            rot = true;
           }
-        } else {
-          p = q = -1;
         }
+        rd.p[lane] = p;
+        rd.q[lane] = q;
+        rd.c[lane] = c;
+        rd.s[lane] = rot ? s : 0.f;
       }
-      // rows: A <- J^T A
+      if (!__any_sync(0xffffffffu, rot)) continue;
+      any = true;
       __syncwarp();
-      for (int pi = 0; pi < m / 2; ++pi) {
-        const int pp = __shfl_sync(0xffffffffu, p, pi), qq = __shfl_sync(0xffffffffu, q, pi);
-        const float cc = __shfl_sync(0xffffffffu, c, pi), ss = __shfl_sync(0xffffffffu, s, pi);
-        if (pp < 0 || ss == 0.f) continue;
-        for (int col = lane; col < n; col += 32) {
-          const float ap = A[pp * ld + col], aq = A[qq * ld + col];
-          A[pp * ld + col] = cc * ap - ss * aq;
-          A[qq * ld + col] = ss * ap + cc * aq;
-        }
+      // rows: A <- J^T A, every (plane, column) item
+      for (int t = lane; t < half * n; t += 32) {
+        const int pi = t / n, col = t - pi * n;
+        const float ss = rd.s[pi];
+        if (ss == 0.f) continue;
+        const int pp = rd.p[pi], qq = rd.q[pi];
+        const float cc = rd.c[pi];
+        const float ap = A[pp * ld + col], aq = A[qq * ld + col];
+        A[pp * ld + col] = cc * ap - ss * aq;
+        A[qq * ld + col] = ss * ap + cc * aq;
       }
       __syncwarp();
-      // columns: A <- A J, V <- V J
-      for (int pi = 0; pi < m / 2; ++pi) {
-        const int pp = __shfl_sync(0xffffffffu, p, pi), qq = __shfl_sync(0xffffffffu, q, pi);
-        const float cc = __shfl_sync(0xffffffffu, c, pi), ss = __shfl_sync(0xffffffffu, s, pi);
-        if (pp < 0 || ss == 0.f) continue;
-        for (int row = lane; row < n; row += 32) {
-          const float ap = A[row * ld + pp], aq = A[row * ld + qq];
-          A[row * ld + pp] = cc * ap - ss * aq;
-          A[row * ld + qq] = ss * ap + cc * aq;
-          const float vp = V[row * ld + pp], vq = V[row * ld + qq];
-          V[row * ld + pp] = cc * vp - ss * vq;
-          V[row * ld + qq] = ss * vp + cc * vq;
-        }
+      // columns: A <- A J, V <- V J, every (plane, row) item
+      for (int t = lane; t < half * n; t += 32) {
+        const int pi = t / n, row = t - pi * n;
+        const float ss = rd.s[pi];
+        if (ss == 0.f) continue;
+        const int pp = rd.p[pi], qq = rd.q[pi];
+        const float cc = rd.c[pi];
+        const float ap = A[row * ld + pp], aq = A[row * ld + qq];
+        A[row * ld + pp] = cc * ap - ss * aq;
+        A[row * ld + qq] = ss * ap + cc * aq;
+        const float vp = V[row * ld + pp], vq = V[row * ld + qq];
+        V[row * ld + pp] = cc * vp - ss * vq;
+        V[row * ld + qq] = ss * vp + cc * vq;
+      }
+      __syncwarp();
+      if (lane < half && rot) {
+        A[rd.p[lane] * ld + rd.q[lane]] = 0.f;
+        A[rd.q[lane] * ld + rd.p[lane]] = 0.f;
       }
       __syncwarp();
     }
+    if (!any) return true;
   }
   return false;
 }
 
 // --------------------------------------------------------- top eigenpairs ----
-// For slice k: Gt = M2^T G M2 (ell x ell), eigen-decomposed; T_k (LP x R) =
-// M2 U~_R with U~_R the eigenvectors of the R largest eigenvalues.  (B = M2^T
-// B1 is the projected sketch Q^T X, B B^T = Gt, and A_k = Q1 T_k.)
+// For slice k: Gt = M2^T G M2 (ell x ell, FP32), eigen-decomposed; T_k (LP x R)
+// = M2 U~_R with U~_R the eigenvectors of the R largest eigenvalues.  (B =
+// M2^T B1 is the projected sketch Q^T X, B B^T = Gt, and A_k = Q1 T_k.)  Only
+// the R leading eigenvectors are used, so FP32 products suffice: their error
+// is a rounding of ||Gt|| while those eigenvalues are a sizeable part of it.
 __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, const float* __restrict__ M2,
                                                 int ell, int LP, int R, float* __restrict__ T,
                                                 float* __restrict__ lam, int* __restrict__ status) {
@@ -351,40 +356,41 @@ __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, co
   float* A = sm;               // n x ld
   float* V = A + n * ld;       // n x ld
   float* Ms = V + n * ld;      // n x n  (M2 restricted)
-  float* Wt = Ms + n * n;      // n x n
+  float* Wt = Ms + n * n;      // n x n  (G, then G M2)
   __shared__ int order[kMaxEll];
+  __shared__ JacobiRound rd;
   const int k = blockIdx.x, lane = threadIdx.x;
   const double* g = G + (int64_t)k * LP * LP;
   const float* m2 = M2 + (int64_t)k * LP * LP;
-  for (int e = lane; e < n * n; e += 32) Ms[e] = m2[(e / n) * LP + e % n];
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, c = e - i * n;
+    Ms[e] = m2[i * LP + c];
+    A[i * ld + c] = (float)g[i * LP + c];
+  }
   __syncwarp();
   // Wt = G M2
   for (int e = lane; e < n * n; e += 32) {
-    const int i = e / n, c = e % n;
-    double s = 0.0;
-    for (int m = 0; m < n; ++m) s += g[i * LP + m] * (double)Ms[m * n + c];
-    Wt[e] = (float)s;
-  }
-  __syncwarp();
-  // A = M2^T Wt
-  for (int e = lane; e < n * n; e += 32) {
-    const int a = e / n, c = e % n;
+    const int i = e / n, c = e - i * n;
     float s = 0.f;
-    for (int i = 0; i < n; ++i) s = fmaf(Ms[i * n + a], Wt[i * n + c], s);
-    A[a * ld + c] = s;
+    for (int q = 0; q < n; ++q) s = fmaf(A[i * ld + q], Ms[q * n + c], s);
+    Wt[e] = s;
   }
   __syncwarp();
-  // symmetrise
+  // A = M2^T Wt, symmetrised
   for (int e = lane; e < n * n; e += 32) {
-    const int a = e / n, c = e % n;
-    if (a < c) {
-      const float v = 0.5f * (A[a * ld + c] + A[c * ld + a]);
-      A[a * ld + c] = v;
-      A[c * ld + a] = v;
+    const int a = e / n, c = e - a * n;
+    if (a > c) continue;
+    float s1 = 0.f, s2 = 0.f;
+    for (int i = 0; i < n; ++i) {
+      s1 = fmaf(Ms[i * n + a], Wt[i * n + c], s1);
+      s2 = fmaf(Ms[i * n + c], Wt[i * n + a], s2);
     }
+    const float v = 0.5f * (s1 + s2);
+    A[a * ld + c] = v;
+    A[c * ld + a] = v;
   }
   __syncwarp();
-  const bool ok = warp_jacobi_eig(A, V, n, 1e-7f, 40);
+  const bool ok = warp_jacobi_eig(A, V, n, 1e-7f, 40, rd);
   if (!ok && lane == 0) set_status(status, ST_SWEEP_CAP);
   __syncwarp();
   if (lane == 0) {
@@ -416,11 +422,28 @@ __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, co
 // -------------------------------------------------------- M blocks C_k B_k ----
 // M_k (J x R) = B1_k^T T_k; sigma_r = ||M_k(:, r)|| (the stage-1 singular
 // values B_k); columns with sigma_r <= tau * max sigma are zeroed in M_k and
-// T_k (numerical rank rule).
+// T_k (numerical rank rule).  Two passes over B1_k (norms and signs, then
+// M_k); the slices of the resident blocks (about 5 per SM) stay in L2 for the
+// second pass.  Every thread keeps 8 rows of B1_k in flight.
 constexpr int MB_THREADS = 256;
 
 template <int RB>
-__global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__ B1, int Jp, int J, int ell,
+__device__ inline void mblock_col(const float* __restrict__ b1, int Jp, int j, int ell, const float* ts, float* o) {
+#pragma unroll
+  for (int r = 0; r < RB; ++r) o[r] = 0.f;
+  for (int c0 = 0; c0 < ell; c0 += 8) {
+    float b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) b[u] = (c0 + u < ell) ? __ldg(b1 + (int64_t)(c0 + u) * Jp + j) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int r = 0; r < RB; ++r) o[r] = fmaf(b[u], ts[(c0 + u) * RB + r], o[r]);
+  }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 4 : 2) k_mblock(const float* __restrict__ B1, int Jp, int J, int ell,
                                                        int LP, int R, float* __restrict__ T,
                                                        float* __restrict__ Bk, float* __restrict__ Mblk,
                                                        int* __restrict__ rank, float tau) {
@@ -430,9 +453,10 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
   __shared__ float keep[RB];  // 0 (dropped) or the sign +-1 of a kept component
   const int k = blockIdx.x, tid = threadIdx.x;
   float* t = T + (int64_t)k * LP * R;
-  for (int e = tid; e < ell * RB; e += MB_THREADS) {
+  const int ellp = round_up(ell, 8);
+  for (int e = tid; e < ellp * RB; e += MB_THREADS) {
     const int c = e / RB, r = e % RB;
-    ts[e] = r < R ? t[c * R + r] : 0.f;
+    ts[e] = (r < R && c < ell) ? t[c * R + r] : 0.f;
   }
   __syncthreads();
   const float* b1 = B1 + (int64_t)k * LP * Jp;
@@ -441,13 +465,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
   for (int r = 0; r < RB; ++r) nrm[r] = csum[r] = 0.f;
   for (int j = tid; j < J; j += MB_THREADS) {
     float o[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) o[r] = 0.f;
-    for (int c = 0; c < ell; ++c) {
-      const float b = b1[(int64_t)c * Jp + j];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) o[r] = fmaf(b, ts[c * RB + r], o[r]);
-    }
+    mblock_col<RB>(b1, Jp, j, ell, ts, o);
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       nrm[r] = fmaf(o[r], o[r], nrm[r]);
@@ -464,39 +482,42 @@ __global__ void __launch_bounds__(MB_THREADS) k_mblock(const float* __restrict__
     }
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 32) {
+    // sigma_r and the column sum of component r for r = lane, lane + 32
+    double sg[2] = {0.0, 0.0}, cs[2] = {0.0, 0.0};
     double smax = 0.0;
-    double sg[RB];
-    for (int r = 0; r < RB; ++r) {
-      double s = 0.0;
-      for (int w = 0; w < MB_THREADS / 32; ++w) s += red[w][r];
-      sg[r] = sqrt(s);
-      if (r < R) smax = fmax(smax, sg[r]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + 32 * h;
+      if (r < RB) {
+        for (int w = 0; w < MB_THREADS / 32; ++w) {
+          sg[h] += red[w][r];
+          cs[h] += red2[w][r];
+        }
+        sg[h] = sqrt(sg[h]);
+        if (r < R) smax = fmax(smax, sg[h]);
+      }
     }
+    smax = warp_max_d(smax);
     int rk = 0;
-    for (int r = 0; r < RB; ++r) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + 32 * h;
       // sign rule: the right singular vector (column of C_k) has a non-negative sum
-      double cs = 0.0;
-      for (int w = 0; w < MB_THREADS / 32; ++w) cs += red2[w][r];
-      const bool kp = r < R && r < ell && sg[r] > (double)tau * smax && smax > 0.0;
-      keep[r] = kp ? (cs < 0.0 ? -1.f : 1.f) : 0.f;
-      if (r < R) Bk[(int64_t)k * R + r] = kp ? (float)sg[r] : 0.f;
+      const bool kp = r < R && r < ell && sg[h] > (double)tau * smax && smax > 0.0;
+      if (r < RB) keep[r] = kp ? (cs[h] < 0.0 ? -1.f : 1.f) : 0.f;
+      if (r < R) Bk[(int64_t)k * R + r] = kp ? (float)sg[h] : 0.f;
       rk += kp;
     }
-    if (rank) rank[k] = rk;
+    rk = __reduce_add_sync(0xffffffffu, rk);
+    if (tid == 0 && rank) rank[k] = rk;
   }
   __syncthreads();
   for (int e = tid; e < LP * R; e += MB_THREADS) t[e] *= keep[e % R];
   float* mk = Mblk + (int64_t)k * J * R;
   for (int j = tid; j < J; j += MB_THREADS) {
     float o[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) o[r] = 0.f;
-    for (int c = 0; c < ell; ++c) {
-      const float b = b1[(int64_t)c * Jp + j];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) o[r] = fmaf(b, ts[c * RB + r], o[r]);
-    }
+    mblock_col<RB>(b1, Jp, j, ell, ts, o);
 #pragma unroll
     for (int r = 0; r < RB; ++r)
       if (r < R) mk[(int64_t)j * R + r] = o[r] * keep[r];
@@ -704,26 +725,44 @@ __global__ void k_sum_splits(const double* __restrict__ Gpart, int nsplit, int K
   }
 }
 
+template <int NP>
+static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
+                    cudaStream_t s) {
+  k_gram_dd<NP><<<dim3(K, nsplit), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, G, nsplit);
+}
+
+static void gram_dispatch(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
+                          cudaStream_t s) {
+  const int np = (ell * (ell + 1) / 2 + GR_THREADS - 1) / GR_THREADS;
+  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, s);
+}
+
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
                     int nsplit, cudaStream_t s) {
   if (nsplit <= 1 || !Gpart) {
-    k_gram_dd<<<dim3(K, 1), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, G, 1);
+    gram_dispatch(Y, LP, d_off, K, ell, G, 1, s);
     return;
   }
-  k_gram_dd<<<dim3(K, nsplit), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, Gpart, nsplit);
+  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, s);
   const int n = LP * LP;
   k_sum_splits<<<(K * n + 255) / 256, 256, 0, s>>>(Gpart, nsplit, K, n, G);
 }
 
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
-                      cudaStream_t s) {
-  const int smem = 2 * ell * ell * (int)sizeof(double);
+                      bool fp64, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_chol_drop, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8);
+    cudaFuncSetAttribute(k_chol_drop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 8);
     attr = true;
   }
-  k_chol_drop<<<K, 32, smem, s>>>(G, ell, LP, tau, Minv, rank, status);
+  if (fp64)
+    k_chol_drop<double><<<K, 32, 2 * ell * ell * sizeof(double), s>>>(G, ell, LP, tau, Minv, rank, status);
+  else
+    k_chol_drop<float><<<K, 32, 2 * ell * ell * sizeof(float), s>>>(G, ell, LP, tau, Minv, rank, status);
 }
 
 void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s) {
@@ -752,7 +791,15 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
 
 void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
                    int* rank, float tau, cudaStream_t s) {
-  DP2_LP_SWITCH(round_up(R, 8), (k_mblock<L><<<K, MB_THREADS, 0, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau)));
+#define DP2_MB(RB) k_mblock<RB><<<K, MB_THREADS, 0, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau)
+  switch (R) {
+    case 10: DP2_MB(10); return;
+    case 20: DP2_MB(20); return;
+    case 30: DP2_MB(30); return;
+    default: break;
+  }
+  DP2_LP_SWITCH(round_up(R, 8), DP2_MB(L));
+#undef DP2_MB
 }
 
 void launch_seg_product(const float* In, int ldin, int nin, const float* T, int64_t tstride, int nout, float* Out,
