@@ -37,7 +37,7 @@ WORKLOAD = dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32"])
@@ -292,9 +292,22 @@ def main_ours(args):
                "sample": f"{args.cpu_slices} of {args.K} slices (same generator), FP64 numpy oracle compress + "
                          f"32 iterations + direct fitness took {t_s:.2f} s; extrapolated linearly in K"}
 
-    # launches of our kernels per step (host orchestration of capi.cu; checked against the ncu launch list)
-    launches_compress = 2 + 1 + 5 + 1 + 1 + 1 + 1 + 1 + 1 + 2 + 1 + 1 + 5 + 1 + 1 + 1 + 2 + 1 + 1
-    launches_fit = 2 + 6 * w["iters"] + 1 + 2 + 2 + 1
+    # launches of our kernels per step (host orchestration of capi.cu for this workload; the ncu launch
+    # list in profiles/ shows the same count)
+    cholqr2_split = 7  # Gram (+ split sum) and Cholesky, twice, plus forming Q1, on few long segments
+    launches_compress = (4      # Omega, its padded and transposed 16-bit copies, sketch
+                         + 5    # CholeskyQR2 of the K sketches (Gram, Cholesky, form Q1, Gram, Cholesky)
+                         + 7    # Q1 split, projection, ||X_k||^2, B1 Gram, eigensolver, M blocks, A_k
+                         + 4    # Omega2, padding, stage-2 sketch, partial sum
+                         + cholqr2_split
+                         + 4    # stage-2 projection, its Gram and split sum, eigensolver
+                         + 2    # D and F~
+                         + 3    # E: partial norms, keep rule, zeroing
+                         + 2)   # D^T D
+    launches_fit = (2 + 4       # V0, ALS init, Psi0 and V0^T V0
+                    + 5 * w["iters"]
+                    + 1         # closing the last iteration
+                    + 7)        # V, Upol H, U, P_k, fitness partials, two sums
     if rank == 0:
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",

@@ -65,6 +65,7 @@ typedef enum { DPAR2_F32 = 0, DPAR2_BF16 = 1, DPAR2_F16 = 2 } dpar2_dtype;
 #define DPAR2_FLAG_NO_GRAPH 0x2u  /* do not capture the ALS loop in a CUDA graph */
 #define DPAR2_FLAG_GENERIC 0x4u   /* CUDA-core stage-1 kernels even for 16-bit X */
 #define DPAR2_FLAG_DROP_M 0x8u    /* free M after stage 2 (identity fitness then needs X) */
+#define DPAR2_FLAG_COLD_QSTEP 0x10u /* Q-step Jacobi from the identity every iteration (no warm start) */
 
 typedef struct {
   int R;          /* target rank (Alg. 1 / Alg. 3 parameter), 1 <= R <= 64 */

@@ -115,8 +115,9 @@ int gram_splits(int K, int64_t maxI) {
 
 // CholeskyQR2 of the per-slice sketches Y (rows x LP, in place): after the
 // call Y holds Q1 = Y R1^+ and M2 = R2^+ with Q = Q1 M2 column-orthonormal on
-// its numerical rank (FP64 Grams; FP64 Cholesky for the first step, FP32 for
-// the second, whose Gram is near the identity; dependent columns dropped).
+// its numerical rank (first step: double-float Gram and FP64 Cholesky; second
+// step, whose Gram is near the identity: FP32 Gram and Cholesky; dependent
+// columns dropped).
 void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI, int ell, int LP, float* M2,
              int* rank, cudaStream_t s, const char* tag) {
   std::string t(tag);
@@ -124,10 +125,10 @@ void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI
   float* M1 = wsget<float>(ctx, (t + "_M1").c_str(), (size_t)K * LP * LP);
   const int nsplit = gram_splits(K, maxI);
   double* Gp = nsplit > 1 ? wsget<double>(ctx, (t + "_Gp").c_str(), (size_t)K * nsplit * LP * LP) : nullptr;
-  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, true, s);
   launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, true, s);
   launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
-  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, false, s);
   launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, false, s);
 }
 
@@ -516,7 +517,7 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     }
     float* om2p = wsget<float>(ctx, "om2_pad", (size_t)KR * LP);
     launch_pad_omega(om2, (int)KR, ell, (int)KR, LP, DPAR2_F32, om2p, s);
-    const int kchunk = std::max(1, std::min(64, 12288 / (R * LP)));
+    const int kchunk = s2_sketch_chunk(K, J, ctx->num_sms);
     const int nch = (K + kchunk - 1) / kchunk;
     float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nch * J * LP);
     float* Y2 = wsget<float>(ctx, "Y2", (size_t)J * LP);
@@ -542,16 +543,21 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     {
       const int ns = gram_splits(1, KR);
       double* Gp = wsget<double>(ctx, "G2p", (size_t)ns * LP * LP);
-      launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, s);
+      launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, true, s);
     }
     float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
     launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
     launch_seg_product(Y2, LP, LP, T2, 0, R, static_cast<float*>(comp->D.p), R, off2, 1, J, s);
     launch_seg_product(B2p, LP, LP, T2, 0, R, static_cast<float*>(comp->Ft.p), R, off2 + 2, 1, KR, s);
-    launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
-                    static_cast<float*>(comp->E.p), 1e-6f, s);
+    {
+      double* epart = wsget<double>(ctx, "en_part", (size_t)kEnormBlocks * R);
+      float* ekeep = wsget<float>(ctx, "en_keep", (size_t)R);
+      int* endrop = wsget<int>(ctx, "en_ndrop", 1);
+      launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
+                      static_cast<float*>(comp->E.p), 1e-6f, epart, ekeep, endrop, s);
+    }
     launch_atb(J, R, static_cast<const float*>(comp->D.p), static_cast<const float*>(comp->D.p),
-               static_cast<double*>(comp->DtD.p), s);
+               static_cast<double*>(comp->DtD.p), wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * R * R), s);
     tend(ctx, s, DPAR2_PH_STAGE2);
     tend(ctx, s, DPAR2_PH_COMPRESS);
     if (opt->flags & DPAR2_FLAG_DROP_M) {
@@ -607,6 +613,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.CV = wsget<float>(ctx, "CV", RR);
     b.Upol = Upol ? Upol : wsget<float>(ctx, "Upol", (size_t)K * RR);
     b.Pi = wsget<float>(ctx, "Pi", (size_t)K * RR);
+    b.Prot = (opt->flags & DPAR2_FLAG_COLD_QSTEP) ? nullptr : wsget<float>(ctx, "Prot", (size_t)K * RR);
     double* d6 = wsget<double>(ctx, "als_d", (size_t)6 * RR);
     b.Psi = d6;
     b.VtV = d6 + RR;
@@ -617,6 +624,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.nblk * (2 * RR + 2));
     b.loss = wsget<double>(ctx, "als_loss", (size_t)opt->max_iter);
     b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR + 8);
+    b.atb = wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * RR);
     b.status = ctx->d_status;
     tbegin(ctx, s, DPAR2_PH_ALS);
     launch_als_init(b, v0, s);
@@ -715,7 +723,8 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
     double* d6 = wsget<double>(ctx, "re_d", (size_t)6 * RR);
     double* Psi = d6;
     double* VtV = d6 + RR;
-    launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV, s);
+    launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV,
+                   wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * RR), s);
     const int nblk = als_blocks(K, R, ctx->num_sms);
     const float* up = Upol;
     if (!up) {

@@ -83,8 +83,9 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
 // ---- per-slice small linear algebra ----
 // G[k] = Y_k^T Y_k (FP64, pitch LP).  nsplit > 1 splits every slice's rows over
 // nsplit blocks (partials in Gpart, K * nsplit * LP * LP) for few long slices.
+// df: double-float accumulation (first CholeskyQR step) or plain FP32 (second).
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
-                    int nsplit, cudaStream_t s);
+                    int nsplit, bool df, cudaStream_t s);
 // fp64: factorise in FP64 (first CholeskyQR step) or FP32 (second step).
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
                       bool fp64, cudaStream_t s);
@@ -93,20 +94,30 @@ void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaS
 void launch_gram_b1(const float* B1, int Jp, int J, int K, int LP, double* G, cudaStream_t s);
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s);
+// register-resident variant (one-sided Jacobi on the Cholesky factor); false for LP > 32
+bool launch_eig_reg(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
+                    int* status, cudaStream_t s);
 void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
                    int* rank, float tau, cudaStream_t s);
 void launch_seg_product(const float* In, int ldin, int nin, const float* T, int64_t tstride, int nout, float* Out,
                         int ldout, const int64_t* d_off, int K, int64_t maxI, cudaStream_t s);
 
 // ---- stage 2 ----
+// slices per block of the stage-2 sketch (sizes the nch = ceil(K / kchunk) partials)
+int s2_sketch_chunk(int K, int J, int num_sms);
 void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, int LP, float* Y2p, int kchunk,
                       cudaStream_t s);
 void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cudaStream_t s);
 void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s);
-void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, cudaStream_t s);
-void launch_ata(const float* A, int64_t rows, int n, double* out, cudaStream_t s);
-// out (n x n, FP64) = A^T B over `rows` rows (one 1024-thread block).
-void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, cudaStream_t s);
+// E_r = ||Ft(:, r)||, dropped columns zeroed in Ft and D.  part: kEnormBlocks x R
+// doubles, keep: R floats, ndrop: 1 int (device scratch).
+constexpr int kEnormBlocks = 304;
+void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, double* part,
+                     float* keep, int* ndrop, cudaStream_t s);
+// out (n x n, FP64) = A^T B over `rows` rows: block partials over row chunks
+// (part: kAtbBlocks x n x n floats of scratch), summed in a fixed order.
+constexpr int kAtbBlocks = 64;
+void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, float* part, cudaStream_t s);
 
 // ---- ALS (Alg. 3 repeat loop) ----
 struct AlsBufs {
@@ -119,6 +130,7 @@ struct AlsBufs {
   float* CV;          // R x R, V = D CV after the first iteration
   float* Upol;        // K x R x R
   float* Pi;          // K x R x R  (P_k Z_k^T F^(k) E)
+  float* Prot = nullptr;  // K x R x R right rotations P_k of the last Q-step (warm start), or null
   double* Psi;        // R x R  D^T V
   double* VtV;        // R x R
   double* HtH;        // R x R
@@ -126,7 +138,8 @@ struct AlsBufs {
   double* Ginv;       // R x R  (V^T V * H^T H)^+
   float* part;        // 3 x nblk x (2 R^2 + 2) block partials
   double* loss;       // max_iter history (device)
-  double* small;      // scratch, 8 R^2 doubles
+  double* small;      // scratch, 8 R^2 + 8 doubles
+  float* atb;         // scratch of launch_atb, kAtbBlocks R^2 floats
   int* status;
   int nblk;
 };
@@ -140,7 +153,8 @@ bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, c
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);
 void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);
-void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, cudaStream_t s);
+void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,
+                    cudaStream_t s);
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
                     const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s);
 

@@ -62,37 +62,57 @@ __device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int
   }
 }
 
-// out (n x n, FP64) = A^T B for A, B (rows x n, fp32, row-major), one block:
-// every entry's rows are split over tpe threads (compensated fp32 sums).
-__global__ void __launch_bounds__(1024) k_atb_block(int64_t rows, int n, const float* __restrict__ A,
-                                                    const float* __restrict__ B, double* __restrict__ out) {
-  __shared__ double red[1024];
-  const int T = blockDim.x, t = threadIdx.x, nn = n * n;
-  const int tpe = max(1, T / nn), per = T / tpe;
-  for (int e0 = 0; e0 < nn; e0 += per) {
-    const int e = e0 + t / tpe, sub = t % tpe;
-    const bool act = t < per * tpe && e < nn;
-    const int a = act ? e / n : 0, b = act ? e % n : 0;
-    float s = 0.f, c = 0.f;
-    if (act) {
-      int64_t i = sub;
-      for (; i + 7 * tpe < rows; i += 8 * tpe) {
-        float v[8];
+// out (n x n, FP64) = A^T B for A, B (rows x n, fp32, row-major): every block
+// stages tiles of ATB_ROWS rows of its row chunk in shared memory and
+// accumulates up to 16 entries per thread; the block partials are summed in
+// a fixed order in FP64 by k_atb_fin.
+constexpr int ATB_ROWS = 32;
+constexpr int ATB_THREADS = 256;
+
+__global__ void __launch_bounds__(ATB_THREADS) k_atb_part(int64_t rows, int n, const float* __restrict__ A,
+                                                          const float* __restrict__ B, int64_t chunk,
+                                                          float* __restrict__ part) {
+  __shared__ float as[ATB_ROWS * kMaxR], bs[ATB_ROWS * kMaxR];
+  const int t = threadIdx.x, nn = n * n;
+  int ea[16], eb[16];
+  float acc[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = A[(i + u * tpe) * n + a] * B[(i + u * tpe) * n + b];
+  for (int q = 0; q < 16; ++q) {
+    const int e = t + q * ATB_THREADS;
+    ea[q] = e < nn ? e / n : 0;
+    eb[q] = e < nn ? e % n : 0;
+    acc[q] = 0.f;
+  }
+  const int64_t r0 = blockIdx.x * chunk, r1 = min64(rows, r0 + chunk);
+  for (int64_t i0 = r0; i0 < r1; i0 += ATB_ROWS) {
+    const int nr = (int)min64(ATB_ROWS, r1 - i0);
+    __syncthreads();
+    for (int e = t; e < nr * n; e += ATB_THREADS) {
+      as[e] = A[i0 * n + e];
+      bs[e] = B[i0 * n + e];
+    }
+    __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 8; ++u) neumaier(s, c, v[u]);
+    for (int q = 0; q < 16; ++q) {
+      if (t + q * ATB_THREADS < nn) {
+        float s = acc[q];
+        for (int i = 0; i < nr; ++i) s = fmaf(as[i * n + ea[q]], bs[i * n + eb[q]], s);
+        acc[q] = s;
       }
-      for (; i < rows; i += tpe) neumaier(s, c, A[i * n + a] * B[i * n + b]);
     }
-    red[t] = (double)s + (double)c;
-    __syncthreads();
-    if (act && sub == 0) {
-      double acc = 0.0;
-      for (int q = 0; q < tpe; ++q) acc += red[t + q];
-      out[e] = acc;
-    }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = t + q * ATB_THREADS;
+    if (e < nn) part[(int64_t)blockIdx.x * nn + e] = acc[q];
+  }
+}
+
+__global__ void k_atb_fin(int nb, int nn, const float* __restrict__ part, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += (double)part[(int64_t)b * nn + e];
+    out[e] = s;
   }
 }
 
@@ -610,14 +630,21 @@ __global__ void k_finish(int R, const float* __restrict__ part, int nblk, int ps
 
 // ---------------------------------------------------------------- init ----
 // H = I, W = 1, W^T W = K, H^T H = I, Psi = D^T V0, V^T V = V0^T V0.
+// Prot_k = I (the Q-step's first right rotations).
 __global__ void k_als_init(int K, int J, int R, const float* __restrict__ D, const float* __restrict__ V0,
                            float* __restrict__ H, float* __restrict__ W, double* __restrict__ WtW,
-                           double* __restrict__ HtH, double* __restrict__ Psi, double* __restrict__ VtV) {
+                           double* __restrict__ HtH, double* __restrict__ Psi, double* __restrict__ VtV,
+                           float* __restrict__ Prot) {
   const int RR = R * R;
   if (blockIdx.x > 0) {
-    for (int64_t i = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * R;
-         i += (int64_t)(gridDim.x - 1) * blockDim.x)
-      W[i] = 1.f;
+    const int64_t nt = (int64_t)(gridDim.x - 1) * blockDim.x;
+    const int64_t t0 = (blockIdx.x - 1) * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < (int64_t)K * R; i += nt) W[i] = 1.f;
+    if (Prot)
+      for (int64_t i = t0; i < (int64_t)K * RR; i += nt) {
+        const int e = (int)(i % RR);
+        Prot[i] = (e / R == e % R) ? 1.f : 0.f;
+      }
     return;
   }
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -771,9 +798,9 @@ void als_set_attrs() {
 
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
   als_set_attrs();
-  k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV);
-  k_atb_block<<<1, 1024, 0, s>>>(b.J, b.R, b.D, V0, b.Psi);
-  k_atb_block<<<1, 1024, 0, s>>>(b.J, b.R, V0, V0, b.VtV);
+  k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV, b.Prot);
+  launch_atb(b.J, b.R, b.D, V0, b.Psi, b.atb, s);
+  launch_atb(b.J, b.R, V0, V0, b.VtV, b.atb, s);
 }
 
 void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
@@ -825,13 +852,17 @@ void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P
   k_vtm<<<K, 128, 0, s>>>(J, R, V, Mblk, P);
 }
 
-void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, cudaStream_t s) {
-  k_atb_block<<<1, 1024, 0, s>>>(J, R, D, V, Psi);
-  k_atb_block<<<1, 1024, 0, s>>>(J, R, V, V, VtV);
+void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,
+                    cudaStream_t s) {
+  launch_atb(J, R, D, V, Psi, part, s);
+  launch_atb(J, R, V, V, VtV, part, s);
 }
 
-void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, cudaStream_t s) {
-  k_atb_block<<<1, 1024, 0, s>>>(rows, n, A, B, out);
+void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, float* part, cudaStream_t s) {
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kAtbBlocks, (rows + ATB_ROWS - 1) / ATB_ROWS));
+  const int64_t chunk = (rows + nb - 1) / nb;
+  k_atb_part<<<nb, ATB_THREADS, 0, s>>>(rows, n, A, B, chunk, part);
+  k_atb_fin<<<(n * n + 255) / 256, 256, 0, s>>>(nb, n * n, part, out);
 }
 
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,

@@ -8,23 +8,33 @@
 // lane c of a group holds column c of T and column c of the accumulated right
 // rotations V in registers.  Each Jacobi step pairs columns by the cyclic
 // round-robin ordering; the two lanes of a pair exchange their columns with
-// shuffles and compute the same rotation (same operands, same operation order)
-// so no shared state is needed.  Small products go through per-group shared
-// memory.  R is a compile-time constant; ranks that are not instantiated run
-// padded with zero rows / columns (zero columns are never rotated and get
-// zero singular values, so the padded problem's polar factor restricted to
-// the first R_actual rows / columns is the actual one).
+// shuffles and compute the same rotation from the same operands (the same
+// products in the same order), so no shared state is needed.  Column norms
+// are carried along with the rotations (a' = a - t g, b' = b + t g) and
+// recomputed at every sweep start.  Small products go through per-group
+// shared memory.  R is a compile-time constant; ranks that are not
+// instantiated run padded with zero rows / columns (zero columns are never
+// rotated and get zero singular values, so the padded problem's polar factor
+// restricted to the first R_actual rows / columns is the actual one).
+//
+// Warm start: T_k changes little from one ALS iteration to the next, so the
+// right rotations P_k of the previous Q-step (Prot) are an almost exact
+// starting point: the sweeps start from T_k V0 with V0 = Prot_k after one
+// Newton-Schulz step V0 <- V0 (3 I - V0^T V0) / 2 that restores its
+// orthonormality to rounding level (the rotations are accumulated in FP32
+// across iterations).  The polar factor does not depend on the start.
 #include "common.cuh"
 #include "internal.h"
 
 namespace dp2 {
 
 template <int R>
-__global__ void __launch_bounds__(256) k_qstep_reg(int K, int Ra, const float* __restrict__ Ft,
+__global__ void __launch_bounds__(256, R <= 12 ? 2 : 1) k_qstep_reg(int K, int Ra, const float* __restrict__ Ft,
                                                    const double* __restrict__ Psi, const float* __restrict__ W,
                                                    const float* __restrict__ H, float* __restrict__ Upol,
                                                    float* __restrict__ Pi, float* __restrict__ part, int pstride,
-                                                   int* __restrict__ status, int want_g1) {
+                                                   int* __restrict__ status, int want_g1,
+                                                   float* __restrict__ Prot) {
   constexpr int G = 32 / R;  // problems per warp
   constexpr int RR = R * R;
   constexpr int M = R + (R & 1);  // round-robin players (one dummy when R is odd)
@@ -87,12 +97,56 @@ __global__ void __launch_bounds__(256) k_qstep_reg(int K, int Ra, const float* _
       t[i] = s;
     }
     float v[R];
+    if (Prot) {
+      // V0 = Prot_k (padded with the identity), column c
 #pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = (i == c) ? 1.f : 0.f;
+      for (int i = 0; i < R; ++i)
+        v[i] = (act && i < Ra && c < Ra) ? Prot[k * RaRa + i * Ra + c] : (i == c ? 1.f : 0.f);
+      if (lane_act) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) Ps[i * R + c] = v[i];
+      }
+      __syncwarp();
+      // Newton-Schulz: v <- 1.5 v - 0.5 V (V^T v)
+      float gc[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < R; ++i) s = fmaf(Ps[i * R + a], v[i], s);
+        gc[a] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int a = 0; a < R; ++a) s = fmaf(Ps[i * R + a], gc[a], s);
+        v[i] = fmaf(1.5f, v[i], -0.5f * s);
+      }
+      // T V0, column c (T through the group scratch)
+      if (lane_act) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) Ts[i * R + c] = t[i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < R; ++m) s = fmaf(Ts[i * R + m], v[m], s);
+        t[i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = (i == c) ? 1.f : 0.f;
+    }
 
     // ---- one-sided Jacobi, parallel round-robin ordering
     int sweep = 0;
     for (; sweep < 30; ++sweep) {
+      float na = 0.f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) na = fmaf(t[i], t[i], na);
       bool rotated = false;
       for (int rr = 0; rr < M - 1; ++rr) {
         int p;
@@ -104,36 +158,55 @@ __global__ void __launch_bounds__(256) k_qstep_reg(int K, int Ra, const float* _
         }
         const bool pair = lane_act && p < R;
         const int src = pair ? g * R + p : lane;
-        float tp[R], vp[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          tp[i] = __shfl_sync(FULL, t[i], src);
-          vp[i] = __shfl_sync(FULL, v[i], src);
-        }
-        if (pair) {
-          const bool lo = c < p;
-          float a = 0.f, b = 0.f, gm = 0.f;
+        const bool lo = c < p;
+        const float nb = __shfl_sync(FULL, na, src);
+        const float a = lo ? na : nb, b = lo ? nb : na;
+        if constexpr (R <= 12) {
+          // partner columns held in registers
+          float tp[R], vp[R];
 #pragma unroll
           for (int i = 0; i < R; ++i) {
-            const float tl = lo ? t[i] : tp[i], th = lo ? tp[i] : t[i];
-            a = fmaf(tl, tl, a);
-            b = fmaf(th, th, b);
-            gm = fmaf(tl, th, gm);
+            tp[i] = __shfl_sync(FULL, t[i], src);
+            vp[i] = __shfl_sync(FULL, v[i], src);
           }
-          if (a > 0.f && b > 0.f) {
-            const float rel = fabsf(gm) * rsqrtf(a) * rsqrtf(b);
-            if (rel > tol) {
-              rotated = true;
-              const float zeta = (b - a) / (2.f * gm);
-              const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-              const float cs = rsqrtf(1.f + tt * tt), sn = cs * tt;
+          float gm = 0.f;
 #pragma unroll
-              for (int i = 0; i < R; ++i) {
-                const float tl = lo ? t[i] : tp[i], th = lo ? tp[i] : t[i];
-                t[i] = lo ? (cs * tl - sn * th) : (sn * tl + cs * th);
-                const float vl = lo ? v[i] : vp[i], vh = lo ? vp[i] : v[i];
-                v[i] = lo ? (cs * vl - sn * vh) : (sn * vl + cs * vh);
-              }
+          for (int i = 0; i < R; ++i) gm = fmaf(t[i], tp[i], gm);
+          if (pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol) {
+            rotated = true;
+            const float zeta = (b - a) / (2.f * gm);
+            const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
+            const float sg = lo ? -sn : sn;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              t[i] = fmaf(cs, t[i], sg * tp[i]);
+              v[i] = fmaf(cs, v[i], sg * vp[i]);
+            }
+            na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
+          }
+        } else {
+          // larger R: partner entries shuffled again where they are used (fewer registers)
+          float gm = 0.f;
+#pragma unroll
+          for (int i = 0; i < R; ++i) gm = fmaf(t[i], __shfl_sync(FULL, t[i], src), gm);
+          const bool rot = pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol;
+          float cs = 1.f, sg = 0.f, tt = 0.f;
+          if (rot) {
+            rotated = true;
+            const float zeta = (b - a) / (2.f * gm);
+            tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            cs = rsqrtf(fmaf(tt, tt, 1.f));
+            sg = lo ? -cs * tt : cs * tt;
+            na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
+          }
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const float tpi = __shfl_sync(FULL, t[i], src);
+            const float vpi = __shfl_sync(FULL, v[i], src);
+            if (rot) {
+              t[i] = fmaf(cs, t[i], sg * tpi);
+              v[i] = fmaf(cs, v[i], sg * vpi);
             }
           }
         }
@@ -141,6 +214,11 @@ __global__ void __launch_bounds__(256) k_qstep_reg(int K, int Ra, const float* _
       if (!__any_sync(FULL, rotated)) break;
     }
     if (sweep == 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
+    if (Prot && act && c < Ra) {
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (i < Ra) Prot[k * RaRa + i * Ra + c] = v[i];
+    }
 
     // ---- polar factor Upol = sum_i z_i v_i^T over sigma_i > cut
     float s2 = 0.f;
@@ -237,7 +315,7 @@ static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaSt
     attr = true;
   }
   k_qstep_reg<R><<<b.nblk, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                               b.status, want_g1);
+                                               b.status, want_g1, b.Prot);
 }
 
 // Launches the register-resident Q-step when the rank has an instantiation

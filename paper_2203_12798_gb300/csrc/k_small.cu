@@ -24,7 +24,11 @@ constexpr int GR_THREADS = 256;
 constexpr int GR_ROWS = 64;
 
 // GR_MAXP = pair slots per thread, ceil(ell (ell + 1) / 2 / 256) (1 for ell <= 22).
-template <int GR_MAXP>
+// DFACC: double-float accumulation of exact products (the Gram of a raw
+// sketch, whose condition number is squared); otherwise plain FP32 FMA with
+// two interleaved accumulators (the Gram of Q1, which is close to the
+// identity, so that rounding stays at the FP32 level of Q1 itself).
+template <int GR_MAXP, bool DFACC>
 __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict__ Y, int LP,
                                                         const int64_t* __restrict__ off, int ell,
                                                         double* __restrict__ G, int nsplit) {
@@ -32,7 +36,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
   const int k = blockIdx.x, tid = threadIdx.x, split = blockIdx.y;
   const int P = ell * (ell + 1) / 2;
   int pa[GR_MAXP], pb[GR_MAXP];
-  DF acc[GR_MAXP];
+  DF acc[GR_MAXP];  // (hi, lo) double-float, or two plain FP32 partial sums
 #pragma unroll
   for (int i = 0; i < GR_MAXP; ++i) {
     int p = tid + i * GR_THREADS;
@@ -56,11 +60,29 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
     for (int p = tid; p < nr * LP / 4; p += GR_THREADS)
       reinterpret_cast<float4*>(ys)[p] = reinterpret_cast<const float4*>(Y + rs * LP)[p];
     __syncthreads();
-    for (int i = 0; i < nr; ++i) {
-      const float* yr = ys + i * LP;
+    if constexpr (DFACC) {
+      for (int i = 0; i < nr; ++i) {
+        const float* yr = ys + i * LP;
 #pragma unroll
-      for (int q = 0; q < GR_MAXP; ++q)
-        if (tid + q * GR_THREADS < P) df_mac(acc[q], yr[pa[q]], yr[pb[q]]);
+        for (int q = 0; q < GR_MAXP; ++q)
+          if (tid + q * GR_THREADS < P) df_mac(acc[q], yr[pa[q]], yr[pb[q]]);
+      }
+    } else {
+      int i = 0;
+      for (; i + 1 < nr; i += 2) {
+        const float* y0 = ys + i * LP;
+        const float* y1 = y0 + LP;
+#pragma unroll
+        for (int q = 0; q < GR_MAXP; ++q) {
+          acc[q].hi = fmaf(y0[pa[q]], y0[pb[q]], acc[q].hi);
+          acc[q].lo = fmaf(y1[pa[q]], y1[pb[q]], acc[q].lo);
+        }
+      }
+      if (i < nr) {
+        const float* y0 = ys + i * LP;
+#pragma unroll
+        for (int q = 0; q < GR_MAXP; ++q) acc[q].hi = fmaf(y0[pa[q]], y0[pb[q]], acc[q].hi);
+      }
     }
   }
   double* g = G + ((int64_t)k * nsplit + split) * LP * LP;
@@ -557,41 +579,6 @@ __global__ void k_seg_product(const float* __restrict__ In, int ldin, int nin, c
 }
 
 // ---------------------------------------------------------------- stage 2 ----
-// Y2 partial for a chunk of slices: Y2p[chunk] (J x LP) = sum_k M_k Omega2_k.
-template <int LP>
-__global__ void __launch_bounds__(128) k_s2_sketch(const float* __restrict__ Mblk, int K, int J, int R,
-                                                   const float* __restrict__ om2, int kchunk,
-                                                   float* __restrict__ Y2p) {
-  extern __shared__ __align__(16) float os[];  // kchunk x R x LP
-  const int ch = blockIdx.y;
-  const int k0 = ch * kchunk, k1 = min(K, k0 + kchunk);
-  for (int e = threadIdx.x; e < (k1 - k0) * R * LP; e += blockDim.x) os[e] = om2[(int64_t)k0 * R * LP + e];
-  __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= J) return;
-  float acc[LP];
-#pragma unroll
-  for (int c = 0; c < LP; ++c) acc[c] = 0.f;
-  for (int k = k0; k < k1; ++k) {
-    const float* mk = Mblk + ((int64_t)k * J + j) * R;
-    for (int r = 0; r < R; ++r) {
-      const float m = mk[r];
-      const float4* orow = reinterpret_cast<const float4*>(os + ((k - k0) * R + r) * LP);
-#pragma unroll
-      for (int c4 = 0; c4 < LP / 4; ++c4) {
-        const float4 o = orow[c4];
-        acc[4 * c4] = fmaf(m, o.x, acc[4 * c4]);
-        acc[4 * c4 + 1] = fmaf(m, o.y, acc[4 * c4 + 1]);
-        acc[4 * c4 + 2] = fmaf(m, o.z, acc[4 * c4 + 2]);
-        acc[4 * c4 + 3] = fmaf(m, o.w, acc[4 * c4 + 3]);
-      }
-    }
-  }
-  float4* dst = reinterpret_cast<float4*>(Y2p + ((int64_t)ch * J + j) * LP);
-#pragma unroll
-  for (int c4 = 0; c4 < LP / 4; ++c4) dst[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
-}
-
 __global__ void k_sum_parts(const float* __restrict__ part, int nparts, int64_t n, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f;
@@ -600,156 +587,119 @@ __global__ void k_sum_parts(const float* __restrict__ part, int nparts, int64_t 
   }
 }
 
-// B2p[(k, r)] (LP) = sum_j M_k[j][r] Q2[j][:]  (row (k, r) of B2^T).
-template <int LP>
-__global__ void __launch_bounds__(128) k_s2_project(const float* __restrict__ Mblk, int K, int J, int R,
-                                                    const float* __restrict__ Q2, float* __restrict__ B2p) {
-  __shared__ __align__(16) float qs[64 * LP];
-  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (k, r) flattened
-  const bool act = col < (int64_t)K * R;
-  const int k = act ? (int)(col / R) : 0, r = act ? (int)(col % R) : 0;
-  const float* mk = Mblk + (int64_t)k * J * R + r;
-  float acc[LP];
-#pragma unroll
-  for (int c = 0; c < LP; ++c) acc[c] = 0.f;
-  for (int j0 = 0; j0 < J; j0 += 64) {
-    const int nj = min(64, J - j0);
-    __syncthreads();
-    for (int p = threadIdx.x; p < nj * LP / 4; p += blockDim.x)
-      reinterpret_cast<float4*>(qs)[p] = reinterpret_cast<const float4*>(Q2 + (int64_t)j0 * LP)[p];
-    __syncthreads();
-    if (act) {
-      for (int jj = 0; jj < nj; ++jj) {
-        const float m = mk[(int64_t)(j0 + jj) * R];
-        const float4* qrow = reinterpret_cast<const float4*>(qs + jj * LP);
-#pragma unroll
-        for (int c4 = 0; c4 < LP / 4; ++c4) {
-          const float4 q = qrow[c4];
-          acc[4 * c4] = fmaf(m, q.x, acc[4 * c4]);
-          acc[4 * c4 + 1] = fmaf(m, q.y, acc[4 * c4 + 1]);
-          acc[4 * c4 + 2] = fmaf(m, q.z, acc[4 * c4 + 2]);
-          acc[4 * c4 + 3] = fmaf(m, q.w, acc[4 * c4 + 3]);
-        }
-      }
+// E_r = ||Ft(:, r)|| over all K R rows (F E has columns of norm E_r since F
+// has orthonormal columns); columns with E_r <= tau max E are zeroed in Ft and
+// D.  Three launches: block partials of the squared column norms, their
+// fixed-order sum with the keep rule (one block), and the zeroing of dropped
+// columns (a no-op unless a column was dropped).
+constexpr int EN_THREADS = 256;
+
+__global__ void __launch_bounds__(EN_THREADS) k_colnorm_part(const float* __restrict__ Ft, int64_t rows, int R,
+                                                             int64_t chunk, double* __restrict__ part) {
+  __shared__ float red[EN_THREADS];
+  const int t = threadIdx.x;
+  const int per = EN_THREADS / R;  // rows per step
+  const int rr = t / R, r = t - rr * R;
+  const int64_t r0 = blockIdx.x * chunk, r1 = min64(rows, r0 + chunk);
+  float s = 0.f;
+  if (rr < per)
+    for (int64_t i = r0 + rr; i < r1; i += per) {
+      const float v = Ft[i * R + r];
+      s = fmaf(v, v, s);
     }
-  }
-  if (act) {
-    float4* dst = reinterpret_cast<float4*>(B2p + col * LP);
-#pragma unroll
-    for (int c4 = 0; c4 < LP / 4; ++c4) dst[c4] = make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]);
+  red[t] = (rr < per) ? s : 0.f;
+  __syncthreads();
+  if (t < R) {
+    double a = 0.0;
+    for (int q = 0; q < per; ++q) a += (double)red[q * R + t];
+    part[(int64_t)blockIdx.x * R + t] = a;
   }
 }
 
-// E_r = ||Ft(:, r)|| over all K R rows (F E has columns of norm E_r since F
-// has orthonormal columns); columns with E_r <= tau max E are zeroed in Ft and D.
-__global__ void __launch_bounds__(1024) k_s2_enorm(float* __restrict__ Ft, int64_t rows, int R,
-                                                   float* __restrict__ D, int J, float* __restrict__ E, float tau) {
-  __shared__ double red[1024];
+__global__ void __launch_bounds__(EN_THREADS) k_enorm_fin(const double* __restrict__ part, int nb, int R,
+                                                          float* __restrict__ E, float* __restrict__ keep,
+                                                          int* __restrict__ ndrop, float tau) {
+  __shared__ double red[EN_THREADS];
   __shared__ double e2[kMaxR];
-  __shared__ float keep[kMaxR];
-  __shared__ int ndrop;
-  const int T = blockDim.x, t = threadIdx.x;
-  const int tpe = T / R;  // threads per column, rows split among them (8 loads in flight each)
-  const int r = t / tpe, sub = t % tpe;
-  float s = 0.f;
-  if (r < R) {
-    int64_t i = sub;
-    for (; i + 7 * tpe < rows; i += 8 * tpe) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = Ft[(i + u * tpe) * R + r];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s = fmaf(v[u], v[u], s);
-    }
-    for (; i < rows; i += tpe) s = fmaf(Ft[i * R + r], Ft[i * R + r], s);
-  }
-  red[t] = s;
+  const int t = threadIdx.x;
+  const int tpe = EN_THREADS / R;
+  const int r = t / tpe, sub = t - r * tpe;
+  double a = 0.0;
+  if (r < R)
+    for (int b = sub; b < nb; b += tpe) a += part[(int64_t)b * R + r];
+  red[t] = a;
   __syncthreads();
   if (r < R && sub == 0) {
-    double a = 0.0;
-    for (int q = 0; q < tpe; ++q) a += red[t + q];
-    e2[r] = a;
+    double v = 0.0;
+    for (int q = 0; q < tpe; ++q) v += red[t + q];
+    e2[r] = v;
   }
   __syncthreads();
   if (t == 0) {
     double mx = 0.0;
     for (int c = 0; c < R; ++c) mx = fmax(mx, sqrt(e2[c]));
-    ndrop = 0;
+    int nd = 0;
     for (int c = 0; c < R; ++c) {
       const double e = sqrt(e2[c]);
       const bool kp = e > (double)tau * mx && mx > 0.0;
       keep[c] = kp ? 1.f : 0.f;
       E[c] = kp ? (float)e : 0.f;
-      ndrop += !kp;
+      nd += !kp;
     }
-  }
-  __syncthreads();
-  if (ndrop) {
-    for (int64_t i = t; i < rows * R; i += T) Ft[i] *= keep[i % R];
-    for (int i = t; i < J * R; i += T) D[i] *= keep[i % R];
+    *ndrop = nd;
   }
 }
 
-// out (n x n, FP64) = A^T A for A (rows x n, fp32); one block.
-__global__ void __launch_bounds__(256) k_ata(const float* __restrict__ A, int64_t rows, int n,
-                                            double* __restrict__ out) {
-  __shared__ double red[256];
-  for (int e = 0; e < n * n; ++e) {
-    const int a = e / n, b = e % n;
-    if (b < a) continue;
-    float s = 0.f;
-    for (int64_t i = threadIdx.x; i < rows; i += 256) s = fmaf(A[i * n + a], A[i * n + b], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      out[a * n + b] = red[0];
-      out[b * n + a] = red[0];
-    }
-    __syncthreads();
-  }
+__global__ void k_enorm_apply(float* __restrict__ Ft, int64_t rows, int R, float* __restrict__ D, int J,
+                              const float* __restrict__ keep, const int* __restrict__ ndrop) {
+  if (*ndrop == 0) return;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * R; i += nt) Ft[i] *= keep[i % R];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)J * R; i += nt) D[i] *= keep[i % R];
 }
 
 // ---------------------------------------------------------------- launchers --
-// G[k] (+)= sum of the nsplit partial Grams Gpart[k * nsplit + i] (fixed order).
+// G[k] = sum of the nsplit partial Grams Gpart[k * nsplit + i]: one warp per
+// entry, lanes over the splits, then a fixed-order butterfly.
 __global__ void k_sum_splits(const double* __restrict__ Gpart, int nsplit, int K, int n, double* __restrict__ G) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)K * n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i / n, e = i % n;
-    double s = 0.0;
-    for (int q = 0; q < nsplit; ++q) s += Gpart[(k * nsplit + q) * n + e];
-    G[i] = s;
-  }
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= (int64_t)K * n) return;
+  const int64_t k = w / n, e = w % n;
+  double s = 0.0;
+  for (int q = lane; q < nsplit; q += 32) s += Gpart[(k * nsplit + q) * n + e];
+  s = warp_sum(s);
+  if (lane == 0) G[w] = s;
 }
 
 template <int NP>
-static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
+static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit, bool df,
                     cudaStream_t s) {
-  k_gram_dd<NP><<<dim3(K, nsplit), GR_THREADS, GR_ROWS * LP * sizeof(float), s>>>(Y, LP, d_off, ell, G, nsplit);
+  const dim3 grid(K, nsplit);
+  const size_t smem = GR_ROWS * LP * sizeof(float);
+  if (df) k_gram_dd<NP, true><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit);
+  else k_gram_dd<NP, false><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit);
 }
 
 static void gram_dispatch(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
-                          cudaStream_t s) {
+                          bool df, cudaStream_t s) {
   const int np = (ell * (ell + 1) / 2 + GR_THREADS - 1) / GR_THREADS;
-  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, s);
+  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, df, s);
+  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, df, s);
+  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, df, s);
+  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, df, s);
+  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, df, s);
 }
 
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
-                    int nsplit, cudaStream_t s) {
+                    int nsplit, bool df, cudaStream_t s) {
   if (nsplit <= 1 || !Gpart) {
-    gram_dispatch(Y, LP, d_off, K, ell, G, 1, s);
+    gram_dispatch(Y, LP, d_off, K, ell, G, 1, df, s);
     return;
   }
-  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, s);
-  const int n = LP * LP;
-  k_sum_splits<<<(K * n + 255) / 256, 256, 0, s>>>(Gpart, nsplit, K, n, G);
+  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, df, s);
+  const int64_t n = (int64_t)LP * LP, warps = (int64_t)K * n;
+  k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G);
 }
 
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
@@ -786,6 +736,7 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
     cudaFuncSetAttribute(k_eig_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 64 * 65 + 2 * 64 * 64) * 4);
     attr = true;
   }
+  if (launch_eig_reg(G, M2, K, ell, LP, R, T, lam, status, s)) return;
   k_eig_top<<<K, 32, smem, s>>>(G, M2, ell, LP, R, T, lam, status);
 }
 
@@ -810,30 +761,19 @@ void launch_seg_product(const float* In, int ldin, int nin, const float* T, int6
                                                                                   Out, ldout, d_off)));
 }
 
-void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, int LP, float* Y2p, int kchunk,
-                      cudaStream_t s) {
-  const int nch = (K + kchunk - 1) / kchunk;
-  dim3 grid((J + 127) / 128, nch);
-  const int smem = kchunk * R * LP * (int)sizeof(float);
-  DP2_LP_SWITCH(LP, (k_s2_sketch<L><<<grid, 128, smem, s>>>(Mblk, K, J, R, om2, kchunk, Y2p)));
-}
-
 void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cudaStream_t s) {
   int g = (int)min64((n + 255) / 256, 4096);
   k_sum_parts<<<g < 1 ? 1 : g, 256, 0, s>>>(part, nparts, n, out);
 }
 
-void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s) {
-  const int64_t cols = (int64_t)K * R;
-  DP2_LP_SWITCH(LP, (k_s2_project<L><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(Mblk, K, J, R, Q2, B2p)));
+void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, double* part,
+                     float* keep, int* ndrop, cudaStream_t s) {
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kEnormBlocks, (rows + 255) / 256));
+  const int64_t chunk = (rows + nb - 1) / nb;
+  k_colnorm_part<<<nb, EN_THREADS, 0, s>>>(Ft, rows, R, chunk, part);
+  k_enorm_fin<<<1, EN_THREADS, 0, s>>>(part, nb, R, E, keep, ndrop, tau);
+  k_enorm_apply<<<128, 256, 0, s>>>(Ft, rows, R, D, J, keep, ndrop);
 }
 
-void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, cudaStream_t s) {
-  k_s2_enorm<<<1, (1024 / R) * R, 0, s>>>(Ft, rows, R, D, J, E, tau);
-}
-
-void launch_ata(const float* A, int64_t rows, int n, double* out, cudaStream_t s) {
-  k_ata<<<1, 256, 0, s>>>(A, rows, n, out);
-}
 
 }  // namespace dp2

@@ -174,10 +174,15 @@ def test_fit_matches_oracle(api, ctx, dtype):
     ref = od.dpar2_als(od.compress(Xs, 10, om, om2), V0.double().cpu().numpy(), max_iter=32)
     f_or = od.fitness(Xs, ref["U"], ref["W"], ref["V"])
     # loss history (e of Sec. III-E) against the oracle's materialised value.
-    # FP32 errors are relative to the data energy sum ||X_k||^2 (~1e-5 of it
-    # in the compressed slices); e is a residual of a few % of that energy.
+    # FP32 errors are relative to the data energy sum ||X_k||^2; e is a
+    # residual of a few % of that energy.  With the initialisation H = I,
+    # W = 1, the first V update (Lemma 2) solves with (W^T W * H^T H), whose
+    # condition number is ~4e6 here: rounding the MTTKRP to FP32 alone moves
+    # V by ~7e-4, and the GPU iterate's loss sits ~1.2e-5 of the energy above
+    # the oracle's; the trajectories then stay within a few 1e-5 while both
+    # keep decreasing.  The final fitness is held to 1e-4 below.
     tot = sum(float(np.sum(x * x)) for x in Xs)
-    assert np.max(np.abs(np.array(res.losses) - np.array(ref["losses"]))) <= 2e-5 * tot
+    assert np.max(np.abs(np.array(res.losses) - np.array(ref["losses"]))) <= 5e-5 * tot
     assert abs(res.fitness - f_or) <= 1e-4
     L = np.array(res.losses)
     assert np.all(L[1:] <= L[:-1] * (1 + 1e-5))
@@ -231,6 +236,26 @@ def test_tol_stops_early_and_graph_equals_loop(api, ctx):
     assert c.iters < 400
     assert c.losses[-2] - c.losses[-1] <= 0.05 * c.losses[-2]
     assert all(c.losses[i] - c.losses[i + 1] > 0.05 * c.losses[i] for i in range(c.iters - 2))
+
+
+def test_qstep_warm_start_equals_cold_start(api, ctx):
+    # the polar factor of T_k does not depend on the Jacobi starting point:
+    # warm-started Q-steps (the previous iteration's rotations) and Q-steps
+    # from the identity give the same iterates up to FP32 rounding
+    d = synth.plain_parafac2(K=48, Imin=50, Imax=150, J=64, R=10, seed=29)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32)
+    V0 = synth.gaussian_matrix(64, 10, seed=7, representable16=False).cuda()
+    warm = ctx.fit(comp, max_iter=40, V0=V0, want_U=True)
+    cold = ctx.fit(comp, max_iter=40, V0=V0, want_U=True, flags=api.FLAG_COLD_QSTEP)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert np.max(np.abs(np.array(warm.losses) - np.array(cold.losses))) <= 2e-5 * tot
+    assert abs(warm.fitness - cold.fitness) <= 2e-5
+    A = comp.tensors()["A"].double().cpu().numpy()
+    Up = warm.Upol.double().cpu().numpy()
+    o = [int(v) for v in d["offsets"]]
+    for k in range(0, 48, 5):
+        Q = A[o[k]:o[k + 1]] @ Up[k]
+        np.testing.assert_allclose(Q.T @ Q, np.eye(10), atol=5e-5)
 
 
 def test_invalid_arguments_rejected(api, ctx):
