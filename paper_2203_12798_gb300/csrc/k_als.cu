@@ -219,23 +219,20 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
     __syncwarp();
     const int sw = warp_onesided_jacobi(Tm, Vm, R, ld, tol, 30);
     if (sw > 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
-    // sigma_i = ||T(:, i)||; Upol = sum_{sigma_i > tau sigma_max} T(:, i) V(:, i)^T / sigma_i
-    float smax = 0.f;
+    // sigma_i = ||T(:, i)||; Upol = sum_{sigma_i > 0} T(:, i) V(:, i)^T / sigma_i
+    // (the final columns are mutually orthogonal however small)
     for (int i = lane; i < R; i += 32) {
       float s = 0.f;
       for (int a = 0; a < R; ++a) s = fmaf(Tm[a * ld + i], Tm[a * ld + i], s);
       A1[i] = sqrtf(s);
-      smax = fmaxf(smax, A1[i]);
     }
-    smax = warp_max(smax);
     __syncwarp();
-    const float cut = smax * (float)R * 1.2e-7f;
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e % R;
       float s = 0.f;
       for (int i = 0; i < R; ++i) {
         const float sg = A1[i];
-        if (sg > cut) s = fmaf(Tm[a * ld + i] / sg, Vm[b * ld + i], s);
+        if (sg > 0.f) s = fmaf(Tm[a * ld + i] / sg, Vm[b * ld + i], s);
       }
       Up[e] = s;
     }

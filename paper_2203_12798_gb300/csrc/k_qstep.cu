@@ -220,15 +220,15 @@ __global__ void __launch_bounds__(256, R <= 12 ? 2 : 1) k_qstep_reg(int K, int R
         if (i < Ra) Prot[k * RaRa + i * Ra + c] = v[i];
     }
 
-    // ---- polar factor Upol = sum_i z_i v_i^T over sigma_i > cut
+    // ---- polar factor Upol = sum_i z_i v_i^T over sigma_i > 0.  The final
+    // columns are mutually orthogonal however small, so every nonzero one is
+    // kept (an FP32-level cut would drop directions of ill-conditioned T_k
+    // that an FP64 SVD resolves); only zero (padded) columns are left out.
     float s2 = 0.f;
 #pragma unroll
     for (int i = 0; i < R; ++i) s2 = fmaf(t[i], t[i], s2);
     const float sg = sqrtf(s2);
-    float smax = 0.f;
-#pragma unroll
-    for (int j = 0; j < R; ++j) smax = fmaxf(smax, __shfl_sync(FULL, sg, lane_act ? g * R + j : lane));
-    const float inv = (sg > smax * (float)Ra * 1.2e-7f && sg > 0.f) ? 1.f / sg : 0.f;
+    const float inv = sg > 0.f ? 1.f / sg : 0.f;
     __syncwarp();
     if (lane_act) {
 #pragma unroll

@@ -183,16 +183,16 @@ __global__ void k_reduce_rows_f64(const double* __restrict__ part, int K, int n,
 }
 
 // -------------------------------------------------------- Gram of B1 rows ----
-// G_k (LP x LP, FP64) = B1_k B1_k^T over columns j < J; B1_k is LP x Jp.
-// Threads own 4x4 tiles of the upper triangle; thread groups split the
-// columns.  The next 64-column chunk is loaded into registers while the
-// current one is consumed from shared memory.
+// G_k (LP x LP, FP64) = B1_k B1_k^T over columns j < J; B1_k is LP x Jp (rows
+// >= l zero).  Threads own 4x4 tiles of the upper triangle; thread groups
+// split the columns.  The next chunk of 128 (64 for l > 32) columns is loaded
+// into registers while the current one is consumed from shared memory.
 constexpr int GB_THREADS = 256;
-constexpr int GB_CJ = 64;
 
 template <int LP>
-__global__ void __launch_bounds__(GB_THREADS) k_gram_b1(const float* __restrict__ B1, int Jp, int J,
+__global__ void __launch_bounds__(GB_THREADS, 3) k_gram_b1(const float* __restrict__ B1, int Jp, int J, int ell,
                                                         double* __restrict__ G) {
+  constexpr int GB_CJ = LP <= 32 ? 128 : 64;  // columns per chunk (static shared memory <= 48 KB)
   constexpr int T = LP / 4;
   constexpr int NT = T * (T + 1) / 2;
   constexpr int NG = GB_THREADS / NT > 0 ? GB_THREADS / NT : 1;
@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(GB_THREADS) k_gram_b1(const float* __restrict_
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = tid + u * GB_THREADS;
-      const int c = e / GB_CJ, jj = e % GB_CJ;
-      pre[u] = (j0 + jj < J) ? __ldg(src + (int64_t)c * Jp + j0 + jj) : 0.f;
+      const int c = e / GB_CJ, jj = e % GB_CJ;  // rows c >= ell of B1 are zero and not read
+      pre[u] = (c < ell && j0 + jj < J) ? __ldg(src + (int64_t)c * Jp + j0 + jj) : 0.f;
     }
   };
   fetch(0);
@@ -445,9 +445,11 @@ __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, co
 // M_k (J x R) = B1_k^T T_k; sigma_r = ||M_k(:, r)|| (the stage-1 singular
 // values B_k); columns with sigma_r <= tau * max sigma are zeroed in M_k and
 // T_k (numerical rank rule).  Two passes over B1_k (norms and signs, then
-// M_k); the slices of the resident blocks (about 5 per SM) stay in L2 for the
+// M_k); a shared-memory reservation caps the resident blocks at three per SM
+// so that the slices being processed (~80 MB in all) stay in L2 for the
 // second pass.  Every thread keeps 8 rows of B1_k in flight.
-constexpr int MB_THREADS = 256;
+constexpr int MB_THREADS = 512;
+constexpr int MB_SMEM_CAP = 64 * 1024;  // dynamic shared memory requested per block (unused)
 
 template <int RB>
 __device__ inline void mblock_col(const float* __restrict__ b1, int Jp, int j, int ell, const float* ts, float* o) {
@@ -465,7 +467,7 @@ __device__ inline void mblock_col(const float* __restrict__ b1, int Jp, int j, i
 }
 
 template <int RB>
-__global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 4 : 2) k_mblock(const float* __restrict__ B1, int Jp, int J, int ell,
+__global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 2 : 1) k_mblock(const float* __restrict__ B1, int Jp, int J, int ell,
                                                        int LP, int R, float* __restrict__ T,
                                                        float* __restrict__ Bk, float* __restrict__ Mblk,
                                                        int* __restrict__ rank, float tau) {
@@ -724,8 +726,8 @@ void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaS
   k_reduce_rows_f64<<<(K + 127) / 128, 128, 0, s>>>(part, K, n, out);
 }
 
-void launch_gram_b1(const float* B1, int Jp, int J, int K, int LP, double* G, cudaStream_t s) {
-  DP2_LP_SWITCH(LP, (k_gram_b1<L><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, G)));
+void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, double* G, cudaStream_t s) {
+  DP2_LP_SWITCH(LP, (k_gram_b1<L><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G)));
 }
 
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
@@ -742,7 +744,11 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
 
 void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
                    int* rank, float tau, cudaStream_t s) {
-#define DP2_MB(RB) k_mblock<RB><<<K, MB_THREADS, 0, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau)
+#define DP2_MB(RB)                                                                                   \
+  do {                                                                                               \
+    cudaFuncSetAttribute(k_mblock<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, MB_SMEM_CAP);    \
+    k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau); \
+  } while (0)
   switch (R) {
     case 10: DP2_MB(10); return;
     case 20: DP2_MB(20); return;
