@@ -499,7 +499,7 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     // ---- small SVD of B = M2^T B1 -> C_k B_k blocks of M, T_k, A_k ----
     double* GB = wsget<double>(ctx, "GB", (size_t)K * LP * LP);
     float* T = wsget<float>(ctx, "T", (size_t)K * LP * R);
-    launch_gram_b1(B1, Jp, J, K, LP, GB, s);
+    launch_gram_b1(B1, Jp, J, K, ell, LP, GB, s);
     launch_eig_top(GB, M2, K, ell, LP, R, T, nullptr, ctx->d_status, s);
     launch_mblock(B1, Jp, J, K, ell, LP, R, T, static_cast<float*>(comp->Bk.p), static_cast<float*>(comp->M.p),
                   static_cast<int*>(comp->rank1.p), 1e-5f, s);

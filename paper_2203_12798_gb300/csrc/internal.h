@@ -91,7 +91,7 @@ void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float
                       bool fp64, cudaStream_t s);
 void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s);
 void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s);
-void launch_gram_b1(const float* B1, int Jp, int J, int K, int LP, double* G, cudaStream_t s);
+void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, double* G, cudaStream_t s);
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s);
 // register-resident variant (one-sided Jacobi on the Cholesky factor); false for LP > 32
