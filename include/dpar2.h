@@ -177,6 +177,28 @@ DPAR2_API dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp*
                                      dpar2_dtype dtype, const float* H, const float* V, const float* W,
                                      const float* Upol, double* sq_err, double* fitness, void* stream);
 
+/* Identity-mode dpar2_reconstruct_error (X == NULL, Upol given) that
+ * allocates no device memory.  The paper has no counterpart: this variant
+ * exists for callers that must not allocate during a call.  Its scratch is a
+ * fixed array of DPAR2_NOALLOC_SCRATCH_BYTES (18 MiB) in the library's device
+ * image, one per device, enough for K R^2 <= 4,194,304 (for example K = 8000
+ * slices at R <= 22); larger problems are rejected with DPAR2_ERR_INVALID_ARG
+ * before anything is launched.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  No scratch word has to start at zero: every word a call
+ * reads is written earlier in the same call.  All calls on a device share the
+ * one array, so calls that overlap in time (other host threads, other
+ * contexts on the same device) race on it and must be serialised by the
+ * caller; consecutive calls are safe since each call has finished its device
+ * work when it returns.
+ *   H, V, W, Upol    device R x R, J x R, K x R, K x R x R (as dpar2_reconstruct_error)
+ *   sq_err, fitness  host outputs (either may be NULL) */
+#define DPAR2_NOALLOC_SCRATCH_BYTES (18u << 20)
+#define DPAR2_NOALLOC_MAX_KRR (1u << 22) /* largest K R^2 accepted */
+DPAR2_API dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpar2_comp* comp, const float* H,
+                                                       const float* V, const float* W, const float* Upol,
+                                                       double* sq_err, double* fitness, void* stream);
+
 /* Copy `rows` rows of J elements of `dtype` from host memory (rows packed,
  * row stride J; pinned memory gives asynchronous, full-bandwidth copies) into
  * the device layout dpar2_compress reads (row stride ldx elements, X_dev

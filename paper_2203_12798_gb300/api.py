@@ -58,6 +58,7 @@ SIGNATURES = {
     "dpar2_fit": (ctypes.c_int, [VP, VP, ctypes.POINTER(Options), VP, VP, VP, VP, VP, VP, DP,
                                  ctypes.POINTER(ctypes.c_int), DP, VP]),
     "dpar2_reconstruct_error": (ctypes.c_int, [VP, VP, VP, I64, ctypes.c_int, VP, VP, VP, VP, DP, DP, VP]),
+    "dpar2_reconstruct_error_noalloc": (ctypes.c_int, [VP, VP, VP, VP, VP, VP, DP, DP, VP]),
     "dpar2_comp_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_device_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_view_get": (ctypes.c_int, [VP, ctypes.POINTER(CompView)]),
@@ -206,6 +207,15 @@ class Context:
         dt = _DT[X.dtype] if X is not None else 0
         self._check(lib().dpar2_reconstruct_error(self._h, comp._h, _ptr(X), ldx, dt, _ptr(H), _ptr(V), _ptr(W),
                                                   _ptr(Upol), ctypes.byref(sq), ctypes.byref(fit), _stream()))
+        return sq.value, fit.value
+
+    def reconstruct_error_noalloc(self, comp: "Compressed", H, V, W, Upol):
+        """Identity-mode error with the library's fixed device scratch (no device
+        allocation; calls must not overlap in time)."""
+        sq = ctypes.c_double()
+        fit = ctypes.c_double()
+        self._check(lib().dpar2_reconstruct_error_noalloc(self._h, comp._h, _ptr(H), _ptr(V), _ptr(W), _ptr(Upol),
+                                                          ctypes.byref(sq), ctypes.byref(fit), _stream()))
         return sq.value, fit.value
 
 

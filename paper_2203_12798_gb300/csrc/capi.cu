@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -749,6 +750,84 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
     launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
     double* fpart = wsget<double>(ctx, "re_fit", (size_t)nblk + 4);
     launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk, s);
+    k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+    CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  });
+  if (st == DPAR2_OK) {
+    if (sq_err) *sq_err = res[0];
+    if (fitness) *fitness = res[1] > 0 ? 1.0 - res[0] / res[1] : 0.0;
+  }
+  return st;
+}
+
+// ------------------------------------- reconstruct error without allocation ----
+// Some callers must not allocate device memory inside a call: a serving loop
+// that reserves all of its device memory up front in its own pool, or one that
+// cannot take the device-wide synchronisation of a cudaFree when the
+// context's grow-only scratch has to grow for a larger problem.  For them the
+// identity-mode error evaluation has a variant whose scratch is a fixed array
+// in the library's device image (one per device, created when the module is
+// loaded), carved into its buffers on every call.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DPAR2_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocDevices = 64;
+void* g_noalloc_base[kNoAllocDevices] = {};
+
+// Device address of the array on the current device (looked up once per device).
+void* noalloc_base(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  require(dev >= 0 && dev < kNoAllocDevices, DPAR2_ERR_INVALID_ARG, "device ordinal out of range");
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_base[dev] = p;
+  }
+  return g_noalloc_base[dev];
+}
+
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpar2_comp* comp, const float* H, const float* V,
+                                             const float* W, const float* Upol, double* sq_err, double* fitness,
+                                             void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!comp || !H || !V || !W || !Upol) {
+    ctx->err = "comp, H, V, W and Upol must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (!comp->M.p) {
+    ctx->err = "identity mode needs M (compressed without DPAR2_FLAG_DROP_M)";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  const int K = comp->K, J = comp->J, R = comp->R, RR = R * R;
+  const int nblk = als_blocks(K, R, ctx->num_sms);
+  // P_k = V^T M_k, Psi and V^T V, the A^T B block partials, the fitness partials
+  const size_t bP = up256((size_t)K * RR * sizeof(float));
+  const size_t bD = up256((size_t)2 * RR * sizeof(double));
+  const size_t bA = up256((size_t)kAtbBlocks * RR * sizeof(float));
+  const size_t bF = up256(((size_t)nblk + 4) * sizeof(double));
+  // P takes the first 16 MiB (K R^2 <= 4,194,304); the rest (< 1.2 MiB for R <= 64) follows
+  if ((int64_t)K * RR > (int64_t)DPAR2_NOALLOC_MAX_KRR || bP + bD + bA + bF > (size_t)DPAR2_NOALLOC_SCRATCH_BYTES) {
+    ctx->err = "K R^2 = " + std::to_string((int64_t)K * RR) + " is above " +
+               std::to_string((int64_t)DPAR2_NOALLOC_MAX_KRR) + ", the limit of the fixed " +
+               std::to_string((size_t)DPAR2_NOALLOC_SCRATCH_BYTES) + "-byte scratch (use dpar2_reconstruct_error)";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  double res[2] = {0, 0};
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    unsigned char* base = static_cast<unsigned char*>(noalloc_base(ctx->device));
+    float* P = reinterpret_cast<float*>(base);
+    double* Psi = reinterpret_cast<double*>(base + bP);
+    double* VtV = Psi + RR;
+    float* apart = reinterpret_cast<float*>(base + bP + bD);
+    double* fpart = reinterpret_cast<double*>(base + bP + bD + bA);
+    launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV, apart, s);
+    launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
+    launch_fitness(K, R, P, Upol, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
+                   s);
     k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
     CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   });
