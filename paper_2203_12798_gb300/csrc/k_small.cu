@@ -189,22 +189,23 @@ __global__ void k_reduce_rows_f64(const double* __restrict__ part, int K, int n,
 // into registers while the current one is consumed from shared memory.
 constexpr int GB_THREADS = 256;
 
-template <int LP>
+template <int LP, int TE>  // TE = ceil(l / 4) tiles carry data (rows >= l of B1 are zero)
 __global__ void __launch_bounds__(GB_THREADS, 3) k_gram_b1(const float* __restrict__ B1, int Jp, int J, int ell,
                                                         double* __restrict__ G) {
-  constexpr int GB_CJ = LP <= 32 ? 128 : 64;  // columns per chunk (static shared memory <= 48 KB)
-  constexpr int T = LP / 4;
-  constexpr int NT = T * (T + 1) / 2;
+  constexpr int CR = 4 * TE;                   // rows of B1 staged
+  constexpr int GB_CJ = CR <= 32 ? 128 : 64;  // columns per chunk (static shared memory <= 48 KB)
+  constexpr int NT = TE * (TE + 1) / 2;
   constexpr int NG = GB_THREADS / NT > 0 ? GB_THREADS / NT : 1;
-  constexpr int PER = LP * GB_CJ / GB_THREADS;  // chunk elements per thread
-  __shared__ __align__(16) float bs[GB_CJ][LP + 4];
-  __shared__ float red[NG > 1 ? NG : 1][LP][LP + 1];
+  constexpr int PER = CR * GB_CJ / GB_THREADS;  // chunk elements per thread
+  static_assert(CR * GB_CJ % GB_THREADS == 0, "chunk split");
+  __shared__ __align__(16) float bs[GB_CJ][CR + 4];
+  __shared__ float red[NG > 1 ? NG : 1][CR][CR + 1];
   const int k = blockIdx.x, tid = threadIdx.x;
   const int grp = tid / NT, tt = tid % NT;
   int ta = 0, tb = 0;
   {
     int p = tt;
-    while (p >= T - ta) { p -= T - ta; ++ta; }
+    while (p >= TE - ta) { p -= TE - ta; ++ta; }
     tb = ta + p;
   }
   const bool act = grp < NG;
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(GB_THREADS, 3) k_gram_b1(const float* __restri
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = tid + u * GB_THREADS;
-      const int c = e / GB_CJ, jj = e % GB_CJ;  // rows c >= ell of B1 are zero and not read
+      const int c = e / GB_CJ, jj = e % GB_CJ;
       pre[u] = (c < ell && j0 + jj < J) ? __ldg(src + (int64_t)c * Jp + j0 + jj) : 0.f;
     }
   };
@@ -257,12 +258,14 @@ __global__ void __launch_bounds__(GB_THREADS, 3) k_gram_b1(const float* __restri
   double* g = G + (int64_t)k * LP * LP;
   for (int e = tid; e < LP * LP; e += GB_THREADS) {
     const int a = e / LP, b = e % LP;
-    // off-diagonal tiles hold only the (ua, ub) order; diagonal tiles both
-    const bool diag = (a / 4) == (b / 4);
-    const int ra = diag ? a : min(a, b), rb = diag ? b : max(a, b);
     float s = 0.f;
+    if (a < CR && b < CR) {
+      // off-diagonal tiles hold only the (ua, ub) order; diagonal tiles both
+      const bool diag = (a / 4) == (b / 4);
+      const int ra = diag ? a : min(a, b), rb = diag ? b : max(a, b);
 #pragma unroll
-    for (int q = 0; q < NG; ++q) s += red[q][ra][rb];
+      for (int q = 0; q < NG; ++q) s += red[q][ra][rb];
+    }
     g[e] = (double)s;
   }
 }
@@ -548,6 +551,96 @@ __global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 2 : 1) k_mblock(const f
   }
 }
 
+// Single-pass form for M_k that fits in shared memory: every column of B1_k is
+// read once (all l rows at once), M_k is kept in shared memory while its
+// column norms and sums are reduced, then scaled by the keep / sign factors
+// and written out contiguously.  EB = l rounded up to 8.
+constexpr int MB1_THREADS = 256;
+
+template <int RB, int EB>
+__global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restrict__ B1, int Jp, int J, int ell,
+                                                            int LP, int R, float* __restrict__ T,
+                                                            float* __restrict__ Bk, float* __restrict__ Mblk,
+                                                            int* __restrict__ rank, float tau) {
+  extern __shared__ __align__(16) float msm[];  // J x R
+  __shared__ __align__(16) float ts[EB * RB];
+  __shared__ double red[MB1_THREADS / 32][RB];
+  __shared__ double red2[MB1_THREADS / 32][RB];
+  __shared__ float keep[RB];
+  const int k = blockIdx.x, tid = threadIdx.x;
+  float* t = T + (int64_t)k * LP * R;
+  for (int e = tid; e < EB * RB; e += MB1_THREADS) {
+    const int c = e / RB, r = e % RB;
+    ts[e] = (r < R && c < ell) ? t[c * R + r] : 0.f;
+  }
+  __syncthreads();
+  const float* b1 = B1 + (int64_t)k * LP * Jp;
+  float nrm[RB], csum[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) nrm[r] = csum[r] = 0.f;
+  for (int j = tid; j < J; j += MB1_THREADS) {
+    float b[EB];
+#pragma unroll
+    for (int c = 0; c < EB; ++c) b[c] = (c < ell) ? __ldg(b1 + (int64_t)c * Jp + j) : 0.f;
+    float o[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) o[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < EB; ++c)
+#pragma unroll
+      for (int r = 0; r < RB; ++r) o[r] = fmaf(b[c], ts[c * RB + r], o[r]);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r < R) msm[j * R + r] = o[r];
+      nrm[r] = fmaf(o[r], o[r], nrm[r]);
+      csum[r] += o[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const float v = warp_sum(nrm[r]);
+    const float c = warp_sum(csum[r]);
+    if ((tid & 31) == 0) {
+      red[tid >> 5][r] = v;
+      red2[tid >> 5][r] = c;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double sg[2] = {0.0, 0.0}, cs[2] = {0.0, 0.0};
+    double smax = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + 32 * h;
+      if (r < RB) {
+        for (int w = 0; w < MB1_THREADS / 32; ++w) {
+          sg[h] += red[w][r];
+          cs[h] += red2[w][r];
+        }
+        sg[h] = sqrt(sg[h]);
+        if (r < R) smax = fmax(smax, sg[h]);
+      }
+    }
+    smax = warp_max_d(smax);
+    int rk = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = tid + 32 * h;
+      // sign rule: the right singular vector (column of C_k) has a non-negative sum
+      const bool kp = r < R && r < ell && sg[h] > (double)tau * smax && smax > 0.0;
+      if (r < RB) keep[r] = kp ? (cs[h] < 0.0 ? -1.f : 1.f) : 0.f;
+      if (r < R) Bk[(int64_t)k * R + r] = kp ? (float)sg[h] : 0.f;
+      rk += kp;
+    }
+    rk = __reduce_add_sync(0xffffffffu, rk);
+    if (tid == 0 && rank) rank[k] = rk;
+  }
+  __syncthreads();
+  for (int e = tid; e < LP * R; e += MB1_THREADS) t[e] *= keep[e % R];
+  float* mk = Mblk + (int64_t)k * J * R;
+  for (int e = tid; e < J * R; e += MB1_THREADS) mk[e] = msm[e] * keep[e % R];
+}
+
 // -------------------------------------------- row-segment small products ----
 // Out[row] (nout) = In[row] (nin, pitch ldin) * T_seg (nin x nout, stride tstride
 // per segment), segments given by offsets (K + 1).
@@ -727,7 +820,11 @@ void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaS
 }
 
 void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, double* G, cudaStream_t s) {
-  DP2_LP_SWITCH(LP, (k_gram_b1<L><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G)));
+  if (LP == 24 && ell <= 20) {  // the common l = R + p = 20
+    k_gram_b1<24, 5><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G);
+    return;
+  }
+  DP2_LP_SWITCH(LP, (k_gram_b1<L, L / 4><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G)));
 }
 
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
@@ -749,6 +846,20 @@ void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R
     cudaFuncSetAttribute(k_mblock<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, MB_SMEM_CAP);    \
     k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau); \
   } while (0)
+  // single pass when M_k fits twice per SM in shared memory
+  const size_t msm = (size_t)J * R * sizeof(float);
+  const int eb = round_up(ell, 8);
+#define DP2_MB1(RB, EB)                                                                                  \
+  do {                                                                                                   \
+    cudaFuncSetAttribute(k_mblock1<RB, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);      \
+    k_mblock1<RB, EB><<<K, MB1_THREADS, msm, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau);      \
+  } while (0)
+  if (msm <= 100 * 1024) {
+    if (R == 10 && eb == 24) { DP2_MB1(10, 24); return; }
+    if (R == 20 && eb == 32) { DP2_MB1(20, 32); return; }
+    if (R == 30 && eb == 40) { DP2_MB1(30, 40); return; }
+  }
+#undef DP2_MB1
   switch (R) {
     case 10: DP2_MB(10); return;
     case 20: DP2_MB(20); return;
