@@ -113,6 +113,14 @@ DPAR2_API dpar2_status dpar2_options_default(dpar2_options* opt);
 DPAR2_API dpar2_status dpar2_create(dpar2_ctx** ctx, int device);
 DPAR2_API void dpar2_destroy(dpar2_ctx* ctx);
 DPAR2_API const char* dpar2_last_error(const dpar2_ctx* ctx);
+/* Information bits of the last call's device status word (not errors; the
+ * paper has no counterpart): a CholeskyQR step dropped a numerically
+ * dependent sketch column, a Jacobi solver stopped at its sweep cap, a
+ * Gram-Hadamard solve fell back to the eigen pseudoinverse.  0 for a null ctx. */
+#define DPAR2_INFO_RANK_DROP 4
+#define DPAR2_INFO_SWEEP_CAP 8
+#define DPAR2_INFO_PINV 16
+DPAR2_API int dpar2_last_info(const dpar2_ctx* ctx);
 
 /* Fill out[0..n) (device, float32) with the Gaussian stream (seed, stream_id):
  * Philox4x32-10 (Salmon et al. SC'11) with counter (n/4 lo, n/4 hi, stream_id, 0)

@@ -59,6 +59,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_int), DP, VP]),
     "dpar2_reconstruct_error": (ctypes.c_int, [VP, VP, VP, I64, ctypes.c_int, VP, VP, VP, VP, DP, DP, VP]),
     "dpar2_reconstruct_error_noalloc": (ctypes.c_int, [VP, VP, VP, VP, VP, VP, DP, DP, VP]),
+    "dpar2_last_info": (ctypes.c_int, [VP]),
     "dpar2_comp_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_device_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_view_get": (ctypes.c_int, [VP, ctypes.POINTER(CompView)]),
@@ -142,6 +143,11 @@ class Context:
     # ------------------------------------------------------------- timing
     def set_timing(self, on: bool = True):
         self._check(lib().dpar2_set_timing(self._h, int(on)))
+
+    def last_info(self) -> dict:
+        """Information bits of the last call (dropped pivots, Jacobi sweep cap, pinv fallback)."""
+        v = lib().dpar2_last_info(self._h)
+        return {"rank_drop": bool(v & 4), "sweep_cap": bool(v & 8), "pinv": bool(v & 16)}
 
     def timings(self) -> dict:
         """Milliseconds of each phase of the last compress / fit (CUDA events

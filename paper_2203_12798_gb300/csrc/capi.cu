@@ -274,6 +274,9 @@ void dpar2_destroy(dpar2_ctx* ctx) {
 }
 
 const char* dpar2_last_error(const dpar2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int dpar2_last_info(const dpar2_ctx* ctx) {
+  return (ctx && ctx->h_status) ? (*ctx->h_status & (ST_RANK_DROP | ST_SWEEP_CAP | ST_PINV)) : 0;
+}
 
 dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* Xh, int64_t rows, int J, dpar2_dtype dtype, void* Xd,
                                int64_t ldx, void* stream) {
@@ -471,7 +474,7 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
       CK(cudaMemcpyAsync(d_poff, hp.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
       void* Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * Npad);
       launch_qsplit(Y, LP, LPN, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
-      const int nJb_tc = (Jp + 127) / 128;
+      const int nJb_tc = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
       // one partial ||X_k||^2 per (slice, column block, norm warp)
       double* xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
       CK(cudaStreamSynchronize(s));  // hp must outlive the pageable copy
@@ -622,7 +625,9 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.WtW = d6 + 3 * RR;
     b.Ginv = d6 + 4 * RR;
     b.nblk = als_blocks(K, R, ctx->num_sms);
-    b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.nblk * (2 * RR + 2));
+    b.nq = qstep_blocks(K, R, b.nblk);
+    b.pr = std::max(b.nblk, b.nq);
+    b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.pr * (2 * RR + 2));
     b.loss = wsget<double>(ctx, "als_loss", (size_t)opt->max_iter);
     b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR + 8);
     b.atb = wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * RR);
@@ -740,7 +745,9 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       b.Psi = Psi;
       b.Upol = wsget<float>(ctx, "re_upol", (size_t)K * RR);
       b.Pi = wsget<float>(ctx, "re_pi", (size_t)K * RR);
-      b.part = wsget<float>(ctx, "re_part", (size_t)3 * nblk * (2 * RR + 2));
+      b.nq = qstep_blocks(K, R, nblk);
+      b.pr = std::max(nblk, b.nq);
+      b.part = wsget<float>(ctx, "re_part", (size_t)3 * b.pr * (2 * RR + 2));
       b.status = ctx->d_status;
       b.nblk = nblk;
       launch_qstep_only(b, s);

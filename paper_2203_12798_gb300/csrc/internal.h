@@ -76,6 +76,8 @@ bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int
                       int LPN, int LP, float* Y, int num_sms, int* status, cudaStream_t s);
 void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
                    int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
+// X columns per work item of the tensor-core projection (nJb = ceil(Jp / cols))
+int project_tc_cols(int LPN);
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
                        float* B1, double* xpart, int nJb, int num_sms, int* status, cudaStream_t s);
@@ -136,12 +138,14 @@ struct AlsBufs {
   double* HtH;        // R x R
   double* WtW;        // R x R
   double* Ginv;       // R x R  (V^T V * H^T H)^+
-  float* part;        // 3 x nblk x (2 R^2 + 2) block partials
+  float* part;        // 3 regions x pr x (2 R^2 + 2) block partials
   double* loss;       // max_iter history (device)
   double* small;      // scratch, 8 R^2 + 8 doubles
   float* atb;         // scratch of launch_atb, kAtbBlocks R^2 floats
   int* status;
-  int nblk;
+  int nblk;      // blocks of the Lemma 2 / 3 kernels (partials in regions 2, 3)
+  int nq = 0;    // blocks of the Q-step (Lemma 1 partials in region 1)
+  int pr = 0;    // partials per region of `part` (max(nblk, nq))
 };
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
@@ -150,6 +154,8 @@ int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
 // register-resident Q-step (lane = column); false when R has no instantiation (R > 32)
 bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
+// blocks of the Q-step launch for K slices at rank R (one wave of resident blocks when it fits)
+int qstep_blocks(int K, int R, int nblk);
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);
 void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);

@@ -62,6 +62,50 @@ __device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int
   }
 }
 
+// Two-phase reduction out[e] = sum_b part[b * pstride + e] (e < n, n <= T) by
+// the threads [t0, t0 + T) of the block: every entry's partials are split over
+// tpe = T / n threads, each of which keeps 16 loads in flight and sums them
+// with compensation in FP32 (phase 1, into red); after a barrier the tpe
+// sub-sums of an entry are added in a fixed order in FP64 (phase 2).
+constexpr int kRedMax = 1024;
+__device__ inline void par_reduce_load(const float* __restrict__ part, int nparts, int pstride, int n, int t0, int T,
+                                       double* red) {
+  const int t = threadIdx.x - t0;
+  if (t < 0 || t >= T) return;
+  const int tpe = max(1, T / n);
+  const int e = t / tpe, sub = t - e * tpe;
+  double v = 0.0;
+  if (e < n) {
+    float s = 0.f, c = 0.f;
+    int b = sub;
+    for (; b + 15 * tpe < nparts; b += 16 * tpe) {
+      float x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = part[(int64_t)(b + u * tpe) * pstride + e];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) neumaier(s, c, x[u]);
+    }
+    for (; b < nparts; b += tpe) neumaier(s, c, part[(int64_t)b * pstride + e]);
+    v = (double)s + (double)c;
+  }
+  red[t] = v;
+}
+__device__ inline void par_reduce_combine(int n, int t0, int T, const double* red, double* out) {
+  const int t = threadIdx.x - t0;
+  if (t < 0 || t >= T) return;
+  const int tpe = max(1, T / n);
+  if (t >= n) return;  // thread t combines entry t
+  const double* r = red + t * tpe;
+  double a = 0.0, b = 0.0;
+  int q = 0;
+  for (; q + 1 < tpe; q += 2) {
+    a += r[q];
+    b += r[q + 1];
+  }
+  if (q < tpe) a += r[q];
+  out[t] = a + b;
+}
+
 // out (n x n, FP64) = A^T B for A, B (rows x n, fp32, row-major): every block
 // stages tiles of ATB_ROWS rows of its row chunk in shared memory and
 // accumulates up to 16 entries per thread; the block partials are summed in
@@ -432,31 +476,52 @@ __device__ void jacobi_eig_f64(double* A, double* V, int n) {
 __host__ __device__ inline size_t spd_pinv_smem(int n) {
   return (size_t)(2 * n * n + n) * sizeof(double) + (size_t)(n * (n + 1) / 2) * sizeof(unsigned short);
 }
+// the same in doubles, rounded up
+__host__ __device__ inline size_t spd_pinv_words(int n) { return (spd_pinv_smem(n) + 7) / 8; }
+// shared memory of the H / V updates: the pseudoinverse workspace plus 5 R^2 + 2
+// doubles of intermediates when that fits in 160 KB (R <= 48), else the workspace only
+inline size_t update_smem(int R, int* inshared) {
+  const size_t full = (spd_pinv_words(R) + 5 * (size_t)R * R + 2) * sizeof(double);
+  *inshared = full <= 160 * 1024;
+  return *inshared ? full : spd_pinv_smem(R);
+}
 
-__device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* V, int n, double* sh,
-                               int* status) {
-  __shared__ int ok;
-  double* Rm = sh;
-  double* Mi = Rm + n * n;
-  double* rinv = Mi + n * n;
+// Warp 0: Cholesky A = R^T R and R^-1 (in T precision) into the workspace sh;
+// returns (in warp 0) whether every pivot was above 1e-300 (FP64) / the FP32
+// rounding level of A's diagonal (FP32).
+template <typename T>
+__device__ bool warp_spd_factor(const double* A, int n, T* sh) {
+  T* Rm = sh;
+  T* Mi = Rm + n * n;
+  T* rinv = Mi + n * n;
   unsigned short* pairs = reinterpret_cast<unsigned short*>(rinv + n);
-  if (threadIdx.x < 32) {
-    for (int e = threadIdx.x; e < n * n; e += 32) {
-      Rm[e] = A[e];
-      Mi[e] = 0.0;
-    }
-    warp_pair_table(pairs, n);
-    const int nd = warp_chol_upper<double>(Rm, n, 1e-300, false, rinv, pairs);
-    if (nd == 0) warp_tri_inv<double>(Rm, n, rinv, Mi);
-    if (threadIdx.x == 0) ok = (nd == 0);
+  T md = T(0);
+  for (int e = threadIdx.x; e < n * n; e += 32) {
+    Rm[e] = (T)A[e];
+    Mi[e] = T(0);
+    if (e / n == e % n) md = fmax(md, Rm[e]);
   }
-  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+  warp_pair_table(pairs, n);
+  const T thr = sizeof(T) == 8 ? T(1e-300) : T(64 * 1.2e-7) * md;
+  const int nd = warp_chol_upper<T>(Rm, n, thr, false, rinv, pairs);
+  if (nd == 0) warp_tri_inv<T>(Rm, n, rinv, Mi);
+  return nd == 0;
+}
+
+// Whole block, after warp_spd_factor and a barrier: Inv = R^-1 R^-T, or (ok
+// false) the eigen pseudoinverse (MATLAB tolerance n eps ||A||) of A.
+template <typename T, typename OutT>
+__device__ void block_spd_finish(bool ok, const double* A, OutT* Inv, double* L, double* V, int n, const T* sh,
+                                 int* status) {
+  const T* Mi = sh + n * n;
   if (ok) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int a = e / n, b = e - a * n;
-      double s = 0.0;
+      T s = T(0);
       for (int i = max(a, b); i < n; ++i) s = fma(Mi[a * n + i], Mi[b * n + i], s);
-      Inv[e] = s;
+      Inv[e] = (OutT)s;
     }
     __syncthreads();
     return;
@@ -475,10 +540,22 @@ __device__ void block_spd_pinv(const double* A, double* Inv, double* L, double* 
           const double l = L[i * n + i];
           if (l > tol) s += V[a * n + i] * V[b * n + i] / l;
         }
-        Inv[a * n + b] = s;
+        Inv[a * n + b] = (OutT)s;
       }
   }
   __syncthreads();
+}
+
+// Inv <- A^+ for symmetric PSD A (n x n), computed by the whole block.
+template <typename T, typename OutT>
+__device__ void block_spd_pinv(const double* A, OutT* Inv, double* L, double* V, int n, T* sh, int* status) {
+  __shared__ int ok;
+  if (threadIdx.x < 32) {
+    const bool f = warp_spd_factor<T>(A, n, sh);
+    if (threadIdx.x == 0) ok = f;
+  }
+  __syncthreads();
+  block_spd_finish<T, OutT>(ok != 0, A, Inv, L, V, n, sh, status);
 }
 
 // Scale factors 1 / ||column r|| for the R columns whose squared norms are
@@ -492,24 +569,32 @@ __device__ inline double inv_norm(double n2, int* status) {
 // H = G1 (W^T W * V^T V)^+, columns normalised; HtH = H^T H.
 // When it > 0 it first closes the previous iteration: W^T W and its e from the
 // partials of the W update (part3; e as a (hi, lo) float pair).
-__global__ void __launch_bounds__(512) k_update_h(int R, const float* __restrict__ part,
+__global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restrict__ part, int nq,
                                                   const float* __restrict__ part3, int nblk, int pstride, int it,
                                                   double* __restrict__ WtW, const double* __restrict__ VtV,
                                                   float* __restrict__ H, double* __restrict__ HtH,
                                                   double* __restrict__ loss, double* __restrict__ scratch,
-                                                  int* __restrict__ status) {
+                                                  int* __restrict__ status, int inshared) {
   extern __shared__ __align__(16) double ush[];
   __shared__ double scl[kMaxR];
   const int RR = R * R;
-  double* G1 = scratch;
+  // R x R intermediates in shared memory (global scratch for large R); L, V:
+  // work arrays of the pseudoinverse fallback
+  double* L = scratch;
+  double* V = L + RR;
+  double* G1 = inshared ? ush + spd_pinv_words(R) : scratch + 2 * RR;
   double* Gm = G1 + RR;
   double* Inv = Gm + RR;
-  double* L = Inv + RR;
-  double* V = L + RR;
-  double* Hn = V + RR;
+  double* Hn = Inv + RR;
   double* W3 = Hn + RR;  // RR + 2
+  __shared__ int ok;
+  __shared__ double red[kRedMax];
+  const int T = blockDim.x;
   if (it > 0) {
-    block_reduce_parts(part3, nblk, pstride, RR + 2, W3);
+    par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red);
+    __syncthreads();
+    par_reduce_combine(RR + 2, 0, T, red, W3);
+    __syncthreads();
     for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
       if (e < RR) WtW[e] = W3[e];
       else {
@@ -518,12 +603,19 @@ __global__ void __launch_bounds__(512) k_update_h(int R, const float* __restrict
         if (!isfinite(v)) set_status(status, ST_NONFINITE);
       }
     }
-    __syncthreads();
   }
-  block_reduce_parts(part, nblk, pstride, RR, G1);
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * VtV[e];
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = (it > 0 ? W3[e] : WtW[e]) * VtV[e];
   __syncthreads();
-  block_spd_pinv(Gm, Inv, L, V, R, ush, status);
+  // warp 0 factors (W^T W * V^T V) while the other threads reduce the Lemma 1 partials
+  if (threadIdx.x < 32) {
+    const bool f = warp_spd_factor<double>(Gm, R, ush);
+    if (threadIdx.x == 0) ok = f;
+  }
+  par_reduce_load(part, nq, pstride, RR, 32, T - 32, red);
+  __syncthreads();
+  par_reduce_combine(RR, 32, T - 32, red, G1);
+  __syncthreads();
+  block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int i = e / R, r = e - i * R;
     double s = 0.0;
@@ -551,26 +643,37 @@ __global__ void __launch_bounds__(512) k_update_h(int R, const float* __restrict
 // --------------------------------------------------------------- V update --
 // CV = g (W^T W * H^T H)^+ with columns normalised through D^T D; then
 // Psi = D^T D CV, V^T V = CV^T D^T D CV and Ginv = (V^T V * H^T H)^+ for the W update.
-__global__ void __launch_bounds__(512) k_update_v(int R, const float* __restrict__ part, int nblk, int pstride,
+__global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restrict__ part, int nblk, int pstride,
                                                   const double* __restrict__ WtW, const double* __restrict__ HtH,
                                                   const double* __restrict__ DtD, float* __restrict__ CV,
                                                   double* __restrict__ Psi, double* __restrict__ VtV,
                                                   double* __restrict__ Ginv, double* __restrict__ scratch,
-                                                  int* __restrict__ status) {
+                                                  int* __restrict__ status, int inshared) {
   extern __shared__ __align__(16) double ush[];
   __shared__ double scl[kMaxR];
   const int RR = R * R;
-  double* g = scratch;
+  double* L = scratch;
+  double* V = L + RR;
+  double* g = inshared ? ush + spd_pinv_words(R) : scratch + 2 * RR;
   double* Gm = g + RR;
   double* Inv = Gm + RR;
-  double* L = Inv + RR;
-  double* V = L + RR;
-  double* C = V + RR;
+  double* C = Inv + RR;
   double* DC = C + RR;
-  block_reduce_parts(part, nblk, pstride, RR, g);
+  __shared__ int ok;
+  __shared__ double red[kRedMax];
+  const int T = blockDim.x;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
   __syncthreads();
-  block_spd_pinv(Gm, Inv, L, V, R, ush, status);
+  // warp 0 factors (W^T W * H^T H) while the other threads reduce the Lemma 2 partials
+  if (threadIdx.x < 32) {
+    const bool f = warp_spd_factor<double>(Gm, R, ush);
+    if (threadIdx.x == 0) ok = f;
+  }
+  par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red);
+  __syncthreads();
+  par_reduce_combine(RR, 32, T - 32, red, g);
+  __syncthreads();
+  block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int i = e / R, r = e - i * R;
     double s = 0.0;
@@ -607,7 +710,18 @@ __global__ void __launch_bounds__(512) k_update_v(int R, const float* __restrict
     Gm[e] = s * HtH[e];
   }
   __syncthreads();
-  block_spd_pinv(Gm, Ginv, L, V, R, ush, status);
+  // Ginv only enters the W update in FP32 (W_k = G3_k Ginv with G3 and Ginv as
+  // floats), so it is factored in FP32 (FP64 fallback when a pivot fails)
+  {
+    float* fsh = reinterpret_cast<float*>(ush);
+    if (threadIdx.x < 32) {
+      const bool f = warp_spd_factor<float>(Gm, R, fsh);
+      if (threadIdx.x == 0) ok = f;
+    }
+    __syncthreads();
+    if (ok) block_spd_finish<float, double>(true, Gm, Ginv, L, V, R, fsh, status);
+    else block_spd_pinv<double, double>(Gm, Ginv, L, V, R, ush, status);
+  }
 }
 
 // ----------------------------------------------------- iteration epilogue --
@@ -788,8 +902,8 @@ void als_set_attrs() {
   cudaFuncSetAttribute(k_g2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g3w, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_fitness, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_update_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spd_pinv_smem(kMaxR));
-  cudaFuncSetAttribute(k_update_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spd_pinv_smem(kMaxR));
+  cudaFuncSetAttribute(k_update_h, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  cudaFuncSetAttribute(k_update_v, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   done = true;
 }
 
@@ -814,16 +928,18 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   const int R = b.R, RR = R * R, nw = als_warps(R);
   const int ps = 2 * RR + 2;
   float* p1 = b.part;
-  float* p2 = b.part + (size_t)b.nblk * ps;
-  float* p3 = b.part + (size_t)2 * b.nblk * ps;
+  float* p2 = b.part + (size_t)b.pr * ps;
+  float* p3 = b.part + (size_t)2 * b.pr * ps;
   if (!launch_qstep_reg(b, p1, ps, 1, s))
     k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
                                                        b.status, 1);
-  const size_t psm = spd_pinv_smem(R);
-  k_update_h<<<1, 512, psm, s>>>(R, p1, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small, b.status);
+  int insh = 0;
+  const size_t psm = update_smem(R, &insh);
+  k_update_h<<<1, 1024, psm, s>>>(R, p1, b.nq, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small,
+                                 b.status, insh);
   k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps);
-  k_update_v<<<1, 512, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
-                               b.status);
+  k_update_v<<<1, 1024, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
+                               b.status, insh);
   k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
       b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, p3, ps);
 }
@@ -831,7 +947,7 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
 // Closes the last iteration `it`: W^T W and loss[it] from the W-update partials.
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s) {
   const int R = b.R, RR = R * R, ps = 2 * RR + 2;
-  k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.nblk * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
+  k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.pr * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
                              b.status);
 }
 

@@ -29,7 +29,7 @@
 namespace dp2 {
 
 template <int R>
-__global__ void __launch_bounds__(256, R <= 12 ? 2 : 1) k_qstep_reg(int K, int Ra, const float* __restrict__ Ft,
+__global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_reg(int K, int Ra, const float* __restrict__ Ft,
                                                    const double* __restrict__ Psi, const float* __restrict__ W,
                                                    const float* __restrict__ H, float* __restrict__ Upol,
                                                    float* __restrict__ Pi, float* __restrict__ part, int pstride,
@@ -303,19 +303,51 @@ __global__ void __launch_bounds__(256, R <= 12 ? 2 : 1) k_qstep_reg(int K, int R
   }
 }
 
+// Warps per block: six for R <= 12 (three resident blocks per SM at <= 112
+// registers, so that K = 8000 fits one wave), else eight (shared-memory bound).
+template <int R>
+constexpr int qreg_warps() { return R <= 12 ? 6 : 8; }
+
+template <int R>
+static int qreg_nw() {
+  constexpr int G = 32 / R;
+  const size_t per_warp = (size_t)G * 4 * R * R * sizeof(float);
+  return (int)std::min<size_t>(qreg_warps<R>(), std::max<size_t>(1, (96 * 1024) / per_warp));
+}
+
 template <int R>
 static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
   constexpr int G = 32 / R;
   const size_t per_warp = (size_t)G * 4 * R * R * sizeof(float);
-  int nw = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
+  const int nw = qreg_nw<R>();
   const size_t smem = nw * per_warp;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_qstep_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     attr = true;
   }
-  k_qstep_reg<R><<<b.nblk, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                               b.status, want_g1, b.Prot);
+  k_qstep_reg<R><<<b.nq, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
+                                             b.status, want_g1, b.Prot);
+}
+
+template <int R>
+static int qblocks(int K) {
+  const int per = qreg_nw<R>() * (32 / R);
+  return std::max(1, (K + per - 1) / per);
+}
+
+int qstep_blocks(int K, int R, int nblk) {
+  switch (R) {
+    case 10: return qblocks<10>(K);
+    case 20: return qblocks<20>(K);
+    case 30: return qblocks<30>(K);
+    default: break;
+  }
+  if (R <= 8) return qblocks<8>(K);
+  if (R <= 16) return qblocks<16>(K);
+  if (R <= 24) return qblocks<24>(K);
+  if (R <= 32) return qblocks<32>(K);
+  return nblk;  // shared-memory Q-step on the Lemma 2 / 3 grid
 }
 
 // Launches the register-resident Q-step when the rank has an instantiation

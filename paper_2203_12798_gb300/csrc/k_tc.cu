@@ -321,10 +321,16 @@ constexpr int PJ_THREADS = 32 * (6 + PJ_NORM_WARPS);
 
 template <int LPN>
 struct ProjSmem {
-  static constexpr int NS = 3 * LPN;          // hi / mid / lo splits
-  static constexpr int A = PJ_BM * PJ_BK * 2;  // two 64-column boxes of 64 rows
+  // HV column halves of PJ_BM columns per work item (two when their double-
+  // buffered accumulators fit the 512 TMEM columns): wider rows per TMA load
+  // and one Q tile per stage for both halves
+  static constexpr int HV = (4 * 3 * LPN <= 512) ? 2 : 1;
+  static constexpr int NS = 3 * LPN;               // hi / mid / lo splits
+  static constexpr int A = HV * PJ_BM * PJ_BK * 2;  // 2 HV 64-column boxes of 64 rows, 8 KB each
   static constexpr int B = NS * PJ_BK * 2;
-  static constexpr int BYTES = 1024 + PJ_STAGES * (A + B) + 256;
+  static constexpr int STAGES = HV == 2 ? 4 : PJ_STAGES;
+  static constexpr int BYTES = 1024 + STAGES * (A + B) + 256;
+  static constexpr int COLS = HV * PJ_BM;          // columns of X per work item
 };
 
 template <int LPN>
@@ -335,14 +341,15 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
                                                        int LP, float* __restrict__ B1, double* __restrict__ xpart,
                                                        int nJb, int bf16, int* status) {
   using S = ProjSmem<LPN>;
-  constexpr uint32_t NCOL = 2 * S::NS <= 256 ? 256 : 512;
+  constexpr int ST = S::STAGES;
+  constexpr uint32_t NCOL = 2 * S::HV * S::NS <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
   uint8_t* sA = base;
-  uint8_t* sB = base + PJ_STAGES * S::A;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + PJ_STAGES * S::B);
-  uint64_t* empty = full + PJ_STAGES;
-  uint64_t* accfull = empty + PJ_STAGES;
+  uint8_t* sB = base + ST * S::A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + ST * S::B);
+  uint64_t* empty = full + ST;
+  uint64_t* accfull = empty + ST;
   uint64_t* accempty = accfull + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -350,7 +357,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
   const int64_t nitems = (int64_t)K * nJb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PJ_STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1 + PJ_NORM_WARPS);  // MMA commit + one arrival per norm warp
     }
@@ -390,11 +397,12 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         }
         mbar_arrive_expect_tx(&full[s], S::A + S::B);
         uint8_t* a = sA + s * S::A;
-        tma_load_2d(a, &tmX, &full[s], jb * PJ_BM, (int)(r0 + c * PJ_BK));
-        tma_load_2d(a + S::A / 2, &tmX, &full[s], jb * PJ_BM + 64, (int)(r0 + c * PJ_BK));
+#pragma unroll
+        for (int bx = 0; bx < 2 * S::HV; ++bx)
+          tma_load_2d(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, (int)(r0 + c * PJ_BK));
         tma_load_2d(sB + s * S::B, &tmQ, &full[s], (int)(p0 + c * PJ_BK), 0);
         inflight = true;
-        if (++s == PJ_STAGES) {
+        if (++s == ST) {
           s = 0;
           ph ^= 1;
         }
@@ -402,7 +410,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       if (!ok) break;
     }
     if (*abort_flag && inflight) {
-      const int ls = (s + PJ_STAGES - 1) % PJ_STAGES;
+      const int ls = (s + ST - 1) % ST;
       const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
       const uint64_t t0 = globaltimer();
       while (!mbar_try_wait(&full[ls], lph) && globaltimer() - t0 < kWaitNs) {
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       const uint32_t aph = (t >> 1) & 1;
       if (!wait_bounded(&accempty[acc], aph ^ 1, abort_flag)) break;
       tc_fence_after();
-      const uint32_t d = tmem + acc * S::NS;
+      const uint32_t d = tmem + acc * S::HV * S::NS;
       bool ok = true;
       for (int c = 0; c < nch; ++c) {
         if (!wait_bounded(&full[s], ph, abort_flag)) {
@@ -431,16 +439,20 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
           break;
         }
         tc_fence_after();
-        // A: MN-major, 64-column atoms 8 KB apart, 8-row K groups 1 KB apart
-        const uint64_t ad = sdesc_sw128(smem_u32(sA + s * S::A), S::A / 2, 1024);
         // B: K-major, 8-row groups 1 KB apart
         const uint64_t bd = sdesc_sw128(smem_u32(sB + s * S::B), 16, 1024);
 #pragma unroll
-        for (int kk = 0; kk < PJ_BK / 16; ++kk)
-          tc_mma(d, ad + (uint64_t)(kk * 128), bd + (uint64_t)(kk * 2), idesc, (c | kk) != 0 ? 1u : 0u);
+        for (int h = 0; h < S::HV; ++h) {
+          // A (half h): MN-major, 64-column atoms 8 KB apart, 8-row K groups 1 KB apart
+          const uint64_t ad = sdesc_sw128(smem_u32(sA + s * S::A + h * 16384), 8192, 1024);
+#pragma unroll
+          for (int kk = 0; kk < PJ_BK / 16; ++kk)
+            tc_mma(d + h * S::NS, ad + (uint64_t)(kk * 128), bd + (uint64_t)(kk * 2), idesc,
+                   (c | kk) != 0 ? 1u : 0u);
+        }
         tc_commit(&empty[s]);
         issued = true;
-        if (++s == PJ_STAGES) {
+        if (++s == ST) {
           s = 0;
           ph ^= 1;
         }
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       tc_commit(&accfull[acc]);
     }
     if (*abort_flag && issued) {
-      const int ls = (s + PJ_STAGES - 1) % PJ_STAGES;
+      const int ls = (s + ST - 1) % ST;
       const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
       const uint64_t t0 = globaltimer();
       while (!mbar_try_wait(&empty[ls], lph) && globaltimer() - t0 < kWaitNs) {
@@ -465,22 +477,24 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       const uint32_t aph = (t >> 1) & 1;
       if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
       tc_fence_after();
-      const int j = jb * PJ_BM + q * 32 + lane;
-      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + acc * S::NS;
-      for (int g = 0; g < LPN / 32; ++g) {
-        float v[32], w[32];
-        tmem_ld32(tl + g * 32, v);
-        tmem_ld32(tl + LPN + g * 32, w);
+      for (int h = 0; h < S::HV; ++h) {
+        const int j = jb * S::COLS + h * PJ_BM + q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + acc * S::HV * S::NS + h * S::NS;
+        for (int g = 0; g < LPN / 32; ++g) {
+          float v[32], w[32];
+          tmem_ld32(tl + g * 32, v);
+          tmem_ld32(tl + LPN + g * 32, w);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += w[i];
-        tmem_ld32(tl + 2 * LPN + g * 32, w);
+          for (int i = 0; i < 32; ++i) v[i] += w[i];
+          tmem_ld32(tl + 2 * LPN + g * 32, w);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += w[i];
-        if (j < Jp) {
-          float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
+          for (int i = 0; i < 32; ++i) v[i] += w[i];
+          if (j < Jp) {
+            float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i];
+            for (int i = 0; i < 32; ++i)
+              if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i];
+          }
         }
       }
       tc_fence_before();
@@ -489,7 +503,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
   } else if (warp >= 6) {
     // ------------------------------------------------------------ ||X_k||^2
     // Norm warp nw scans bytes [nw * BYTES_PER, (nw + 1) * BYTES_PER) of every
-    // staged X tile (two 8 KB boxes of 64 rows x 128 bytes), rows of the
+    // staged X tile (2 HV 8 KB boxes of 64 rows x 128 bytes), rows of the
     // current slice only, and writes its own partial sum per work item
     // (xpart is K x nJb x PJ_NORM_WARPS; a later kernel adds them in order).
     constexpr int BYTES_PER = S::A / PJ_NORM_WARPS;
@@ -512,7 +526,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
 #pragma unroll
         for (int it = 0; it < BYTES_PER / 512; ++it) {
           const int byte = nw * BYTES_PER + it * 512 + lane * 16;
-          const int row = (byte % (S::A / 2)) / 128;
+          const int row = (byte % 8192) / 128;
           if (row < valid) {
             const uint4 u = *reinterpret_cast<const uint4*>(a + it * 512 + lane * 16);
             float f[8];
@@ -524,7 +538,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        if (++s == PJ_STAGES) {
+        if (++s == ST) {
           s = 0;
           ph ^= 1;
         }
@@ -656,6 +670,8 @@ bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int
   }
   return true;
 }
+
+int project_tc_cols(int LPN) { return LPN == 32 ? tc::ProjSmem<32>::COLS : tc::ProjSmem<64>::COLS; }
 
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
