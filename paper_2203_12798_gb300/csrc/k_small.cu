@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
   const int k = blockIdx.x, tid = threadIdx.x, split = blockIdx.y;
   const int P = ell * (ell + 1) / 2;
   int pa[GR_MAXP], pb[GR_MAXP];
-  DF acc[GR_MAXP];  // (hi, lo) double-float, or two plain FP32 partial sums
+  DF acc[GR_MAXP];   // (hi, lo) double-float, or two plain FP32 partial sums
+  DF acc2[GR_MAXP];  // second double-float accumulator (odd rows): two independent chains
 #pragma unroll
   for (int i = 0; i < GR_MAXP; ++i) {
     int p = tid + i * GR_THREADS;
@@ -49,6 +50,8 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
     pb[i] = b;
     acc[i].hi = 0.f;
     acc[i].lo = 0.f;
+    acc2[i].hi = 0.f;
+    acc2[i].lo = 0.f;
   }
   // rows of slice k, split in nsplit contiguous ranges (one per blockIdx.y)
   const int64_t s0 = off[k], s1 = off[k + 1];
@@ -61,11 +64,20 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
       reinterpret_cast<float4*>(ys)[p] = reinterpret_cast<const float4*>(Y + rs * LP)[p];
     __syncthreads();
     if constexpr (DFACC) {
-      for (int i = 0; i < nr; ++i) {
-        const float* yr = ys + i * LP;
+      int i = 0;
+      for (; i + 1 < nr; i += 2) {
+        const float* y0 = ys + i * LP;
+        const float* y1 = y0 + LP;
 #pragma unroll
-        for (int q = 0; q < GR_MAXP; ++q)
-          if (tid + q * GR_THREADS < P) df_mac(acc[q], yr[pa[q]], yr[pb[q]]);
+        for (int q = 0; q < GR_MAXP; ++q) {
+          df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
+          df_mac(acc2[q], y1[pa[q]], y1[pb[q]]);
+        }
+      }
+      if (i < nr) {
+        const float* y0 = ys + i * LP;
+#pragma unroll
+        for (int q = 0; q < GR_MAXP; ++q) df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
       }
     } else {
       int i = 0;
@@ -89,7 +101,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
 #pragma unroll
   for (int q = 0; q < GR_MAXP; ++q) {
     if (tid + q * GR_THREADS < P) {
-      const double v = df_value(acc[q]);
+      const double v = df_value(acc[q]) + df_value(acc2[q]);
       g[pa[q] * LP + pb[q]] = v;
       g[pb[q] * LP + pa[q]] = v;
     }
@@ -562,15 +574,16 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
                                                             int LP, int R, float* __restrict__ T,
                                                             float* __restrict__ Bk, float* __restrict__ Mblk,
                                                             int* __restrict__ rank, float tau) {
+  constexpr int RP = (RB + 3) / 4 * 4;  // T_k rows padded for 16-byte loads
   extern __shared__ __align__(16) float msm[];  // J x R
-  __shared__ __align__(16) float ts[EB * RB];
+  __shared__ __align__(16) float ts[EB * RP];
   __shared__ double red[MB1_THREADS / 32][RB];
   __shared__ double red2[MB1_THREADS / 32][RB];
   __shared__ float keep[RB];
   const int k = blockIdx.x, tid = threadIdx.x;
   float* t = T + (int64_t)k * LP * R;
-  for (int e = tid; e < EB * RB; e += MB1_THREADS) {
-    const int c = e / RB, r = e % RB;
+  for (int e = tid; e < EB * RP; e += MB1_THREADS) {
+    const int c = e / RP, r = e % RP;
     ts[e] = (r < R && c < ell) ? t[c * R + r] : 0.f;
   }
   __syncthreads();
@@ -578,22 +591,43 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
   float nrm[RB], csum[RB];
 #pragma unroll
   for (int r = 0; r < RB; ++r) nrm[r] = csum[r] = 0.f;
-  for (int j = tid; j < J; j += MB1_THREADS) {
-    float b[EB];
+  // two columns per thread (j and j + MB1_THREADS): every T_k value read from
+  // shared memory feeds two FMAs
+  for (int j = tid; j < J; j += 2 * MB1_THREADS) {
+    const int j2 = j + MB1_THREADS;
+    const bool has2 = j2 < J;
+    float b[EB], bb[EB];
 #pragma unroll
-    for (int c = 0; c < EB; ++c) b[c] = (c < ell) ? __ldg(b1 + (int64_t)c * Jp + j) : 0.f;
-    float o[RB];
+    for (int c = 0; c < EB; ++c) {
+      b[c] = (c < ell) ? __ldg(b1 + (int64_t)c * Jp + j) : 0.f;
+      bb[c] = (c < ell && has2) ? __ldg(b1 + (int64_t)c * Jp + j2) : 0.f;
+    }
+    float o[RP], oo[RP];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) o[r] = 0.f;
+    for (int r = 0; r < RP; ++r) o[r] = oo[r] = 0.f;
 #pragma unroll
-    for (int c = 0; c < EB; ++c)
+    for (int c = 0; c < EB; ++c) {
 #pragma unroll
-      for (int r = 0; r < RB; ++r) o[r] = fmaf(b[c], ts[c * RB + r], o[r]);
+      for (int q = 0; q < RP / 4; ++q) {
+        const float4 w = *reinterpret_cast<const float4*>(ts + c * RP + 4 * q);
+        o[4 * q] = fmaf(b[c], w.x, o[4 * q]);
+        o[4 * q + 1] = fmaf(b[c], w.y, o[4 * q + 1]);
+        o[4 * q + 2] = fmaf(b[c], w.z, o[4 * q + 2]);
+        o[4 * q + 3] = fmaf(b[c], w.w, o[4 * q + 3]);
+        oo[4 * q] = fmaf(bb[c], w.x, oo[4 * q]);
+        oo[4 * q + 1] = fmaf(bb[c], w.y, oo[4 * q + 1]);
+        oo[4 * q + 2] = fmaf(bb[c], w.z, oo[4 * q + 2]);
+        oo[4 * q + 3] = fmaf(bb[c], w.w, oo[4 * q + 3]);
+      }
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      if (r < R) msm[j * R + r] = o[r];
-      nrm[r] = fmaf(o[r], o[r], nrm[r]);
-      csum[r] += o[r];
+      if (r < R) {
+        msm[j * R + r] = o[r];
+        if (has2) msm[j2 * R + r] = oo[r];
+      }
+      nrm[r] = fmaf(o[r], o[r], fmaf(oo[r], oo[r], nrm[r]));
+      csum[r] += o[r] + oo[r];
     }
   }
 #pragma unroll
