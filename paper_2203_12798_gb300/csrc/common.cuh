@@ -57,6 +57,17 @@ __device__ inline void df_mac(DF& s, float a, float b) {
   s.lo += err + e;
 }
 __device__ inline double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+// Double-float a + b (TwoSum of the high parts, low parts added, renormalised).
+__device__ inline DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);
+  e += a.lo + b.lo;
+  DF r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
 
 // ------------------------------------------- warp-parallel small Cholesky ----
 // FP64 arithmetic runs at a small fraction of the FP32 rate on this part, so

@@ -409,11 +409,17 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
     for (int r = lane; r < R; r += 32) df_mac(ek, -2.f * wn[r], g3[r]);
     __syncwarp();
   }
-  // lane sums -> warp (hi, lo) in double, then per block
-  double ev = warp_sum(df_value(ek));
+  // lane sums -> warp -> block, as double-float sums in a fixed order (FP32 pipes)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF other;
+    other.hi = __shfl_xor_sync(0xffffffffu, ek.hi, o);
+    other.lo = __shfl_xor_sync(0xffffffffu, ek.lo, o);
+    ek = df_add(ek, other);
+  }
   if (lane == 0) {
-    ered[warp][0] = (float)ev;
-    ered[warp][1] = (float)(ev - (double)(float)ev);
+    ered[warp][0] = ek.hi;
+    ered[warp][1] = ek.lo;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -422,10 +428,10 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
     part[(int64_t)blockIdx.x * pstride + e] = s;
   }
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += (double)ered[w][0] + (double)ered[w][1];
-    part[(int64_t)blockIdx.x * pstride + RR] = (float)s;
-    part[(int64_t)blockIdx.x * pstride + RR + 1] = (float)(s - (double)(float)s);
+    DF s = {0.f, 0.f};
+    for (int w = 0; w < nw; ++w) s = df_add(s, DF{ered[w][0], ered[w][1]});
+    part[(int64_t)blockIdx.x * pstride + RR] = s.hi;
+    part[(int64_t)blockIdx.x * pstride + RR + 1] = s.lo;
   }
 }
 

@@ -577,8 +577,8 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
   constexpr int RP = (RB + 3) / 4 * 4;  // T_k rows padded for 16-byte loads
   extern __shared__ __align__(16) float msm[];  // J x R
   __shared__ __align__(16) float ts[EB * RP];
-  __shared__ double red[MB1_THREADS / 32][RB];
-  __shared__ double red2[MB1_THREADS / 32][RB];
+  __shared__ float red[MB1_THREADS / 32][RB];
+  __shared__ float red2[MB1_THREADS / 32][RB];
   __shared__ float keep[RB];
   const int k = blockIdx.x, tid = threadIdx.x;
   float* t = T + (int64_t)k * LP * R;
@@ -641,8 +641,9 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
   }
   __syncthreads();
   if (tid < 32) {
-    double sg[2] = {0.0, 0.0}, cs[2] = {0.0, 0.0};
-    double smax = 0.0;
+    // FP32 suffices: sigma_r to FP32 accuracy against the 1e-5 rank threshold
+    float sg[2] = {0.f, 0.f}, cs[2] = {0.f, 0.f};
+    float smax = 0.f;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = tid + 32 * h;
@@ -651,19 +652,19 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
           sg[h] += red[w][r];
           cs[h] += red2[w][r];
         }
-        sg[h] = sqrt(sg[h]);
-        if (r < R) smax = fmax(smax, sg[h]);
+        sg[h] = sqrtf(sg[h]);
+        if (r < R) smax = fmaxf(smax, sg[h]);
       }
     }
-    smax = warp_max_d(smax);
+    smax = warp_max(smax);
     int rk = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = tid + 32 * h;
       // sign rule: the right singular vector (column of C_k) has a non-negative sum
-      const bool kp = r < R && r < ell && sg[h] > (double)tau * smax && smax > 0.0;
-      if (r < RB) keep[r] = kp ? (cs[h] < 0.0 ? -1.f : 1.f) : 0.f;
-      if (r < R) Bk[(int64_t)k * R + r] = kp ? (float)sg[h] : 0.f;
+      const bool kp = r < R && r < ell && sg[h] > tau * smax && smax > 0.f;
+      if (r < RB) keep[r] = kp ? (cs[h] < 0.f ? -1.f : 1.f) : 0.f;
+      if (r < R) Bk[(int64_t)k * R + r] = kp ? sg[h] : 0.f;
       rk += kp;
     }
     rk = __reduce_add_sync(0xffffffffu, rk);

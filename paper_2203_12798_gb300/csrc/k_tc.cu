@@ -92,6 +92,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
 #pragma unroll
         for (int bx = 0; bx < 2 * S::HV; ++bx)
           tma_load_2d(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, (int)(r0 + c * PJ_BK));
-        tma_load_2d(sB + s * S::B, &tmQ, &full[s], (int)(p0 + c * PJ_BK), 0);
+        tma_load_3d(sB + s * S::B, &tmQ, &full[s], 0, 0, (int)(p0 / PJ_BK + c));
         inflight = true;
         if (++s == ST) {
           s = 0;
@@ -571,12 +578,17 @@ __global__ void k_omega_t16(const float* __restrict__ om, int Jpad, int LP, int 
 
 // Q1 rows (N x LP FP32) -> three exact-sum 16-bit parts, transposed to
 // (3 LPN) x Npad with every slice padded to a multiple of 64 rows (zeros).
+// Layout of the split: 64-row chunks of all 3 LPN columns stored contiguously,
+// element (p, c) at ((p / 64) 3 LPN + c) 64 + p % 64, so that one chunk (the B
+// operand of one projection stage) is a single contiguous 12 KB (LPN = 32) block.
 __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ poff, int K, int64_t Npad, int bf16, void* out) {
   const int k = blockIdx.y;
   const int64_t p0 = poff[k], p1 = poff[k + 1], r0 = off[k], nr = off[k + 1] - r0;
+  const int NSQ = 3 * LPN;
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = p - p0;
+    const int64_t cb = (p / PJ_BK) * NSQ * PJ_BK + (p % PJ_BK);  // element (p, 0)
     for (int c = 0; c < LPN; ++c) {
       const float qv = (i < nr && c < LP) ? Q[(r0 + i) * LP + c] : 0.f;
       if (bf16) {
@@ -584,19 +596,19 @@ __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int
         const float r1 = qv - __bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
         const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out);
-        o[(int64_t)c * Npad + p] = h;
-        o[(int64_t)(LPN + c) * Npad + p] = m;
-        o[(int64_t)(2 * LPN + c) * Npad + p] = l;
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + cb;
+        o[(int64_t)c * PJ_BK] = h;
+        o[(int64_t)(LPN + c) * PJ_BK] = m;
+        o[(int64_t)(2 * LPN + c) * PJ_BK] = l;
       } else {
         const __half h = __float2half_rn(qv);
         const float r1 = qv - __half2float(h);
         const __half m = __float2half_rn(r1);
         const __half l = __float2half_rn(r1 - __half2float(m));
-        __half* o = reinterpret_cast<__half*>(out);
-        o[(int64_t)c * Npad + p] = h;
-        o[(int64_t)(LPN + c) * Npad + p] = m;
-        o[(int64_t)(2 * LPN + c) * Npad + p] = l;
+        __half* o = reinterpret_cast<__half*>(out) + cb;
+        o[(int64_t)c * PJ_BK] = h;
+        o[(int64_t)(LPN + c) * PJ_BK] = m;
+        o[(int64_t)(2 * LPN + c) * PJ_BK] = l;
       }
     }
   }
@@ -627,6 +639,20 @@ static EncodeTiledFn encode_fn() {
 
 // 2-D tensor map of a row-major 16-bit matrix (rows x cols, row pitch
 // ld elements), box (bx cols, by rows), 128-byte swizzle, zero fill outside.
+// 3-D map over [nz][ny][nx] 16-bit elements stored contiguously, box {nx, ny, 1}.
+static bool make_map3(CUtensorMap* m, const void* base, bool bf16, uint64_t nx, uint64_t ny, uint64_t nz) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {nx, ny, nz};
+  cuuint64_t strides[2] = {nx * 2, nx * ny * 2};
+  cuuint32_t box[3] = {(cuuint32_t)nx, (cuuint32_t)ny, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t cols, uint64_t rows, uint64_t ld,
                      uint32_t bx, uint32_t by) {
   EncodeTiledFn fn = encode_fn();
@@ -679,8 +705,7 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
   const bool bf = dt == DPAR2_BF16;
   CUtensorMap mx, mq;
   if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, 64, tc::PJ_BK)) return false;
-  if (!make_map(&mq, Qs, bf, (uint64_t)Npad, (uint64_t)(3 * LPN), (uint64_t)Npad, tc::PJ_BK, (uint32_t)(3 * LPN)))
-    return false;
+  if (!make_map3(&mq, Qs, bf, (uint64_t)tc::PJ_BK, (uint64_t)(3 * LPN), (uint64_t)(Npad / tc::PJ_BK))) return false;
   const int64_t nitems = (int64_t)K * nJb;
   const int grid = (int)std::min<int64_t>(nitems, num_sms);
   if (LPN == 32) {
