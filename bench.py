@@ -31,7 +31,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DPar2 time-to-fit (s) & stage-1 HBM GB/s vs peak; chosen vs plain at Δfit≤1e-3"
-WORKLOAD = dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=10, q=0, seed=1002, iters=32)
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# stage-1 kernels on this workload, from one ncu capture (profiles/), valid
+# only for the kernel source they were taken on (sha1 of k_tc.cu).
+MEASURED_TRAFFIC = {}
+WORKLOADS = {
+    # FMA-shaped spectrogram magnitudes (the default, headline workload)
+    "spectrogram": dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=10, q=0, seed=1002, iters=32),
+    # US-Stock-shaped skewed-length series: I_k log-uniform, z-scored columns, AR(1) rows
+    "skewed": dict(name="skewed", K=4742, Imin=100, Imax=7883, J=88, R=20, p=10, q=0, seed=1003, iters=32),
+    # Urban-shaped rank sweep (R set with --R)
+    "ranksweep": dict(name="ranksweep", K=8455, Imin=32, Imax=174, J=2049, R=10, p=10, q=0, seed=1004, iters=32),
+}
+WORKLOAD = WORKLOADS["spectrogram"]
 
 
 def parse():
@@ -41,12 +54,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "f32"])
-    ap.add_argument("--K", type=int, default=WORKLOAD["K"])
+    ap.add_argument("--K", type=int, default=None, help="slices (default: the workload's)")
+    ap.add_argument("--workload", default="spectrogram", choices=sorted(WORKLOADS))
+    ap.add_argument("--R", type=int, default=None, help="rank (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--with-plain", action="store_true", help="also time the plain form (FP32 X, per-slice launches)")
     ap.add_argument("--cpu-slices", type=int, default=400)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--learned", action="store_true",
+                    help="learned-sketch leg: train Omega on 2000 slices, compare held-out fits with Gaussian q=0,1,2")
+    ap.add_argument("--lr", type=float, default=0.05)
     return ap.parse_args()
 
 
@@ -107,7 +125,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- CPU baseline ----
-def cpu_oracle_time(n_slices: int, seed: int = 1002):
+def cpu_oracle_time(n_slices: int, seed: int = None):
     """Oracle (FP64 numpy) compress + 32 iterations + direct fitness on a
     sample of n_slices slices of the same workload; returns (seconds for the
     sample, seconds extrapolated to K slices, cores)."""
@@ -117,8 +135,8 @@ def cpu_oracle_time(n_slices: int, seed: int = 1002):
     from oracle import dpar2 as od
 
     w = WORKLOAD
-    d = synth.spectrogram_like(K=n_slices, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=seed,
-                               out_dtype=__import__("torch").bfloat16)
+    seed = w["seed"] if seed is None else seed
+    d = generate(dict(w, seed=seed), n_slices, device="cpu", out_dtype=__import__("torch").bfloat16)
     X = d["X"].double().numpy()
     off = d["offsets"].tolist()
     Xs = [X[off[k]:off[k + 1]] for k in range(n_slices)]
@@ -155,10 +173,25 @@ def reference_arm(args):
                       "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def measured_traffic(kernel: str, args):
+    """ncu DRAM bytes per launch of `kernel` when they were taken on the current
+    k_tc.cu and this workload, else None."""
+    import hashlib
+
+    t = MEASURED_TRAFFIC.get(kernel)
+    if not t or args.K != WORKLOAD["K"] or args.dtype != "bf16":
+        return None
+    src = open(os.path.join(ROOT, "paper_2203_12798_gb300", "csrc", "k_tc.cu"), "rb").read()
+    return t["bytes"] if hashlib.sha1(src).hexdigest() == t["k_tc_sha1"] else None
+
+
 def workload_config(args):
     w = WORKLOAD
-    return {"workload": f"spectrogram-like |PARAFAC2+noise| K={args.K} I_k~U{{{w['Imin']}..{w['Imax']}}} "
-                        f"J={w['J']} R={w['R']} p={w['p']} q={w['q']} {w['iters']} ALS iters",
+    kind = {"spectrogram": "spectrogram-like |PARAFAC2+noise|", "ranksweep": "spectrogram-like |PARAFAC2+noise|",
+            "skewed": "skewed-length z-scored AR(1) + PARAFAC2 series"}[w["name"]]
+    dist = f"I_k~logU[{w['Imin']},{w['Imax']}]" if w["name"] == "skewed" else f"I_k~U{{{w['Imin']}..{w['Imax']}}}"
+    return {"workload": f"{kind} K={args.K} {dist} J={w['J']} R={w['R']} p={w['p']} q={w['q']} "
+                        f"{w['iters']} ALS iters",
             "K": args.K, "J": w["J"], "R": w["R"], "p": w["p"], "q": w["q"], "iters": w["iters"],
             "x_dtype": args.dtype, "l2": "inputs larger than L2 (X > 129 MB), no flush",
             "parallelism": "single GPU" if args.gpus == 1 else f"{args.gpus} independent replicas"}
@@ -184,8 +217,7 @@ def main_ours(args):
     tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}[args.dtype]
     es = torch.empty((), dtype=tdt).element_size()
     ld = (w["J"] + 16 // es - 1) // (16 // es) * (16 // es)
-    d = synth.spectrogram_like(K=args.K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"],
-                               device="cuda", out_dtype=tdt, ld=ld)
+    d = generate(w, args.K, device="cuda", out_dtype=tdt, ld=ld)
     X, off = d["X"], d["offsets"]
     N = int(off[-1])
     ctx = api.Context(local)
@@ -313,7 +345,7 @@ def main_ours(args):
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": workload_config(args),
                "roofline": {"bound": "hbm", "kernel": f"stage-1 {dom} pass", "achieved": achieved, "peak": peak,
-                            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                            "unit": "GB/s", "frac": achieved / peak, "traffic": measured_traffic(dom, args),
                             "peak_source": peak_src,
                             "algorithmic_bytes_per_launch": dom_bytes},
                "stage1_gbs": stage1_gbs, "stage1_frac": stage1_gbs / peak,
@@ -328,9 +360,142 @@ def main_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------- learned sketch ----
+LEARNED = dict(Ktr=2000, Kev=8000, Imin=100, Imax=704, J=2049, R=20, p=10, seed=2000, iters=32)
+
+
+def main_learned(args):
+    """Train a test matrix Omega (J x 30) on 2000 spectrogram-like slices with
+    the library's forward / backward kernels (Adam), timing the training step;
+    then compress + fit 8000 held-out slices of the same generator instance
+    with the trained Omega (q = 0) and with the Gaussian one (q = 0, 1, 2)."""
+    import torch
+
+    import paper_2203_12798_gb300 as pkg
+    import synth
+    from paper_2203_12798_gb300.api import _DevPtr
+    from paper_2203_12798_gb300.sketch import SketchLoss, gaussian_omega
+
+    torch.cuda.set_device(0)
+    pkg.build()
+    api = pkg.load()
+    w = LEARNED
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}[args.dtype]
+    es = torch.empty((), dtype=tdt).element_size()
+    J, R, ell = w["J"], w["R"], w["R"] + w["p"]
+    ld = (J + 16 // es - 1) // (16 // es) * (16 // es)
+    d = synth.spectrogram_like(K=w["Ktr"] + w["Kev"], Imin=w["Imin"], Imax=w["Imax"], J=J, R=R, seed=w["seed"],
+                               device="cuda", out_dtype=tdt, ld=ld)
+    off = d["offsets"]
+    r = int(off[w["Ktr"]])
+    Xtr, otr = d["X"][:r], off[:w["Ktr"] + 1]
+    Xev, oev = d["X"][r:], off[w["Ktr"]:] - r
+    ctx = api.Context(0)
+    om_g = gaussian_omega(ctx, J, ell, seed=0)
+    om = om_g.clone().requires_grad_(True)
+    opt = torch.optim.Adam([om], lr=args.lr)
+
+    def train_step():
+        opt.zero_grad(set_to_none=True)
+        loss = SketchLoss.apply(om, Xtr, otr, ctx)
+        loss.backward()
+        opt.step()
+        return loss
+
+    losses = []
+    for _ in range(args.warmup):
+        losses.append(float(train_step()))
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            losses.append(float(train_step()))
+        e1.record()
+        torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / args.steps
+    # forward and backward alone (library stream, CUDA events around each call)
+    f0, f1, b1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    f0.record()
+    ctx.sketch_loss_fwd(Xtr, otr, om.detach().contiguous())
+    f1.record()
+    ctx.sketch_loss_bwd(1.0)
+    b1.record()
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = f0.elapsed_time(f1), f1.elapsed_time(b1)
+    xbytes = int(off[w["Ktr"]]) * J * es
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = 4 * xbytes / (step_ms * 1e-3) / 1e9
+
+    om_t = om.detach().contiguous()
+    held = {"loss_gaussian": ctx.sketch_loss_fwd(Xev, oev, om_g), "loss_learned": ctx.sketch_loss_fwd(Xev, oev, om_t)}
+
+    def stage1_residual(comp):
+        v = comp.view()
+        bk = torch.empty(v.K, v.R, device="cuda")
+        bk.view(-1).view(torch.uint8).copy_(_DevPtr(v.Bk, bk.numel() * 4).as_tensor("cuda"))
+        xn = torch.empty(v.K, dtype=torch.float64, device="cuda")
+        xn.view(torch.uint8).copy_(_DevPtr(v.xnorm2, xn.numel() * 8).as_tensor("cuda"))
+        return float((1.0 - (bk.double() ** 2).sum(1) / xn).mean())
+
+    forms = {}
+    for name, o, q in [("learned_q0", om_t, 0), ("gaussian_q0", om_g, 0), ("gaussian_q1", om_g, 1),
+                       ("gaussian_q2", om_g, 2)]:
+        ts = []
+        for i in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            comp = ctx.compress(Xev, oev, R=R, p=w["p"], q=q, omega=o, J=J)
+            res = ctx.fit(comp, max_iter=w["iters"])
+            torch.cuda.synchronize()
+            if i:
+                ts.append(time.perf_counter() - t0)
+            if i == 3:
+                forms[name] = {"s": statistics.median(ts), "fitness": res.fitness,
+                               "stage1_residual": stage1_residual(comp)}
+            comp.free()
+    fl = forms["learned_q0"]["fitness"]
+    match = next((n for n in ("gaussian_q0", "gaussian_q1", "gaussian_q2") if forms[n]["fitness"] >= fl - 1e-3), None)
+    out = {"metric": "learned sketch: training step (s) and held-out time-to-fit vs Gaussian q=0,1,2",
+           "value": step_ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": step_ms, "higher_is_better": False, "dtype": args.dtype, "data": "synthetic",
+           "config": {"workload": f"spectrogram-like |PARAFAC2+noise| train K={w['Ktr']} / held-out K={w['Kev']} "
+                                  f"I_k~U{{{w['Imin']}..{w['Imax']}}} J={J} R={R} l={ell} (one generator instance)",
+                      "optimizer": f"Adam lr={args.lr}", "x_dtype": args.dtype},
+           "train": {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "loss_first": losses[0], "loss_last": losses[-1],
+                     "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+                     "algorithmic_bytes_per_step": 4 * xbytes, "steps_total": len(losses)},
+           "held_out": held, "fits": forms, "gaussian_form_at_learned_fitness": match,
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
+def generate(w, K, device="cuda", out_dtype=None, ld=None):
+    """The workload's synthetic slices (same generator, seed and shapes)."""
+    import synth
+
+    if w["name"] == "skewed":
+        return synth.skewed_series(K=K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"],
+                                   device=device, out_dtype=out_dtype, ld=ld)
+    return synth.spectrogram_like(K=K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"],
+                                  device=device, out_dtype=out_dtype, ld=ld)
+
+
 if __name__ == "__main__":
     a = parse()
+    WORKLOAD = dict(WORKLOADS[a.workload])
+    if a.R is not None:
+        WORKLOAD["R"] = a.R
+    if a.K is None:
+        a.K = WORKLOAD["K"]
     if a.impl == "reference":
         reference_arm(a)
+    elif a.learned:
+        main_learned(a)
     else:
         main_ours(a)

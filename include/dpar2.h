@@ -248,17 +248,37 @@ DPAR2_API size_t dpar2_comp_device_bytes(const dpar2_comp* comp);
 DPAR2_API dpar2_status dpar2_comp_view_get(const dpar2_comp* comp, dpar2_comp_view* view);
 DPAR2_API void dpar2_comp_free(dpar2_comp* comp);
 
-/* Learned sketch (range-finder loss of a trainable test matrix Omega):
- *   L(Omega) = (1/K) sum_k ||X_k - Y_k Y_k^+ X_k||_F^2 / ||X_k||_F^2,  Y_k = X_k Omega,
- * the quantity Alg. 1's range finder leaves out of each slice.
- * dpar2_sketch_loss_fwd computes L (host double) and saves what the backward
- * pass needs in the context; dpar2_sketch_loss_bwd writes dL/dOmega
- * (device J x l float32) for the same X and Omega, scaled by grad_scale.
- *   X, row_offsets, ldx, dtype as for dpar2_compress; omega device J x l, l <= 64. */
+/* Learned sketch (range-finder loss of a trainable test matrix Omega).
+ *
+ * Alg. 1 replaces slice X_k by Q_k Q_k^T X_k, Q_k an orthonormal basis of the
+ * sketch Y_k = X_k Omega; the loss of Omega is what it leaves out:
+ *   L(Omega) = (1/K) sum_k ||X_k - Y_k Y_k^+ X_k||_F^2 / ||X_k||_F^2
+ *            = (1/K) sum_k (||X_k||^2 - tr(G_k^+ Y_k^T X_k X_k^T Y_k)) / ||X_k||^2,  G_k = Y_k^T Y_k
+ * (the paper draws Omega at random; training it is this library's extension).
+ *
+ * dpar2_sketch_loss_fwd: X, K, J, row_offsets (host, K + 1), ldx and dtype as
+ *   for dpar2_compress; omega device J x l row-major FP32, 1 <= l <= min(J, 64).
+ *   For 16-bit X, omega is rounded to X's type before use (as dpar2_compress
+ *   rounds its test matrix).  Writes L to *loss (host) and keeps in the
+ *   context what the backward pass needs (the sketch's QR factors, Q_k^T X_k,
+ *   ||X_k||^2).  X must stay unchanged and valid until the matching backward.
+ *   Slices whose sketch is rank deficient use the pseudo-inverse (the
+ *   columns CholeskyQR2 drops).  Errors: INVALID_ARG / SHAPE before any launch.
+ * dpar2_sketch_loss_bwd: grad_omega (device J x l FP32, caller-owned) <-
+ *   grad_scale * dL/dOmega at the omega of the last forward on this context
+ *   (for 16-bit X: at the rounded omega).  INVALID_ARG without a preceding
+ *   successful forward.  Two more streams of X (four per training step). */
 DPAR2_API dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X,
                                    int64_t ldx, dpar2_dtype dtype, const float* omega, int ell,
                                    double* loss, void* stream);
 DPAR2_API dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, float* grad_omega, void* stream);
+
+/* In place: A (device rows x cols row-major FP32, 1 <= cols <= min(rows, 64))
+ * <- A R^-1, an orthonormal basis of its column space by CholeskyQR2 (the QR
+ * of Alg. 1's sketch; numerically dependent columns come out zero).  Used to
+ * re-normalise a learned test matrix, whose loss depends on its column space
+ * only.  Errors: INVALID_ARG (null A), SHAPE. */
+DPAR2_API dpar2_status dpar2_orthonormalize(dpar2_ctx* ctx, int64_t rows, int cols, float* A, void* stream);
 
 #ifdef __cplusplus
 }

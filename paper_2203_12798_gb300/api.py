@@ -67,6 +67,7 @@ SIGNATURES = {
     "dpar2_sketch_loss_fwd": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP,
                                              I64, ctypes.c_int, VP, ctypes.c_int, DP, VP]),
     "dpar2_sketch_loss_bwd": (ctypes.c_int, [VP, ctypes.c_double, VP, VP]),
+    "dpar2_orthonormalize": (ctypes.c_int, [VP, I64, ctypes.c_int, VP, VP]),
     "dpar2_upload_rows": (ctypes.c_int, [VP, VP, I64, ctypes.c_int, ctypes.c_int, VP, I64, VP]),
     "dpar2_scratch": (ctypes.c_int, [VP, ctypes.c_char_p, ctypes.POINTER(VP), ctypes.POINTER(ctypes.c_size_t)]),
     "dpar2_set_timing": (ctypes.c_int, [VP, ctypes.c_int]),
@@ -214,6 +215,41 @@ class Context:
         self._check(lib().dpar2_reconstruct_error(self._h, comp._h, _ptr(X), ldx, dt, _ptr(H), _ptr(V), _ptr(W),
                                                   _ptr(Upol), ctypes.byref(sq), ctypes.byref(fit), _stream()))
         return sq.value, fit.value
+
+    # ------------------------------------------------------------- learned sketch
+    def sketch_loss_fwd(self, X: torch.Tensor, offsets, omega: torch.Tensor) -> float:
+        """Range-finder loss (1/K) sum_k ||X_k - Y_k Y_k^+ X_k||^2 / ||X_k||^2 of
+        omega (J x l, float32, CUDA; X's first J columns are the slices' columns);
+        keeps what the backward pass needs."""
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        assert omega.is_cuda and omega.dtype == torch.float32 and omega.is_contiguous()
+        J = omega.shape[0]
+        assert X.shape[1] >= J
+        off = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
+        offp = ctypes.cast(off.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+        loss = ctypes.c_double()
+        self._check(lib().dpar2_sketch_loss_fwd(self._h, off.numel() - 1, J, offp, _ptr(X), X.stride(0),
+                                                _DT[X.dtype], _ptr(omega), omega.shape[1], ctypes.byref(loss),
+                                                _stream()))
+        self._sk_gen = getattr(self, "_sk_gen", 0) + 1
+        self._sk_shape = tuple(omega.shape)
+        return loss.value
+
+    def sketch_loss_bwd(self, grad_scale: float = 1.0, out=None) -> torch.Tensor:
+        """grad_scale * dL/dOmega for the X and omega of the last sketch_loss_fwd."""
+        shape = getattr(self, "_sk_shape", None)
+        if shape is None:
+            raise RuntimeError("sketch_loss_bwd needs a sketch_loss_fwd first")
+        out = torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}") if out is None else out
+        self._check(lib().dpar2_sketch_loss_bwd(self._h, float(grad_scale), _ptr(out), _stream()))
+        return out
+
+    def orthonormalize(self, A: torch.Tensor) -> torch.Tensor:
+        """In place: A (rows x cols, float32, CUDA) <- an orthonormal basis of
+        its column space (CholeskyQR2, A = Q R with R upper triangular)."""
+        assert A.is_cuda and A.dtype == torch.float32 and A.is_contiguous() and A.dim() == 2
+        self._check(lib().dpar2_orthonormalize(self._h, A.shape[0], A.shape[1], _ptr(A), _stream()))
+        return A
 
     def reconstruct_error_noalloc(self, comp: "Compressed", H, V, W, Upol):
         """Identity-mode error with the library's fixed device scratch (no device

@@ -42,12 +42,27 @@ T* wsget(dpar2_ctx* ctx, const char* name, size_t count) {
   return static_cast<T*>(p);
 }
 
-void alloc(dp2::DevBuf& b, size_t bytes) {
-  if (b.p) cudaFree(b.p);
+inline cudaStream_t work_stream(dpar2_ctx* ctx) {
+  return reinterpret_cast<cudaStream_t>(ctx->ws["__work_stream"].p);
+}
+
+// Buffer of a compression object: from the owner's stream-ordered pool on its
+// work stream (no device-wide synchronisation, memory reused across objects),
+// else plain cudaMalloc.
+void release(dpar2_comp* c, dp2::DevBuf& b) {
+  if (!b.p) return;
+  if (c->owner && c->owner->pool) cudaFreeAsync(b.p, work_stream(c->owner));
+  else cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
+}
+
+void alloc(dpar2_comp* c, dp2::DevBuf& b, size_t bytes) {
+  release(c, b);
   if (bytes == 0) return;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = (c->owner && c->owner->pool)
+                      ? cudaMallocFromPoolAsync(&b.p, bytes, c->owner->pool, work_stream(c->owner))
+                      : cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
@@ -56,13 +71,60 @@ void alloc(dp2::DevBuf& b, size_t bytes) {
   b.bytes = bytes;
 }
 
+// Frees what the context holds; the work stream and the pool stay while
+// compression objects made by it are alive (the last one's free finishes).
+void ctx_release(dpar2_ctx* ctx) {
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->ws) {
+    if (!kv.second.p || kv.first == "__work_stream") continue;
+    if (kv.first == "__event") cudaEventDestroy(reinterpret_cast<cudaEvent_t>(kv.second.p));
+    else cudaFree(kv.second.p);
+    kv.second.p = nullptr;
+  }
+  for (int i = 0; i < 2 * DPAR2_NUM_PHASES; ++i)
+    if (ctx->tev[i]) cudaEventDestroy(ctx->tev[i]), ctx->tev[i] = nullptr;
+  if (ctx->d_status) cudaFree(ctx->d_status), ctx->d_status = nullptr;
+  if (ctx->h_status) cudaFreeHost(ctx->h_status), ctx->h_status = nullptr;
+  if (ctx->hstage) cudaFreeHost(ctx->hstage), ctx->hstage = nullptr;
+  if (ctx->live_comps > 0) {
+    ctx->closing = true;
+    return;
+  }
+  if (ctx->ws["__work_stream"].p) cudaStreamDestroy(work_stream(ctx));
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+}
+
 size_t dtype_size(dpar2_dtype dt) { return dt == DPAR2_F32 ? 4 : 2; }
+
+// n int64 values host -> device through the context's pinned staging area, so
+// that the copy is asynchronous (a copy from pageable memory waits for the
+// stream first).  The area grows (after draining the stream) when a call needs more.
+void h2d_i64(dpar2_ctx* ctx, int64_t* dst, const int64_t* src, size_t n, cudaStream_t s) {
+  if (ctx->hstage_used + n > ctx->hstage_cap) {
+    CK(cudaStreamSynchronize(s));
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
+    ctx->hstage = nullptr;
+    ctx->hstage_cap = std::max<size_t>(2 * (ctx->hstage_used + n), 1 << 16);
+    ctx->hstage_used = 0;
+    if (cudaMallocHost(&ctx->hstage, ctx->hstage_cap * sizeof(int64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->hstage = nullptr;
+      ctx->hstage_cap = 0;
+      throw Fail{DPAR2_ERR_OOM, "pinned host allocation failed"};
+    }
+  }
+  int64_t* h = ctx->hstage + ctx->hstage_used;
+  ctx->hstage_used += n;
+  std::memcpy(h, src, n * sizeof(int64_t));
+  CK(cudaMemcpyAsync(dst, h, n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+}
 
 // Runs `body` with the context's device current and a private work stream
 // ordered after `user` work; converts failures into status codes.
 template <typename F>
 dpar2_status guarded(dpar2_ctx* ctx, void* user_stream, F&& body) {
-  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!ctx || ctx->closing) return DPAR2_ERR_INVALID_ARG;
   ctx->err.clear();
   int prev = -1;
   cudaGetDevice(&prev);
@@ -74,6 +136,7 @@ dpar2_status guarded(dpar2_ctx* ctx, void* user_stream, F&& body) {
     CK(cudaEventRecord(ev, us));
     CK(cudaStreamWaitEvent(work, ev, 0));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), work));
+    ctx->hstage_used = 0;
     body(work);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, work));
@@ -201,8 +264,7 @@ size_t dpar2_comp::device_bytes() const {
 }
 
 dpar2_comp::~dpar2_comp() {
-  for (dp2::DevBuf* b : {&offsets, &A, &Bk, &M, &D, &E, &Ft, &xnorm2, &rank1, &DtD})
-    if (b->p) cudaFree(b->p);
+  for (dp2::DevBuf* b : {&offsets, &A, &Bk, &M, &D, &E, &Ft, &xnorm2, &rank1, &DtD}) release(this, *b);
 }
 
 extern "C" {
@@ -237,7 +299,7 @@ dpar2_status dpar2_create(dpar2_ctx** out, int device) {
   cudaStream_t work;
   cudaEvent_t ev;
   if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, 64) != cudaSuccess ||  // status word + pinned scalars
       cudaStreamCreateWithFlags(&work, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -246,6 +308,18 @@ dpar2_status dpar2_create(dpar2_ctx** out, int device) {
     return DPAR2_ERR_CUDA;
   }
   for (int i = 0; i < 2 * DPAR2_NUM_PHASES; ++i) cudaEventCreate(&ctx->tev[i]);
+  cudaMemPoolProps pp = {};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.handleTypes = cudaMemHandleTypeNone;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = device;
+  if (cudaMemPoolCreate(&ctx->pool, &pp) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // freed buffers stay in the pool for the next objects
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    ctx->pool = nullptr;
+  }
   ctx->ws["__work_stream"].p = reinterpret_cast<void*>(work);
   ctx->ws["__event"].p = reinterpret_cast<void*>(ev);
   *out = ctx;
@@ -254,22 +328,11 @@ dpar2_status dpar2_create(dpar2_ctx** out, int device) {
 }
 
 void dpar2_destroy(dpar2_ctx* ctx) {
-  if (!ctx) return;
+  if (!ctx || ctx->closing) return;
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
-  for (auto& kv : ctx->ws) {
-    if (!kv.second.p) continue;
-    if (kv.first == "__work_stream") cudaStreamDestroy(reinterpret_cast<cudaStream_t>(kv.second.p));
-    else if (kv.first == "__event") cudaEventDestroy(reinterpret_cast<cudaEvent_t>(kv.second.p));
-    else cudaFree(kv.second.p);
-  }
-  for (int i = 0; i < 2 * DPAR2_NUM_PHASES; ++i)
-    if (ctx->tev[i]) cudaEventDestroy(ctx->tev[i]);
-  if (ctx->d_status) cudaFree(ctx->d_status);
-  if (ctx->h_status) cudaFreeHost(ctx->h_status);
-  delete ctx;
+  ctx_release(ctx);
   if (prev >= 0) cudaSetDevice(prev);
 }
 
@@ -381,6 +444,8 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     int64_t maxI = 0;
     for (int k = 0; k < K; ++k) maxI = std::max<int64_t>(maxI, row_offsets[k + 1] - row_offsets[k]);
     comp = new dpar2_comp();
+    comp->owner = ctx;
+    ++ctx->live_comps;
     comp->K = K;
     comp->J = J;
     comp->R = R;
@@ -389,18 +454,18 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     comp->N = N;
     comp->maxI = maxI;
     comp->h_offsets.assign(row_offsets, row_offsets + K + 1);
-    alloc(comp->offsets, (K + 1) * sizeof(int64_t));
-    alloc(comp->A, (size_t)N * R * 4);
-    alloc(comp->Bk, (size_t)K * R * 4);
-    alloc(comp->M, (size_t)K * J * R * 4);
-    alloc(comp->D, (size_t)J * R * 4);
-    alloc(comp->E, (size_t)R * 4);
-    alloc(comp->Ft, (size_t)K * R * R * 4);
-    alloc(comp->xnorm2, (size_t)K * 8);
-    alloc(comp->rank1, (size_t)K * 4);
-    alloc(comp->DtD, (size_t)R * R * 8);
+    alloc(comp, comp->offsets, (K + 1) * sizeof(int64_t));
+    alloc(comp, comp->A, (size_t)N * R * 4);
+    alloc(comp, comp->Bk, (size_t)K * R * 4);
+    alloc(comp, comp->M, (size_t)K * J * R * 4);
+    alloc(comp, comp->D, (size_t)J * R * 4);
+    alloc(comp, comp->E, (size_t)R * 4);
+    alloc(comp, comp->Ft, (size_t)K * R * R * 4);
+    alloc(comp, comp->xnorm2, (size_t)K * 8);
+    alloc(comp, comp->rank1, (size_t)K * 4);
+    alloc(comp, comp->DtD, (size_t)R * R * 8);
     int64_t* d_off = static_cast<int64_t*>(comp->offsets.p);
-    CK(cudaMemcpyAsync(d_off, row_offsets, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    h2d_i64(ctx, d_off, row_offsets, (K + 1), s);
     const size_t es = dtype_size(dtype);
 
     // ---- test matrix Omega (Alg. 1, "generate a Gaussian test matrix") ----
@@ -446,13 +511,57 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     tend(ctx, s, DPAR2_PH_SKETCH);
     tbegin(ctx, s, DPAR2_PH_QR);
     cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
+    // tensor-core projection operands: Q1 split into three exact-sum 16-bit
+    // parts, slices padded to 64 rows; one partial ||X_k||^2 per (slice,
+    // column block, norm warp)
+    std::vector<int64_t> hp, htoff;
+    int64_t maxPad = 0;
+    int64_t* d_poff = nullptr;
+    void* Qs = nullptr;
+    double* xp = nullptr;
+    const int nJb_tc = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+    if (use_tc) {
+      hp.assign(K + 1, 0);
+      for (int k = 0; k < K; ++k) {
+        const int64_t pk = round_up64(row_offsets[k + 1] - row_offsets[k], 64);
+        hp[k + 1] = hp[k] + pk;
+        maxPad = std::max(maxPad, pk);
+      }
+      d_poff = wsget<int64_t>(ctx, "poff", (size_t)K + 1);
+      h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
+      Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * hp[K]);
+      xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
+    }
     // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
+    int64_t* d_toff = nullptr;
+    if (use_tc && opt->q > 0) {
+      htoff.assign(K + 1, 0);
+      for (int k = 0; k < K; ++k) htoff[k + 1] = htoff[k] + (row_offsets[k + 1] - row_offsets[k] + 127) / 128;
+      d_toff = wsget<int64_t>(ctx, "toff", (size_t)K + 1);
+      h2d_i64(ctx, d_toff, htoff.data(), (K + 1), s);
+    }
     for (int it = 0; it < opt->q; ++it) {
-      k_apply_m2<<<dim3((unsigned)((maxI + 127) / 128), K), 128, 0, s>>>(Y, d_off, LP, M2);
-      launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, nullptr, nullptr, s);
-      float* omk = wsget<float>(ctx, "omk", (size_t)K * Jpad * LP);
-      k_b1_to_omk<<<4096, 256, 0, s>>>(B1, K, ell, LP, J, Jp, Jpad, omk);
-      launch_sketch_generic_per_slice(X, dtype, ldx, d_off, K, (int)maxI, J, omk, Jpad, LP, Y, s);
+      if (use_tc) {
+        // B1 = Q1^T X, then Y_k = X_k B1_k^T on the tensor cores: X_k X_k^T Q_k =
+        // X_k B1_k^T M2_k up to the upper-triangular M2_k (and the power-of-two
+        // row scales of the operand), which leave the next CholeskyQR2's Q unchanged
+        launch_qsplit(Y, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+        bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, B1, xp, nJb_tc, true,
+                                    ctx->num_sms, ctx->d_status, s);
+        require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+        void* Ms = wsget<uint16_t>(ctx, "Ms", (size_t)K * 3 * LPN * Jpad);
+        launch_sl_rowsplit(B1, K, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr,
+                           wsget<float>(ctx, "Ms_scale", (size_t)K * LP), s);
+        ok = launch_sketch_seg_tc(X, dtype, ldx, N, J, d_off, d_toff, htoff[K], K, Ms, Jpad, LPN, LP, Y,
+                                  ctx->num_sms, ctx->d_status, s);
+        require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+      } else {
+        k_apply_m2<<<dim3((unsigned)((maxI + 127) / 128), K), 128, 0, s>>>(Y, d_off, LP, M2);
+        launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, nullptr, nullptr, s);
+        float* omk = wsget<float>(ctx, "omk", (size_t)K * Jpad * LP);
+        k_b1_to_omk<<<4096, 256, 0, s>>>(B1, K, ell, LP, J, Jp, Jpad, omk);
+        launch_sketch_generic_per_slice(X, dtype, ldx, d_off, K, (int)maxI, J, omk, Jpad, LP, Y, s);
+      }
       cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
     }
 
@@ -461,25 +570,10 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     int nJb_used = nJb;
     bool projected = false;
     if (use_tc) {
-      // Q1 split into three exact-sum 16-bit parts, slices padded to 64 rows
-      std::vector<int64_t> hp(K + 1, 0);
-      int64_t maxPad = 0;
-      for (int k = 0; k < K; ++k) {
-        const int64_t pk = round_up64(row_offsets[k + 1] - row_offsets[k], 64);
-        hp[k + 1] = hp[k] + pk;
-        maxPad = std::max(maxPad, pk);
-      }
       const int64_t Npad = hp[K];
-      int64_t* d_poff = wsget<int64_t>(ctx, "poff", (size_t)K + 1);
-      CK(cudaMemcpyAsync(d_poff, hp.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-      void* Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * Npad);
       launch_qsplit(Y, LP, LPN, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
-      const int nJb_tc = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
-      // one partial ||X_k||^2 per (slice, column block, norm warp)
-      double* xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
-      CK(cudaStreamSynchronize(s));  // hp must outlive the pageable copy
       tbegin(ctx, s, DPAR2_PH_PROJECT);
-      projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, LPN, LP, B1, xp, nJb_tc,
+      projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, LPN, LP, B1, xp, nJb_tc, true,
                                     ctx->num_sms, ctx->d_status, s);
       if (projected) {
         xpart = xp;
@@ -529,7 +623,7 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
     int64_t* off2 = wsget<int64_t>(ctx, "off2", 4);
     const int64_t h_off2[4] = {0, (int64_t)J, 0, KR};
-    CK(cudaMemcpyAsync(off2, h_off2, sizeof(h_off2), cudaMemcpyHostToDevice, s));
+    h2d_i64(ctx, off2, h_off2, sizeof(h_off2) / sizeof(int64_t), s);
     float* M2s = wsget<float>(ctx, "M2s", (size_t)LP * LP);
     cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
     for (int it = 0; it < opt->q; ++it) {
@@ -565,12 +659,11 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     tend(ctx, s, DPAR2_PH_STAGE2);
     tend(ctx, s, DPAR2_PH_COMPRESS);
     if (opt->flags & DPAR2_FLAG_DROP_M) {
-      CK(cudaStreamSynchronize(s));
-      alloc(comp->M, 0);
+      alloc(comp, comp->M, 0);  // stream-ordered after the kernels that read it
     }
   });
   if (st != DPAR2_OK) {
-    delete comp;
+    if (comp) dpar2_comp_free(comp);
     return st;
   }
   *out = comp;
@@ -645,8 +738,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         CK(cudaStreamEndCapture(s, &g));
         CK(cudaGraphInstantiate(&ge, g, 0));
         CK(cudaGraphLaunch(ge, s));
-        CK(cudaStreamSynchronize(s));
-        cudaGraphExecDestroy(ge);
+        cudaGraphExecDestroy(ge);  // freed when the launch completes
         cudaGraphDestroy(g);
       } else {
         for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
@@ -671,7 +763,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     // outputs: V = D CV (Lemma 2 keeps V in span(D)), U_k = A_k Upol_k H
     int64_t* off2 = wsget<int64_t>(ctx, "off_fit", 2);
     const int64_t h2[2] = {0, (int64_t)J};
-    CK(cudaMemcpyAsync(off2, h2, sizeof(h2), cudaMemcpyHostToDevice, s));
+    h2d_i64(ctx, off2, h2, sizeof(h2) / sizeof(int64_t), s);
     launch_seg_product(b.D, R, R, b.CV, 0, R, V, R, off2, 1, J, s);
     if (U) {
       float* Tk = wsget<float>(ctx, "Tk", (size_t)K * RR);
@@ -714,15 +806,20 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
     return DPAR2_ERR_INVALID_ARG;
   }
   if (X) {
-    ctx->err = "streamed mode (X != NULL) is not available in this build";
-    return DPAR2_ERR_UNSUPPORTED;
-  }
-  if (!comp->M.p) {
+    try {
+      require(dtype == DPAR2_F32 || dtype == DPAR2_BF16 || dtype == DPAR2_F16, DPAR2_ERR_INVALID_ARG, "bad dtype");
+      require(ldx >= comp->J, DPAR2_ERR_SHAPE, "ldx < J");
+      require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
+              "ldx * sizeof(dtype) must be a multiple of 16 bytes");
+      require((reinterpret_cast<uintptr_t>(X) & 15) == 0, DPAR2_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    } catch (const Fail& f) {
+      ctx->err = f.msg;
+      return f.st;
+    }
+  } else if (!comp->M.p) {
     ctx->err = "identity mode needs M (compressed without DPAR2_FLAG_DROP_M)";
     return DPAR2_ERR_INVALID_ARG;
   }
-  (void)ldx;
-  (void)dtype;
   double res[2] = {0, 0};
   dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
     const int K = comp->K, J = comp->J, R = comp->R, RR = R * R;
@@ -754,10 +851,58 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       up = b.Upol;
     }
     float* P = wsget<float>(ctx, "re_P", (size_t)K * RR);
-    launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
     double* fpart = wsget<double>(ctx, "re_fit", (size_t)nblk + 4);
-    launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk, s);
-    k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+    if (!X) {
+      // identity mode: A_k^T X_k = B_k C_k^T, so V^T M_k stands for V^T X_k^T A_k
+      launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
+      launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
+                     s);
+      k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+    } else {
+      // streamed mode: one pass over X projects it onto A_k (A_k^T X_k and
+      // ||X_k||^2 measured, not taken from the compression) and A_k^T A_k is
+      // formed, so the error assumes neither the stage-1 identity nor A_k's
+      // orthonormality
+      const int LP = round_up(R, 8), Jp = round_up(J, 4), LPN = tc_lpn(R);
+      const int64_t N = comp->N;
+      const int64_t* d_off = static_cast<const int64_t*>(comp->offsets.p);
+      float* Ap = wsget<float>(ctx, "re_Ap", (size_t)N * LP);
+      launch_pad_omega(static_cast<const float*>(comp->A.p), (int)N, R, (int)N, LP, DPAR2_F32, Ap, s);
+      double* G = wsget<double>(ctx, "re_AtA", (size_t)K * LP * LP);
+      const int nsplit = gram_splits(K, comp->maxI);
+      double* Gp = nsplit > 1 ? wsget<double>(ctx, "re_AtAp", (size_t)K * nsplit * LP * LP) : nullptr;
+      launch_gram_dd(Ap, LP, d_off, K, R, G, Gp, nsplit, true, s);
+      float* Bs = wsget<float>(ctx, "re_B", (size_t)K * LP * Jp);
+      double* xn = wsget<double>(ctx, "re_xn", (size_t)K);
+      bool projected = false;
+      if (dtype != DPAR2_F32 && tc_available()) {
+        std::vector<int64_t> hp(K + 1, 0);
+        int64_t maxPad = 0;
+        for (int k = 0; k < K; ++k) {
+          const int64_t pk = round_up64(comp->h_offsets[k + 1] - comp->h_offsets[k], 64);
+          hp[k + 1] = hp[k] + pk;
+          maxPad = std::max(maxPad, pk);
+        }
+        int64_t* d_poff = wsget<int64_t>(ctx, "re_poff", (size_t)K + 1);
+        h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
+        void* Qs = wsget<uint16_t>(ctx, "re_Qs", (size_t)3 * LPN * hp[K]);
+        launch_qsplit(Ap, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+        const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+        double* xp = wsget<double>(ctx, "re_xpart_tc", (size_t)K * nJb * kProjNormWarps);
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, Bs, xp, nJb,
+                                      true, ctx->num_sms, ctx->d_status, s);
+        if (projected) launch_reduce_rows_f64(xp, K, nJb * kProjNormWarps, xn, s);
+      }
+      if (!projected) {
+        const int nJb = project_blocks(Jp, LP);
+        double* xp = wsget<double>(ctx, "re_xpart", (size_t)K * nJb);
+        launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Ap, LP, Bs, xp, nullptr, s);
+        launch_reduce_rows_f64(xp, K, nJb, xn, s);
+      }
+      launch_p_stream(K, J, Jp, R, LP, V, Bs, P, s);
+      launch_fitness(K, R, P, up, H, W, VtV, xn, fpart, nblk, fpart + nblk, s, G, LP);
+      k_sum_f64<<<1, 256, 0, s>>>(xn, K, fpart + nblk + 1);
+    }
     CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   });
   if (st == DPAR2_OK) {
@@ -873,18 +1018,222 @@ dpar2_status dpar2_comp_view_get(const dpar2_comp* c, dpar2_comp_view* v) {
 
 void dpar2_comp_free(dpar2_comp* c) {
   if (!c) return;
-  cudaDeviceSynchronize();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  dpar2_ctx* owner = c->owner;
+  if (owner) cudaSetDevice(owner->device);
+  cudaDeviceSynchronize();  // work of any stream that still reads the object
   delete c;
+  if (owner && --owner->live_comps == 0 && owner->closing) ctx_release(owner);
+  if (prev >= 0) cudaSetDevice(prev);
 }
 
-dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int, int, const int64_t*, const void*, int64_t, dpar2_dtype,
-                                   const float*, int, double*, void*) {
-  if (ctx) ctx->err = "learned-sketch kernels are not available in this build";
-  return DPAR2_ERR_UNSUPPORTED;
+// ------------------------------------------------------- learned sketch ----
+dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X,
+                                   int64_t ldx, dpar2_dtype dtype, const float* omega, int ell, double* loss,
+                                   void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  try {
+    require(X && row_offsets && omega && loss, DPAR2_ERR_INVALID_ARG, "X, row_offsets, omega and loss must be non-null");
+    require(dtype == DPAR2_F32 || dtype == DPAR2_BF16 || dtype == DPAR2_F16, DPAR2_ERR_INVALID_ARG, "bad dtype");
+    require(K >= 1 && J >= 1, DPAR2_ERR_SHAPE, "K and J must be >= 1");
+    require(ell >= 1 && ell <= std::min(J, kMaxEll), DPAR2_ERR_SHAPE, "need 1 <= l <= min(J, 64)");
+    require(ldx >= J, DPAR2_ERR_SHAPE, "ldx < J");
+    require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
+            "ldx * sizeof(dtype) must be a multiple of 16 bytes");
+    require((reinterpret_cast<uintptr_t>(X) & 15) == 0, DPAR2_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    require(row_offsets[0] == 0, DPAR2_ERR_SHAPE, "row_offsets[0] must be 0");
+    for (int k = 0; k < K; ++k)
+      require(row_offsets[k + 1] > row_offsets[k], DPAR2_ERR_SHAPE, "every slice needs I_k >= 1 rows");
+  } catch (const Fail& f) {
+    ctx->err = f.msg;
+    return f.st;
+  }
+  ctx->sk_ready = false;
+  double* h_loss = nullptr;
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    const int LP = round_up(ell, 8), Jp = round_up(J, 4), Jpad = round_up(J, 32);
+    const int64_t N = row_offsets[K];
+    int64_t maxI = 0;
+    for (int k = 0; k < K; ++k) maxI = std::max<int64_t>(maxI, row_offsets[k + 1] - row_offsets[k]);
+    const bool use_tc = dtype != DPAR2_F32 && tc_available();
+    const int LPN = tc_lpn(ell);
+    ctx->sk_K = K;
+    ctx->sk_J = J;
+    ctx->sk_ell = ell;
+    ctx->sk_LP = LP;
+    ctx->sk_N = N;
+    ctx->sk_ldx = ldx;
+    ctx->sk_maxI = maxI;
+    ctx->sk_X = X;
+    ctx->sk_dtype = dtype;
+    ctx->sk_tc = use_tc;
+    int64_t* d_off = wsget<int64_t>(ctx, "sl_off", (size_t)K + 1);
+    h2d_i64(ctx, d_off, row_offsets, (K + 1), s);
+
+    // pass 1: Y = X Omega (Omega rounded to X's 16-bit type, as in dpar2_compress)
+    float* om_pad = wsget<float>(ctx, "sl_om_pad", (size_t)Jpad * LP);
+    launch_pad_omega(omega, J, ell, Jpad, LP, dtype, om_pad, s);
+    float* Y = wsget<float>(ctx, "sl_Y", (size_t)N * LP);
+    bool done = false;
+    if (use_tc) {
+      void* omT16 = wsget<uint16_t>(ctx, "sl_omT16", (size_t)LPN * Jpad);
+      launch_omega_t16(om_pad, Jpad, LP, LPN, dtype, omT16, s);
+      done = launch_sketch_tc(X, dtype, ldx, N, J, omT16, Jpad, LPN, LP, Y, ctx->num_sms, ctx->d_status, s);
+      require(done, DPAR2_ERR_CUDA, "tensor map encoding failed");
+    } else {
+      launch_sketch_generic(X, dtype, ldx, N, J, om_pad, LP, Y, s);
+    }
+    // CholeskyQR2: Y <- Q1 = Y M1, M2 (Q = Q1 M2)
+    float* M2 = wsget<float>(ctx, "sl_M2", (size_t)K * LP * LP);
+    cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, wsget<int>(ctx, "sl_rank", (size_t)K), s, "sl");
+    // pass 2: B1 = Q1^T X and ||X_k||^2
+    float* B1 = wsget<float>(ctx, "sl_B1", (size_t)K * LP * Jp);
+    double* xn = wsget<double>(ctx, "sl_xn", (size_t)K);
+    if (use_tc) {
+      std::vector<int64_t>& hp = ctx->sk_poff;
+      hp.assign(K + 1, 0);
+      int64_t maxPad = 0;
+      for (int k = 0; k < K; ++k) {
+        const int64_t pk = round_up64(row_offsets[k + 1] - row_offsets[k], 64);
+        hp[k + 1] = hp[k] + pk;
+        maxPad = std::max(maxPad, pk);
+      }
+      int64_t* d_poff = wsget<int64_t>(ctx, "sl_poff", (size_t)K + 1);
+      h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
+      void* Qs = wsget<uint16_t>(ctx, "sl_Qs", (size_t)3 * LPN * hp[K]);
+      launch_qsplit(Y, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+      const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+      double* xp = wsget<double>(ctx, "sl_xpart_tc", (size_t)K * nJb * kProjNormWarps);
+      done = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, B1, xp, nJb, true,
+                               ctx->num_sms, ctx->d_status, s);
+      require(done, DPAR2_ERR_CUDA, "tensor map encoding failed");
+      launch_reduce_rows_f64(xp, K, nJb * kProjNormWarps, xn, s);
+    } else {
+      const int nJb = project_blocks(Jp, LP);
+      double* xp = wsget<double>(ctx, "sl_xpart", (size_t)K * nJb);
+      launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, xp, nullptr, s);
+      launch_reduce_rows_f64(xp, K, nJb, xn, s);
+    }
+    // ||Q_k^T X_k||^2 = tr(M2^T GB M2), GB = B1 B1^T
+    double* GB = wsget<double>(ctx, "sl_GB", (size_t)K * LP * LP);
+    launch_gram_b1(B1, Jp, J, K, ell, LP, GB, s);
+    double* dl = wsget<double>(ctx, "sl_loss", 2);
+    const float* M1 = wsget<float>(ctx, "sl_M1", (size_t)K * LP * LP);
+    float* P = wsget<float>(ctx, "sl_P", (size_t)K * LP * LP);
+    float* S = wsget<float>(ctx, "sl_S", (size_t)K * LP * LP);
+    launch_sl_loss(M1, M2, GB, xn, K, ell, LP, wsget<double>(ctx, "sl_ratio", (size_t)K), P, S, dl, s);
+    h_loss = reinterpret_cast<double*>(ctx->h_status) + 1;
+    CK(cudaMemcpyAsync(h_loss, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+    // row ranges of the gradient's last pass, 64-row aligned: about one per SM,
+    // a multiple of the tensor-core projection's teams (num_sms / column blocks)
+    const int nJb_g = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+    const int nteam = std::max(1, ctx->num_sms / nJb_g);
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(nteam * std::max(1, ctx->num_sms / nteam),
+                                                                (N + 63) / 64));
+    const int64_t per = round_up64((N + want - 1) / want, 64);
+    ctx->sk_off2.clear();
+    for (int64_t r = 0; r < N; r += per) ctx->sk_off2.push_back(r);
+    ctx->sk_off2.push_back(N);
+    ctx->sk_toff.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k)
+      ctx->sk_toff[k + 1] = ctx->sk_toff[k] + (row_offsets[k + 1] - row_offsets[k] + 127) / 128;
+  });
+  if (st == DPAR2_OK) {
+    *loss = *h_loss;
+    ctx->sk_ready = true;
+  }
+  return st;
 }
-dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double, float*, void*) {
-  if (ctx) ctx->err = "learned-sketch kernels are not available in this build";
-  return DPAR2_ERR_UNSUPPORTED;
+
+dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, float* grad_omega, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!grad_omega) {
+    ctx->err = "grad_omega must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (!ctx->sk_ready) {
+    ctx->err = "dpar2_sketch_loss_bwd needs a successful dpar2_sketch_loss_fwd on this context first";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    const int K = ctx->sk_K, J = ctx->sk_J, ell = ctx->sk_ell, LP = ctx->sk_LP;
+    const int Jp = round_up(J, 4), Jpad = round_up(J, 32), LPN = tc_lpn(ell);
+    const int64_t N = ctx->sk_N, maxI = ctx->sk_maxI;
+    const dpar2_dtype dtype = ctx->sk_dtype;
+    const void* X = ctx->sk_X;
+    const int64_t* d_off = wsget<int64_t>(ctx, "sl_off", (size_t)K + 1);
+    const float* Q1 = wsget<float>(ctx, "sl_Y", (size_t)N * LP);
+    const float* B1 = wsget<float>(ctx, "sl_B1", (size_t)K * LP * Jp);
+    const double* xn = wsget<double>(ctx, "sl_xn", (size_t)K);
+    const float* P = wsget<float>(ctx, "sl_P", (size_t)K * LP * LP);
+    const float* S = wsget<float>(ctx, "sl_S", (size_t)K * LP * LP);
+    float* sk = wsget<float>(ctx, "sl_opscale", (size_t)K * LP);
+
+    // pass 3: V_k = X_k B1_k^T (W applies P_k: V_k P_k = X_k Mk)
+    float* U = wsget<float>(ctx, "sl_U", (size_t)N * LP);
+    if (ctx->sk_tc) {
+      void* Ms = wsget<uint16_t>(ctx, "sl_Ms", (size_t)K * 3 * LPN * Jpad);
+      launch_sl_rowsplit(B1, K, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr, sk, s);
+      int64_t* d_toff = wsget<int64_t>(ctx, "sl_toff", (size_t)K + 1);
+      h2d_i64(ctx, d_toff, ctx->sk_toff.data(), (K + 1), s);
+      const bool ok = launch_sketch_seg_tc(X, dtype, ctx->sk_ldx, N, J, d_off, d_toff, ctx->sk_toff[K], K, Ms, Jpad,
+                                           LPN, LP, U, ctx->num_sms, ctx->d_status, s);
+      require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+    } else {
+      float* omk = wsget<float>(ctx, "sl_omk", (size_t)K * Jpad * LP);
+      launch_sl_rowsplit(B1, K, Jp, J, Jpad, ell, LP, LPN, dtype, nullptr, omk, sk, s);
+      launch_sketch_generic_per_slice(X, dtype, ctx->sk_ldx, d_off, K, (int)maxI, J, omk, Jpad, LP, U, s);
+    }
+
+    // W_k = c_k (U_k - Q1_k S_k); pass 4: grad^T = sum over row ranges of W^T X
+    const int np = (int)ctx->sk_off2.size() - 1;
+    int64_t* d_off2 = wsget<int64_t>(ctx, "sl_off2", (size_t)np + 1);
+    h2d_i64(ctx, d_off2, ctx->sk_off2.data(), (np + 1), s);
+    float* GP = wsget<float>(ctx, "sl_GP", (size_t)np * LP * Jp);
+    float* Wf = wsget<float>(ctx, "sl_W", (size_t)N * LP);
+    unsigned* wmax = wsget<unsigned>(ctx, "sl_wmax", (size_t)LP);
+    launch_sl_wrows(U, Q1, d_off, K, maxI, LP, P, S, xn, grad_scale, sk, Wf, wmax, s);
+    if (ctx->sk_tc) {
+      const int64_t Npad = round_up64(N, 64);
+      ctx->sk_poff2 = ctx->sk_off2;
+      ctx->sk_poff2[np] = Npad;
+      int64_t* d_poff2 = wsget<int64_t>(ctx, "sl_poff2", (size_t)np + 1);
+      h2d_i64(ctx, d_poff2, ctx->sk_poff2.data(), (np + 1), s);
+      uint16_t* Ws = wsget<uint16_t>(ctx, "sl_Ws", (size_t)3 * LPN * Npad);
+      if (N % 64) CK(cudaMemsetAsync(Ws + (N / 64) * 3 * LPN * 64, 0, (size_t)3 * LPN * 64 * 2, s));
+      launch_sl_wsplit(Wf, N, LP, LPN, wmax, dtype, Ws, s);
+      const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+      double* xp = wsget<double>(ctx, "sl_xpart2", (size_t)np * nJb * kProjNormWarps);
+      const bool ok = launch_project_tc(X, dtype, ctx->sk_ldx, N, d_off2, d_poff2, np, J, Jp, Ws, Npad, LPN, LP, GP,
+                                        xp, nJb, false, ctx->num_sms, ctx->d_status, s);
+      require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+    } else {
+      launch_project_generic(X, dtype, ctx->sk_ldx, d_off2, np, J, Jp, Wf, LP, GP, nullptr, nullptr, s);
+    }
+    launch_sl_gradsum(GP, np, LP, Jp, J, ell, ctx->sk_tc ? wmax : nullptr, grad_omega, s);
+  });
+}
+
+dpar2_status dpar2_orthonormalize(dpar2_ctx* ctx, int64_t rows, int cols, float* A, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!A || cols < 1 || cols > kMaxEll || rows < cols) {
+    ctx->err = "need A non-null and 1 <= cols <= min(rows, 64)";
+    return A ? DPAR2_ERR_SHAPE : DPAR2_ERR_INVALID_ARG;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    const int LP = round_up(cols, 8);
+    float* Y = wsget<float>(ctx, "on_Y", (size_t)rows * LP);
+    launch_pad_omega(A, (int)rows, cols, (int)rows, LP, DPAR2_F32, Y, s);
+    int64_t* d_off = wsget<int64_t>(ctx, "on_off", 2);
+    const int64_t hoff[2] = {0, rows};
+    h2d_i64(ctx, d_off, hoff, sizeof(hoff) / sizeof(int64_t), s);
+    float* M2 = wsget<float>(ctx, "on_M2", (size_t)LP * LP);
+    cholqr2(ctx, Y, d_off, 1, rows, cols, LP, M2, wsget<int>(ctx, "on_rank", 1), s, "on");
+    k_apply_m2<<<dim3((unsigned)((rows + 127) / 128), 1), 128, 0, s>>>(Y, d_off, LP, M2);
+    CK(cudaMemcpy2DAsync(A, cols * sizeof(float), Y, LP * sizeof(float), cols * sizeof(float), rows,
+                         cudaMemcpyDeviceToDevice, s));
+  });
 }
 
 }  // extern "C"

@@ -21,7 +21,7 @@ struct dpar2_ctx {
   int num_sms = 0;
   std::string err;
   int* d_status = nullptr;  // device status word (dp2::ST_*)
-  int* h_status = nullptr;  // pinned mirror
+  int* h_status = nullptr;  // pinned mirror (64 bytes: the status word, then scalars read back at byte 8)
   std::map<std::string, dp2::DevBuf> ws;  // named scratch buffers, grow-only
   // learned-sketch forward state kept for the backward pass
   int sk_K = 0, sk_J = 0, sk_ell = 0, sk_LP = 0;
@@ -29,6 +29,11 @@ struct dpar2_ctx {
   const void* sk_X = nullptr;
   dpar2_dtype sk_dtype = DPAR2_F32;
   bool sk_ready = false;
+  bool sk_tc = false;                 // 16-bit X on the tensor-core passes
+  std::vector<int64_t> sk_toff;       // K + 1 prefix sums of 128-row tiles per slice
+  std::vector<int64_t> sk_off2;       // row ranges of the gradient's last pass (64-row aligned)
+  std::vector<int64_t> sk_poff2;      // the same, last entry padded to a multiple of 64
+  std::vector<int64_t> sk_poff;       // K + 1 offsets of the slices padded to 64 rows (Q split)
   // phase timing (DPAR2_PH_*): start/end events on the work stream
   bool timing = false;
   cudaEvent_t tev[2 * DPAR2_NUM_PHASES] = {};
@@ -37,9 +42,20 @@ struct dpar2_ctx {
   // scratch buffer of at least `bytes` bytes under `name` (contents undefined);
   // nullptr when the allocation failed
   void* get(const std::string& name, size_t bytes);
+  // stream-ordered pool of the compression objects' buffers (memory kept for
+  // reuse); the context outlives its last compression object
+  cudaMemPool_t pool = nullptr;
+  int live_comps = 0;
+  bool closing = false;
+  // pinned host staging for the small index tables a call copies to the device
+  // (asynchronous copies; a call's regions are reused by the next call, after
+  // the synchronisation every call ends with)
+  int64_t* hstage = nullptr;
+  size_t hstage_cap = 0, hstage_used = 0;
 };
 
 struct dpar2_comp {
+  dpar2_ctx* owner = nullptr;  // context whose pool and work stream hold the buffers
   int K = 0, J = 0, R = 0, ell = 0, LP = 0;
   int64_t N = 0, maxI = 0;
   std::vector<int64_t> h_offsets;
@@ -74,13 +90,38 @@ int tc_lpn(int ell);  // MMA N width of the sketch: 32 or 64
 void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s);
 bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const void* omT16, int Jpad,
                       int LPN, int LP, float* Y, int num_sms, int* status, cudaStream_t s);
+// Q rows -> three 16-bit parts per slice, scaled by a power of two that
+// launch_project_tc divides out when called with qscale
 void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
                    int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
 // X columns per work item of the tensor-core projection (nJb = ceil(Jp / cols))
 int project_tc_cols(int LPN);
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
-                       float* B1, double* xpart, int nJb, int num_sms, int* status, cudaStream_t s);
+                       float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status, cudaStream_t s,
+                       int sched = 0);  // 0: items round-robin over the CTAs; 1: teams of nJb CTAs per slice
+
+// per-slice right operand (three 16-bit parts, [k][3 LPN][Jpad]); ntiles = sum_k ceil(I_k / 128)
+bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const int64_t* d_off,
+                          const int64_t* d_toff, int64_t ntiles, int K, const void* Ms, int Jpad, int LPN, int LP,
+                          float* U, int num_sms, int* status, cudaStream_t s);
+
+// ---- learned sketch (range-finder loss and its gradient) ----
+// per slice: ratio_k, P_k, S_k (K x LP x LP); out = mean ratio
+void launch_sl_loss(const float* M1, const float* M2, const double* GB, const double* xn, int K, int ell, int LP,
+                    double* ratio, float* P, float* S, double* out, cudaStream_t s);
+// rows of B1 as the per-slice right operand of X_k B1_k^T (16-bit parts [k][3 LPN][Jpad]
+// or FP32 [k][Jpad][LP]), each row times a power of two (rscale: K x LP)
+void launch_sl_rowsplit(const float* B1, int K, int Jp, int J, int Jpad, int ell, int LP, int LPN, dpar2_dtype dt,
+                        void* out16, float* out32, float* rscale, cudaStream_t s);
+// W rows (FP32, N x LP) and the largest |W| per column (wmax[LP], zeroed by the call)
+void launch_sl_wrows(const float* U, const float* Q1, const int64_t* d_off, int K, int64_t maxI, int LP,
+                     const float* P, const float* S, const double* xn, double gscale, const float* rs, float* W,
+                     unsigned* wmax, cudaStream_t s);
+void launch_sl_wsplit(const float* W, int64_t N, int LP, int LPN, const unsigned* wmax, dpar2_dtype dt, void* out16,
+                      cudaStream_t s);
+void launch_sl_gradsum(const float* part, int np, int LP, int Jp, int J, int ell, const unsigned* wmax, float* grad,
+                       cudaStream_t s);
 
 // ---- per-slice small linear algebra ----
 // G[k] = Y_k^T Y_k (FP64, pitch LP).  nsplit > 1 splits every slice's rows over
@@ -161,7 +202,11 @@ void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, 
 void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);
 void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,
                     cudaStream_t s);
+// AtA (K x ldg x ldg FP64, A_k^T A_k) or null for orthonormal A_k
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
-                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s);
+                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s,
+                    const double* AtA = nullptr, int ldg = 0);
+// P_k = V^T (A_k^T X_k)^T from the projection rows B (K x LP x Jp)
+void launch_p_stream(int K, int J, int Jp, int R, int LP, const float* V, const float* B, float* P, cudaStream_t s);
 
 }  // namespace dp2

@@ -789,19 +789,24 @@ __global__ void k_upol_h(int K, int R, const float* __restrict__ Upol, const flo
 }
 
 // Squared error through the exact stage-1 identity, one warp per slice:
-//   ||X_k||^2 - 2 tr(P_k Upol_k H S_k) + ||Upol_k H S_k V^T||^2,
-// P_k = V^T M_k (R x R).  Writes block partials (FP64) of the sum.
+//   ||X_k||^2 - 2 tr(P_k Upol_k H S_k) + ||A_k Upol_k H S_k V^T||^2,
+// P_k = V^T M_k (R x R) with M_k = X_k^T A_k.  The last term is
+// sum_ab (S Y1^T G_k Y1 S)_ab (V^T V)_ab, Y1 = Upol_k H, with G_k = A_k^T A_k
+// (FP64, pitch ldg) when AtA is given, else G_k = I (A_k orthonormal).
+// Writes block partials (FP64) of the sum.
 __global__ void k_fitness(int K, int R, const float* __restrict__ P, const float* __restrict__ Upol,
                           const float* __restrict__ H, const float* __restrict__ W, const double* __restrict__ VtV,
-                          const double* __restrict__ xnorm2, double* __restrict__ part) {
+                          const double* __restrict__ xnorm2, const double* __restrict__ AtA, int ldg,
+                          double* __restrict__ part) {
   extern __shared__ __align__(16) float sm[];
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* hs = sm;
   float* vv = hs + RR;
-  float* my = vv + RR + warp * 2 * RR;
+  float* my = vv + RR + warp * 3 * RR;
   float* Y1 = my;        // Upol H
   float* Pk = my + RR;
+  float* GY = my + 2 * RR;  // G_k Y1 (when AtA is given)
   __shared__ double red[32];
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     hs[e] = H[e];
@@ -820,14 +825,26 @@ __global__ void k_fitness(int K, int R, const float* __restrict__ P, const float
       Pk[e] = P[(int64_t)k * RR + e];
     }
     __syncwarp();
+    const float* Z = Y1;
+    if (AtA) {
+      const double* g = AtA + (int64_t)k * ldg * ldg;
+      for (int e = lane; e < RR; e += 32) {
+        const int i = e / R, b = e % R;
+        double t = 0.0;
+        for (int m = 0; m < R; ++m) t = fma(g[i * ldg + m], (double)Y1[m * R + b], t);
+        GY[e] = (float)t;
+      }
+      __syncwarp();
+      Z = GY;
+    }
     double cross = 0.0, model = 0.0;
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e % R;
       // tr(P Y1 S) = sum_{a,b} P[a][b] Y1[b][a] W[a]
       cross += (double)Pk[e] * Y1[b * R + a] * wk[a];
-      // (S Y1^T Y1 S)[a][b] VtV[a][b]
+      // (S Y1^T G Y1 S)[a][b] VtV[a][b]
       float g = 0.f;
-      for (int i = 0; i < R; ++i) g = fmaf(Y1[i * R + a], Y1[i * R + b], g);
+      for (int i = 0; i < R; ++i) g = fmaf(Y1[i * R + a], Z[i * R + b], g);
       model += (double)wk[a] * g * wk[b] * vv[e];
     }
     cross = warp_sum(cross);
@@ -869,6 +886,26 @@ __global__ void k_vtm(int J, int R, const float* __restrict__ V, const float* __
     float s = 0.f, c = 0.f;
     for (int j = 0; j < J; ++j) {
       const float x = V[(int64_t)j * R + a] * mk[(int64_t)j * R + b];
+      const float t = s + x;
+      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    P[(int64_t)k * RR + e] = s + c;
+  }
+}
+
+// P_k (R x R) = V^T (A_k^T X_k)^T from the projection of X onto A_k, stored
+// as B[k] (rows c < R of pitch Jp over j): P[a][b] = sum_j V[j][a] B[k][b][j].
+// One block per slice, compensated sums over j.
+__global__ void k_p_stream(int J, int Jp, int R, int LP, const float* __restrict__ V, const float* __restrict__ B,
+                           float* __restrict__ P) {
+  const int k = blockIdx.x, RR = R * R;
+  const float* bk = B + (int64_t)k * LP * Jp;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    const int a = e / R, b = e % R;
+    float s = 0.f, c = 0.f;
+    for (int j = 0; j < J; ++j) {
+      const float x = V[(int64_t)j * R + a] * bk[(int64_t)b * Jp + j];
       const float t = s + x;
       c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
       s = t;
@@ -985,12 +1022,17 @@ void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out
 }
 
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
-                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s) {
+                    const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s,
+                    const double* AtA, int ldg) {
   als_set_attrs();
-  const int nw = 4;
-  k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 2 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2,
-                                                                           part);
+  const int nw = R > 48 ? 3 : 4;  // (2 + 3 nw) R^2 floats of shared memory <= 200 KB
+  k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 3 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2, AtA,
+                                                                           ldg, part);
   k_reduce_f64<<<1, 32, 0, s>>>(part, nblk, out);
+}
+
+void launch_p_stream(int K, int J, int Jp, int R, int LP, const float* V, const float* B, float* P, cudaStream_t s) {
+  k_p_stream<<<K, 128, 0, s>>>(J, Jp, R, LP, V, B, P);
 }
 
 }  // namespace dp2

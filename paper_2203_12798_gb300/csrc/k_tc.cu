@@ -99,6 +99,34 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+// the same with an L2 cache-eviction policy (createpolicy) for the loaded lines
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 int z, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "l"(pol)
+      : "memory");
+}
+// streamed once: first to go; re-read by sibling work items: kept
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -321,6 +349,202 @@ __global__ void __launch_bounds__(192, 1) k_sketch_tc(const __grid_constant__ CU
   if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
 }
 
+// ------------------------------------------------- per-slice sketch ----
+// U_k = X_k M_k with a different J x LP right operand per slice (the
+// learned-sketch gradient's X_k (X_k^T Y_k G_k^-1) pass).  M_k is given as three
+// exact-sum 16-bit parts, stored [k][3 LPN][Jpad] (K-major rows), so one MMA
+// per K step yields hi / mid / lo products that the epilogue adds.  Work
+// items are (slice, 128-row tile of the slice); rows of a tile past the end of
+// its slice are computed against the wrong operand and not written.
+template <int LPN>
+struct SegSmem {
+  static constexpr int NS = 3 * LPN;
+  static constexpr int A = SK_BM * SK_BK * 2;
+  static constexpr int B = NS * SK_BK * 2;
+  static constexpr int STAGES = LPN == 32 ? 6 : 4;
+  static constexpr int BYTES = 1024 + STAGES * (A + B) + 256;
+};
+
+// slice of work item `item` (toff: K + 1 prefix sums of tiles per slice)
+__device__ __forceinline__ int seg_slice(const int64_t* __restrict__ toff, int K, int64_t item) {
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int LPN>
+__global__ void __launch_bounds__(192, 1) k_sketch_seg_tc(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmM,
+                                                          const int64_t* __restrict__ off,
+                                                          const int64_t* __restrict__ toff, int K, int J, int LP,
+                                                          float* __restrict__ U, int bf16, int* status) {
+  using S = SegSmem<LPN>;
+  constexpr int ST = S::STAGES;
+  constexpr uint32_t NCOL = 2 * S::NS <= 256 ? 256 : 512;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint8_t* sA = base;
+  uint8_t* sB = base + ST * S::A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + ST * S::B);
+  uint64_t* empty = full + ST;
+  uint64_t* accfull = empty + ST;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nitems = toff[K];
+  const int nk = (J + SK_BK - 1) / SK_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 128);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, NCOL);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    prefetch_tmap(&tmX);
+    prefetch_tmap(&tmM);
+    int s = 0;
+    uint32_t ph = 0, inflight = 0;
+    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
+      const int k = seg_slice(toff, K, item);
+      // the last tile of a slice ends at its last row (overlapping the tile
+      // before it) instead of reading rows of the next slice
+      const int row0 = (int)min64(off[k] + (item - toff[k]) * SK_BM, off[k + 1] - SK_BM);
+      for (int kc = 0; kc < nk; ++kc) {
+        if (!wait_bounded(&empty[s], ph ^ 1, abort_flag)) break;
+        mbar_arrive_expect_tx(&full[s], S::A + S::B);
+        tma_load_2d(sA + s * S::A, &tmX, &full[s], kc * SK_BK, row0);
+        tma_load_3d(sB + s * S::B, &tmM, &full[s], kc * SK_BK, 0, k);
+        inflight = 1;
+        if (++s == ST) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    if (*abort_flag && inflight) {
+      const int ls = (s + ST - 1) % ST;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&full[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issue
+    const uint32_t idesc = idesc_f16(SK_BM, S::NS, bf16 != 0, false, false);
+    int s = 0;
+    uint32_t ph = 0;
+    int t = 0;
+    bool issued = false;
+    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x, ++t) {
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accempty[acc], aph ^ 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * S::NS;
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc) {
+        if (!wait_bounded(&full[s], ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc_sw128(smem_u32(sA + s * S::A), 16, 1024);
+        const uint64_t bd = sdesc_sw128(smem_u32(sB + s * S::B), 16, 1024);
+#pragma unroll
+        for (int kk = 0; kk < SK_BK / 16; ++kk)
+          tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (kc | kk) != 0 ? 1u : 0u);
+        tc_commit(&empty[s]);
+        issued = true;
+        if (++s == ST) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      tc_commit(&accfull[acc]);
+    }
+    if (*abort_flag && issued) {
+      const int ls = (s + ST - 1) % ST;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&empty[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    int t = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++t) {
+      const int k = seg_slice(toff, K, item);
+      const int64_t first = off[k] + (item - toff[k]) * SK_BM;  // first row this tile owns
+      const int64_t row = min64(first, off[k + 1] - SK_BM) + q * 32 + lane;
+      const bool valid = row >= first && row < off[k + 1];
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + acc * S::NS;
+#pragma unroll
+      for (int g = 0; g < LPN / 32; ++g) {
+        float v[32], w[32];
+        tmem_ld32(tl + g * 32, v);
+        tmem_ld32(tl + LPN + g * 32, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
+        tmem_ld32(tl + 2 * LPN + g * 32, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += w[i];
+        if (valid) {
+          float4* dst = reinterpret_cast<float4*>(U + row * LP + g * 32);
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4)
+            if (g * 32 + 4 * c4 < LP) dst[c4] = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[acc]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, NCOL);
+  }
+  if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
+}
+
+// Power of two applied to a slice's Q rows before the 16-bit split: Q has
+// orthonormal columns, so its entries are about I_k^-1/2 and at most 1; the
+// scale 2^floor(log2 sqrt(I_k)) lifts them towards 1, which keeps the FP16
+// middle and low parts out of the subnormal range (exact for both types).
+__device__ __forceinline__ float qsplit_scale(int64_t nrows) {
+  return ldexpf(1.f, ilogbf(sqrtf((float)(nrows > 0 ? nrows : 1))));
+}
+
 // -------------------------------------------------------------- project ----
 constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
 constexpr int PJ_NORM_WARPS = kProjNormWarps;          // warps 6 .. 6 + PJ_NORM_WARPS - 1
@@ -346,7 +570,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
                                                        const int64_t* __restrict__ off,
                                                        const int64_t* __restrict__ poff, int K, int J, int Jp,
                                                        int LP, float* __restrict__ B1, double* __restrict__ xpart,
-                                                       int nJb, int bf16, int* status) {
+                                                       int nJb, int bf16, int qscale, int sched, int* status) {
   using S = ProjSmem<LPN>;
   constexpr int ST = S::STAGES;
   constexpr uint32_t NCOL = 2 * S::HV * S::NS <= 256 ? 256 : 512;
@@ -361,7 +585,19 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nitems = (int64_t)K * nJb;
+  // Work items (slice k, column block jb), two schedules:
+  //   sched 0  items k nJb + jb dealt round-robin over the CTAs;
+  //   sched 1  teams of nJb CTAs: CTA b owns column block b % nJb of slices
+  //            team, team + nteam, ... (team = b / nJb), so the nJb items of a
+  //            slice run side by side with equal work (the host launches a
+  //            multiple of nJb CTAs).
+  const bool teams = sched == 1;
+  const int nteam = teams ? (int)gridDim.x / nJb : 1;
+  const int64_t it0 = teams ? (int64_t)(blockIdx.x / nJb) : (int64_t)blockIdx.x;
+  const int64_t its = teams ? nteam : (int64_t)gridDim.x;
+  const int64_t itn = teams ? ((int)(blockIdx.x / nJb) < nteam ? K : 0) : (int64_t)K * nJb;
+#define PJ_ITEM(it) const int k = teams ? (int)(it) : (int)((it) / nJb); \
+  const int jb = teams ? (int)(blockIdx.x % nJb) : (int)((it) % nJb); (void)jb
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -389,13 +625,14 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
     // ------------------------------------------------------------ producer
     prefetch_tmap(&tmX);
     prefetch_tmap(&tmQ);
+    const uint64_t pol_x = policy_evict_first(), pol_q = policy_evict_last();
     int s = 0;
     uint32_t ph = 0;
     bool inflight = false;
-    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
-      const int k = (int)(item / nJb), jb = (int)(item % nJb);
-      const int64_t r0 = off[k], nrows = off[k + 1] - r0, p0 = poff[k];
-      const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
+    for (int64_t it = it0; it < itn && !*abort_flag; it += its) {
+      PJ_ITEM(it);
+      const int64_t r0 = off[k], r1 = off[k + 1], p0 = poff[k];
+      const int nch = (int)((r1 - r0 + PJ_BK - 1) / PJ_BK);
       bool ok = true;
       for (int c = 0; c < nch; ++c) {
         if (!wait_bounded(&empty[s], ph ^ 1, abort_flag)) {
@@ -404,10 +641,13 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         }
         mbar_arrive_expect_tx(&full[s], S::A + S::B);
         uint8_t* a = sA + s * S::A;
+        // the last chunk ends at the slice's last row (it overlaps the chunk
+        // before it, whose rows its Q rows zero) instead of reading past it
+        const int row = (int)(c + 1 < nch ? r0 + (int64_t)c * PJ_BK : r1 - PJ_BK);
 #pragma unroll
         for (int bx = 0; bx < 2 * S::HV; ++bx)
-          tma_load_2d(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, (int)(r0 + c * PJ_BK));
-        tma_load_3d(sB + s * S::B, &tmQ, &full[s], 0, 0, (int)(p0 / PJ_BK + c));
+          tma_load_2d_hint(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, row, pol_x);
+        tma_load_3d_hint(sB + s * S::B, &tmQ, &full[s], 0, 0, (int)(p0 / PJ_BK + c), pol_q);
         inflight = true;
         if (++s == ST) {
           s = 0;
@@ -430,8 +670,8 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
     uint32_t ph = 0;
     int t = 0;
     bool issued = false;
-    for (int64_t item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x, ++t) {
-      const int k = (int)(item / nJb);
+    for (int64_t it = it0; it < itn && !*abort_flag; it += its, ++t) {
+      PJ_ITEM(it);
       const int64_t nrows = off[k + 1] - off[k];
       const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
       const int acc = t & 1;
@@ -478,10 +718,12 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
     int t = 0;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++t) {
-      const int k = (int)(item / nJb), jb = (int)(item % nJb);
+    for (int64_t it = it0; it < itn; it += its, ++t) {
+      PJ_ITEM(it);
       const int acc = t & 1;
       const uint32_t aph = (t >> 1) & 1;
+      // the split Q rows of this slice were scaled by qsplit_scale(I_k)
+      const float inv = qscale ? 1.f / qsplit_scale(off[k + 1] - off[k]) : 1.f;
       if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
       tc_fence_after();
       for (int h = 0; h < S::HV; ++h) {
@@ -500,7 +742,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
             float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i];
+              if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i] * inv;
           }
         }
       }
@@ -517,8 +759,8 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
     const int nw = warp - 6;
     int s = 0;
     uint32_t ph = 0;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-      const int k = (int)(item / nJb), jb = (int)(item % nJb);
+    for (int64_t it = it0; it < itn; it += its) {
+      PJ_ITEM(it);
       const int64_t nrows = off[k + 1] - off[k];
       const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
       float acc = 0.f;
@@ -528,13 +770,15 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
           ok = false;
           break;
         }
+        // rows of this slice in the staged box: the last `valid` ones (the
+        // last chunk is aligned to the slice's end)
         const int valid = (int)min64(PJ_BK, nrows - (int64_t)c * PJ_BK);
         const uint8_t* a = sA + s * S::A + nw * BYTES_PER;
 #pragma unroll
         for (int it = 0; it < BYTES_PER / 512; ++it) {
           const int byte = nw * BYTES_PER + it * 512 + lane * 16;
           const int row = (byte % 8192) / 128;
-          if (row < valid) {
+          if (row >= PJ_BK - valid) {
             const uint4 u = *reinterpret_cast<const uint4*>(a + it * 512 + lane * 16);
             float f[8];
             if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
@@ -564,6 +808,8 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
   if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
 }
 
+#undef PJ_ITEM
+
 // ------------------------------------------------------------- operands ----
 // Omega^T in 16-bit (LPN x Jpad) from the padded FP32 Omega (Jpad x LP).
 __global__ void k_omega_t16(const float* __restrict__ om, int Jpad, int LP, int LPN, int bf16, void* out) {
@@ -577,20 +823,31 @@ __global__ void k_omega_t16(const float* __restrict__ om, int Jpad, int LP, int 
 }
 
 // Q1 rows (N x LP FP32) -> three exact-sum 16-bit parts, transposed to
-// (3 LPN) x Npad with every slice padded to a multiple of 64 rows (zeros).
+// (3 LPN) x Npad with every slice padded to a multiple of 64 rows.
 // Layout of the split: 64-row chunks of all 3 LPN columns stored contiguously,
 // element (p, c) at ((p / 64) 3 LPN + c) 64 + p % 64, so that one chunk (the B
 // operand of one projection stage) is a single contiguous 12 KB (LPN = 32) block.
+// The last chunk of a slice holds the slice's last 64 rows (the projection
+// reads X there from the slice's end backwards), zeros where they repeat
+// rows of the chunk before it.
 __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ poff, int K, int64_t Npad, int bf16, void* out) {
   const int k = blockIdx.y;
   const int64_t p0 = poff[k], p1 = poff[k + 1], r0 = off[k], nr = off[k + 1] - r0;
   const int NSQ = 3 * LPN;
+  const int64_t last0 = p1 - p0 - PJ_BK;  // first padded row of the last chunk
+  const float sc = qsplit_scale(nr);
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = p - p0;
+    int64_t i = p - p0;
+    bool in = i < nr;
+    if (i >= last0) {  // last chunk: box row b holds slice row nr - 64 + b
+      const int64_t b = i - last0;
+      i = nr - PJ_BK + b;
+      in = i >= last0;
+    }
     const int64_t cb = (p / PJ_BK) * NSQ * PJ_BK + (p % PJ_BK);  // element (p, 0)
     for (int c = 0; c < LPN; ++c) {
-      const float qv = (i < nr && c < LP) ? Q[(r0 + i) * LP + c] : 0.f;
+      const float qv = (in && c < LP) ? Q[(r0 + i) * LP + c] * sc : 0.f;
       if (bf16) {
         const __nv_bfloat16 h = __float2bfloat16_rn(qv);
         const float r1 = qv - __bfloat162float(h);
@@ -653,8 +910,23 @@ static bool make_map3(CUtensorMap* m, const void* base, bool bf16, uint64_t nx, 
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map over [nz][ny][nx] 16-bit elements stored contiguously, box {bx, ny, 1}.
+static bool make_map3_box(CUtensorMap* m, const void* base, bool bf16, uint64_t nx, uint64_t ny, uint64_t nz,
+                          uint32_t bx) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {nx, ny, nz};
+  cuuint64_t strides[2] = {nx * 2, nx * ny * 2};
+  cuuint32_t box[3] = {bx, (cuuint32_t)ny, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t cols, uint64_t rows, uint64_t ld,
-                     uint32_t bx, uint32_t by) {
+                     uint32_t bx, uint32_t by, int promo = -1) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cols, rows};
@@ -663,7 +935,7 @@ static bool make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t cols,
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_SWIZZLE_128B, promo < 0 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : (CUtensorMapL2promotion)promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -697,17 +969,58 @@ bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int
   return true;
 }
 
+bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const int64_t* d_off,
+                          const int64_t* d_toff, int64_t ntiles, int K, const void* Ms, int Jpad, int LPN, int LP,
+                          float* U, int num_sms, int* status, cudaStream_t s) {
+  const bool bf = dt == DPAR2_BF16;
+  CUtensorMap mx, mm;
+  if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, tc::SK_BK, tc::SK_BM)) return false;
+  if (!make_map3_box(&mm, Ms, bf, (uint64_t)Jpad, (uint64_t)(3 * LPN), (uint64_t)K, tc::SK_BK)) return false;
+  const int grid = (int)std::min<int64_t>(ntiles, num_sms);
+  if (grid <= 0) return true;
+  if (LPN == 32) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_sketch_seg_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::SegSmem<32>::BYTES);
+      attr = true;
+    }
+    tc::k_sketch_seg_tc<32><<<grid, 192, tc::SegSmem<32>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
+                                                                      bf ? 1 : 0, status);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc::k_sketch_seg_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::SegSmem<64>::BYTES);
+      attr = true;
+    }
+    tc::k_sketch_seg_tc<64><<<grid, 192, tc::SegSmem<64>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
+                                                                      bf ? 1 : 0, status);
+  }
+  return true;
+}
+
 int project_tc_cols(int LPN) { return LPN == 32 ? tc::ProjSmem<32>::COLS : tc::ProjSmem<64>::COLS; }
 
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
-                       float* B1, double* xpart, int nJb, int num_sms, int* status, cudaStream_t s) {
+                       float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status, cudaStream_t s,
+                       int sched) {
   const bool bf = dt == DPAR2_BF16;
   CUtensorMap mx, mq;
-  if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, 64, tc::PJ_BK)) return false;
+  // no L2 promotion: a box row (128 bytes) of X starts anywhere on a 16-byte
+  // boundary, so 256-byte promotion fetches neighbouring columns that belong to
+  // another work item (measured: 5% more DRAM reads, same time)
+  if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, 64, tc::PJ_BK,
+                (int)CU_TENSOR_MAP_L2_PROMOTION_NONE))
+    return false;
   if (!make_map3(&mq, Qs, bf, (uint64_t)tc::PJ_BK, (uint64_t)(3 * LPN), (uint64_t)(Npad / tc::PJ_BK))) return false;
-  const int64_t nitems = (int64_t)K * nJb;
-  const int grid = (int)std::min<int64_t>(nitems, num_sms);
+  int grid;
+  if (sched == 1) {  // teams of nJb CTAs, as many as fit the SMs and have slices
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms / nJb, K)) * nJb;
+  } else {
+    grid = (int)std::min<int64_t>((int64_t)K * nJb, num_sms);
+  }
   if (LPN == 32) {
     static bool attr = false;
     if (!attr) {
@@ -715,7 +1028,7 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
       attr = true;
     }
     tc::k_project_tc<32><<<grid, tc::PJ_THREADS, tc::ProjSmem<32>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
-                                                                      nJb, bf ? 1 : 0, status);
+                                                                      nJb, bf ? 1 : 0, qscale ? 1 : 0, sched, status);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -723,7 +1036,7 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
       attr = true;
     }
     tc::k_project_tc<64><<<grid, tc::PJ_THREADS, tc::ProjSmem<64>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
-                                                                      nJb, bf ? 1 : 0, status);
+                                                                      nJb, bf ? 1 : 0, qscale ? 1 : 0, sched, status);
   }
   return true;
 }

@@ -109,19 +109,23 @@ def test_compression_matches_oracle_plain_workload(api, ctx, dtype):
     assert comp.nbytes() == 4 * od.preprocessed_size([o[k + 1] - o[k] for k in range(64)], 64, 64, 10)
 
 
-def test_ragged_slices_and_tails(api, ctx):
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_ragged_slices_and_tails(api, ctx, dtype):
     """Slices shorter than the sketch width (I_k < R + p, and I_k < R), J not a
     multiple of any tile width, row counts spanning several sketch tiles and
-    projection row chunks."""
+    projection row chunks (16-bit X: the tensor-core passes, whose last row
+    chunk of a slice ends at the slice's last row, reaching before row 0 for
+    the first slices)."""
     rng = np.random.default_rng(3)
     I = np.concatenate([[1, 3, 7, 11, 19], rng.integers(20, 300, 30), [257, 513]])
     off = torch.zeros(len(I) + 1, dtype=torch.int64)
     off[1:] = torch.from_numpy(np.cumsum(I))
     J, R, p = 301, 8, 8
     d = synth.plain_parafac2(K=len(I), J=J, R=R, seed=77, offsets=off)
-    comp, Xs, om, om2 = _run(api, ctx, d, J, R, p, torch.float32)
+    comp, Xs, om, om2 = _run(api, ctx, d, J, R, p, dtype)
     t = comp.tensors()
     ref = od.compress(Xs, R, om, om2)
+    np.testing.assert_allclose(t["xnorm2"].cpu().numpy(), [np.sum(x * x) for x in Xs], rtol=1e-5)
     g1 = _stage1_recs(t, off)
     r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
     assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
@@ -144,11 +148,15 @@ def test_noiseless_lowrank_stage1_exact(api, ctx):
     assert rel_sq_err(Xs, g2) <= 1e-10
 
 
-def test_power_iteration_matches_oracle(api, ctx):
-    d = synth.plain_parafac2(K=32, Imin=50, Imax=120, J=64, R=10, seed=1001)
-    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, torch.float32, q=1)
+@pytest.mark.parametrize("dtype,q", [(torch.float32, 1), (torch.bfloat16, 1), (torch.bfloat16, 2),
+                                     (torch.float16, 1)])
+def test_power_iteration_matches_oracle(api, ctx, dtype, q):
+    # 16-bit X: B1 = Q1^T X and Y = X (B1^T M2) on the tensor cores; I_k spans
+    # several 128-row tiles with ragged ends
+    d = synth.plain_parafac2(K=32, Imin=50, Imax=300, J=64, R=10, seed=1001)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, dtype, q=q)
     t = comp.tensors()
-    ref = od.compress(Xs, 10, om, om2, q=1)
+    ref = od.compress(Xs, 10, om, om2, q=q)
     g1 = _stage1_recs(t, d["offsets"])
     r1 = [a @ np.diag(b) @ c.T for a, b, c in zip(ref["A"], ref["B"], ref["C"])]
     assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
@@ -224,6 +232,33 @@ def test_reconstruct_error_identity_and_qstep(api, ctx):
     # Upol = None: one Q-step from (H, V, W) can only lower the error
     sq2, fit2 = ctx.reconstruct_error(comp, res.H, res.V, res.W)
     assert sq2 <= sq * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_reconstruct_error_streamed_equals_identity_and_direct(api, ctx, dtype):
+    # the exact-fitness identity (no pass over X, A_k assumed orthonormal)
+    # against the streamed mode (one pass over X, A_k^T A_k formed) and the
+    # error computed directly from X and the factors in FP64
+    d = synth.plain_parafac2(K=40, Imin=20, Imax=300, J=77, R=10, seed=25)
+    comp, Xs, om, om2 = _run(api, ctx, d, 77, 10, 10, dtype)
+    res = ctx.fit(comp, max_iter=12, want_U=True)
+    Xd = padded(d["X"].cuda().float(), 77, dtype)
+    sq_i, fit_i = ctx.reconstruct_error(comp, res.H, res.V, res.W, Upol=res.Upol)
+    sq_s, fit_s = ctx.reconstruct_error(comp, res.H, res.V, res.W, Upol=res.Upol, X=Xd)
+    U = res.U.double().cpu().numpy()
+    o = [int(v) for v in d["offsets"]]
+    direct = od.squared_error(Xs, [U[o[k]:o[k + 1]] for k in range(40)], res.W.double().cpu().numpy(),
+                              res.V.double().cpu().numpy())
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert abs(sq_s - direct) <= 1e-6 * tot
+    assert abs(sq_i - sq_s) <= 1e-6 * tot
+    assert abs(fit_s - (1.0 - direct / tot)) <= 1e-6
+    # the streamed mode needs no M: it works on a compression that dropped it
+    c2 = ctx.compress(Xd, d["offsets"], R=10, p=10, omega=torch.from_numpy(om).float().cuda(),
+                      omega2=torch.from_numpy(om2).float().cuda(), flags=api.FLAG_DROP_M, J=77)
+    r2 = ctx.fit(c2, max_iter=12, fitness=False)
+    sq2, _ = ctx.reconstruct_error(c2, r2.H, r2.V, r2.W, Upol=r2.Upol, X=Xd)
+    assert abs(sq2 - sq_s) <= 1e-5 * tot
 
 
 def test_tol_stops_early_and_graph_equals_loop(api, ctx):

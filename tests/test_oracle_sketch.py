@@ -49,3 +49,15 @@ def test_gradient_matches_central_finite_differences():
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
     # the gradient is orthogonal to the invariance directions Omega -> Omega T
     assert abs(np.sum(g * (Om @ rng.standard_normal((5, 5))))) < 1e-9 * np.linalg.norm(g) * np.linalg.norm(Om) * 5
+
+
+def test_loss_is_the_rank_l_randomized_svd_residual():
+    # Alg. 1 at target rank R = l keeps all of Q^T X, so its residual is the loss
+    rng = np.random.default_rng(3)
+    Xs = _slices(rng, K=3, J=12)
+    Om = rng.standard_normal((12, 5))
+    res = []
+    for X in Xs:
+        U, S, V = od.randomized_svd(X, 5, Om)
+        res.append(np.sum((X - U @ np.diag(S) @ V.T) ** 2) / np.sum(X * X))
+    assert od.sketch_loss(Xs, Om) == pytest.approx(np.mean(res), rel=1e-10)
