@@ -74,7 +74,10 @@ typedef struct {
   uint64_t seed;  /* Philox seed of the Gaussian test matrices and of V_0 */
   int max_iter;   /* maximum ALS iterations (Alg. 3 repeat loop) */
   double tol;     /* stop when e_prev - e <= tol * e_prev; tol < 0: run max_iter */
-  int schedule;   /* stage-1 kernel variant: -1 = autotuned choice, >= 0 forced */
+  int schedule;   /* slice-to-CTA schedule of the tensor-core projection: 0 = work items
+                     round-robin over the CTAs, 1 = longest slices first, each item onto
+                     the least-loaded CTA; -1 = autotuned (both timed on the first
+                     compression of a problem shape, the faster kept by the context) */
   unsigned flags; /* DPAR2_FLAG_* */
 } dpar2_options;
 

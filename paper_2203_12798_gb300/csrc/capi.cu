@@ -100,7 +100,8 @@ size_t dtype_size(dpar2_dtype dt) { return dt == DPAR2_F32 ? 4 : 2; }
 // n int64 values host -> device through the context's pinned staging area, so
 // that the copy is asynchronous (a copy from pageable memory waits for the
 // stream first).  The area grows (after draining the stream) when a call needs more.
-void h2d_i64(dpar2_ctx* ctx, int64_t* dst, const int64_t* src, size_t n, cudaStream_t s) {
+void h2d_bytes(dpar2_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  const size_t n = (bytes + 7) / 8;  // staging words
   if (ctx->hstage_used + n > ctx->hstage_cap) {
     CK(cudaStreamSynchronize(s));
     if (ctx->hstage) cudaFreeHost(ctx->hstage);
@@ -116,8 +117,50 @@ void h2d_i64(dpar2_ctx* ctx, int64_t* dst, const int64_t* src, size_t n, cudaStr
   }
   int64_t* h = ctx->hstage + ctx->hstage_used;
   ctx->hstage_used += n;
-  std::memcpy(h, src, n * sizeof(int64_t));
-  CK(cudaMemcpyAsync(dst, h, n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  std::memcpy(h, src, bytes);
+  CK(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, s));
+}
+
+void h2d_i64(dpar2_ctx* ctx, int64_t* dst, const int64_t* src, size_t n, cudaStream_t s) {
+  h2d_bytes(ctx, dst, src, n * sizeof(int64_t), s);
+}
+
+// The projection's slice-to-CTA schedule for this call: 0 round-robin, 1
+// longest-slices-first work lists (copied to the device here).  opt_schedule
+// -1 takes the choice stored for this problem shape, if any (-1 = not tuned).
+struct ProjSched {
+  int choice = 0;
+  const int* lptr = nullptr;
+  const int* items = nullptr;
+  int nlists = 0;
+};
+
+std::string tune_key(int K, int J, int ell, dpar2_dtype dt, int64_t N, int64_t maxI) {
+  return "pj:" + std::to_string(K) + ":" + std::to_string(J) + ":" + std::to_string(ell) + ":" +
+         std::to_string((int)dt) + ":" + std::to_string(N) + ":" + std::to_string(maxI);
+}
+
+ProjSched proj_sched(dpar2_ctx* ctx, int choice, const int64_t* row_offsets, int K, int nJb, const std::string& key,
+                     cudaStream_t s) {
+  ProjSched ps;
+  ps.choice = choice;
+  if (choice != 1) return ps;
+  ps.nlists = ctx->num_sms;
+  const size_t nl = (size_t)ps.nlists + 1, ni = (size_t)K * nJb;
+  int* d_lptr = wsget<int>(ctx, "pj_lptr", nl);
+  int* d_items = wsget<int>(ctx, "pj_items", ni);
+  // the lists on the device are those of the last problem shape that used them
+  const std::string lkey = key + ":" + std::to_string(nJb) + ":" + std::to_string(ps.nlists);
+  if (ctx->pj_lists_key != lkey) {
+    std::vector<int> lptr, items;
+    project_lpt_lists(row_offsets, K, nJb, ps.nlists, lptr, items);
+    h2d_bytes(ctx, d_lptr, lptr.data(), lptr.size() * sizeof(int), s);
+    h2d_bytes(ctx, d_items, items.data(), items.size() * sizeof(int), s);
+    ctx->pj_lists_key = lkey;
+  }
+  ps.lptr = d_lptr;
+  ps.items = d_items;
+  return ps;
 }
 
 // Runs `body` with the context's device current and a private work stream
@@ -516,10 +559,14 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     // column block, norm warp)
     std::vector<int64_t> hp, htoff;
     int64_t maxPad = 0;
+    ProjSched pj;  // the projection's slice-to-CTA schedule (choice -1: tune on this call)
+    const std::string tkey = tune_key(K, J, ell, dtype, N, maxI);
     int64_t* d_poff = nullptr;
     void* Qs = nullptr;
     double* xp = nullptr;
-    const int nJb_tc = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+    int PNS = 0, POFF = 0;  // layout of the projection's Q operand
+    proj_layout(ell, &PNS, &POFF);
+    const int nJb_tc = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
     if (use_tc) {
       hp.assign(K + 1, 0);
       for (int k = 0; k < K; ++k) {
@@ -529,8 +576,15 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
       }
       d_poff = wsget<int64_t>(ctx, "poff", (size_t)K + 1);
       h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
-      Qs = wsget<uint16_t>(ctx, "Qs", (size_t)3 * LPN * hp[K]);
+      Qs = wsget<uint16_t>(ctx, "Qs", (size_t)PNS * hp[K]);
       xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
+      int choice = opt->schedule;
+      if (choice < 0) {
+        auto it = ctx->tuned.find(tkey);
+        if (it != ctx->tuned.end()) choice = it->second;
+      }
+      pj = proj_sched(ctx, choice > 1 ? 0 : choice, row_offsets, K, nJb_tc, tkey, s);
+      if (choice < 0) pj.choice = -1;
     }
     // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
     int64_t* d_toff = nullptr;
@@ -545,9 +599,9 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
         // B1 = Q1^T X, then Y_k = X_k B1_k^T on the tensor cores: X_k X_k^T Q_k =
         // X_k B1_k^T M2_k up to the upper-triangular M2_k (and the power-of-two
         // row scales of the operand), which leave the next CholeskyQR2's Q unchanged
-        launch_qsplit(Y, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
-        bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, B1, xp, nJb_tc, true,
-                                    ctx->num_sms, ctx->d_status, s);
+        launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+        bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], PNS, POFF, LP, B1, xp, nJb_tc, true,
+                                    ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
         require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
         void* Ms = wsget<uint16_t>(ctx, "Ms", (size_t)K * 3 * LPN * Jpad);
         launch_sl_rowsplit(B1, K, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr,
@@ -571,10 +625,32 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     bool projected = false;
     if (use_tc) {
       const int64_t Npad = hp[K];
-      launch_qsplit(Y, LP, LPN, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
+      launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
       tbegin(ctx, s, DPAR2_PH_PROJECT);
-      projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, LPN, LP, B1, xp, nJb_tc, true,
-                                    ctx->num_sms, ctx->d_status, s);
+      if (pj.choice < 0) {
+        // autotune: time both schedules on this call's projection (identical
+        // results) and keep the faster for this problem shape
+        cudaEvent_t ev[3];
+        for (auto& e : ev) CK(cudaEventCreate(&e));
+        const ProjSched cand[2] = {proj_sched(ctx, 0, row_offsets, K, nJb_tc, tkey, s),
+                                   proj_sched(ctx, 1, row_offsets, K, nJb_tc, tkey, s)};
+        CK(cudaEventRecord(ev[0], s));
+        for (int c = 0; c < 2; ++c) {
+          projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
+                                        true, ctx->num_sms, ctx->d_status, s, cand[c].lptr, cand[c].items,
+                                        cand[c].nlists);
+          CK(cudaEventRecord(ev[c + 1], s));
+        }
+        CK(cudaEventSynchronize(ev[2]));
+        float t0 = 0.f, t1 = 0.f;
+        CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+        for (auto& e : ev) cudaEventDestroy(e);
+        ctx->tuned[tkey] = t1 < t0 ? 1 : 0;
+      } else {
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
+                                      true, ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
+      }
       if (projected) {
         xpart = xp;
         nJb_used = nJb_tc * kProjNormWarps;
@@ -711,6 +787,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.Upol = Upol ? Upol : wsget<float>(ctx, "Upol", (size_t)K * RR);
     b.Pi = wsget<float>(ctx, "Pi", (size_t)K * RR);
     b.Prot = (opt->flags & DPAR2_FLAG_COLD_QSTEP) ? nullptr : wsget<float>(ctx, "Prot", (size_t)K * RR);
+    b.rank = static_cast<const int*>(comp->rank1.p);
     double* d6 = wsget<double>(ctx, "als_d", (size_t)6 * RR);
     b.Psi = d6;
     b.VtV = d6 + RR;
@@ -843,6 +920,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       b.Upol = wsget<float>(ctx, "re_upol", (size_t)K * RR);
       b.Pi = wsget<float>(ctx, "re_pi", (size_t)K * RR);
       b.nq = qstep_blocks(K, R, nblk);
+      b.rank = static_cast<const int*>(comp->rank1.p);
       b.pr = std::max(nblk, b.nq);
       b.part = wsget<float>(ctx, "re_part", (size_t)3 * b.pr * (2 * RR + 2));
       b.status = ctx->d_status;
@@ -885,11 +963,13 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
         }
         int64_t* d_poff = wsget<int64_t>(ctx, "re_poff", (size_t)K + 1);
         h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
-        void* Qs = wsget<uint16_t>(ctx, "re_Qs", (size_t)3 * LPN * hp[K]);
-        launch_qsplit(Ap, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
-        const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+        int PNS = 0, POFF = 0;
+        proj_layout(R, &PNS, &POFF);
+        void* Qs = wsget<uint16_t>(ctx, "re_Qs", (size_t)PNS * hp[K]);
+        launch_qsplit(Ap, LP, PNS, POFF, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+        const int nJb = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
         double* xp = wsget<double>(ctx, "re_xpart_tc", (size_t)K * nJb * kProjNormWarps);
-        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, Bs, xp, nJb,
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], PNS, POFF, LP, Bs, xp, nJb,
                                       true, ctx->num_sms, ctx->d_status, s);
         if (projected) launch_reduce_rows_f64(xp, K, nJb * kProjNormWarps, xn, s);
       }
@@ -1101,11 +1181,13 @@ dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int K, int J, const int64_t* 
       }
       int64_t* d_poff = wsget<int64_t>(ctx, "sl_poff", (size_t)K + 1);
       h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
-      void* Qs = wsget<uint16_t>(ctx, "sl_Qs", (size_t)3 * LPN * hp[K]);
-      launch_qsplit(Y, LP, LPN, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
-      const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+      int PNS = 0, POFF = 0;
+      proj_layout(ell, &PNS, &POFF);
+      void* Qs = wsget<uint16_t>(ctx, "sl_Qs", (size_t)PNS * hp[K]);
+      launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
+      const int nJb = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
       double* xp = wsget<double>(ctx, "sl_xpart_tc", (size_t)K * nJb * kProjNormWarps);
-      done = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], LPN, LP, B1, xp, nJb, true,
+      done = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], PNS, POFF, LP, B1, xp, nJb, true,
                                ctx->num_sms, ctx->d_status, s);
       require(done, DPAR2_ERR_CUDA, "tensor map encoding failed");
       launch_reduce_rows_f64(xp, K, nJb * kProjNormWarps, xn, s);
@@ -1127,7 +1209,7 @@ dpar2_status dpar2_sketch_loss_fwd(dpar2_ctx* ctx, int K, int J, const int64_t* 
     CK(cudaMemcpyAsync(h_loss, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
     // row ranges of the gradient's last pass, 64-row aligned: about one per SM,
     // a multiple of the tensor-core projection's teams (num_sms / column blocks)
-    const int nJb_g = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+    const int nJb_g = (Jp + project_tc_cols(3 * LPN) - 1) / project_tc_cols(3 * LPN);
     const int nteam = std::max(1, ctx->num_sms / nJb_g);
     const int64_t want = std::max<int64_t>(1, std::min<int64_t>(nteam * std::max(1, ctx->num_sms / nteam),
                                                                 (N + 63) / 64));
@@ -1193,7 +1275,8 @@ dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, float* gra
     float* GP = wsget<float>(ctx, "sl_GP", (size_t)np * LP * Jp);
     float* Wf = wsget<float>(ctx, "sl_W", (size_t)N * LP);
     unsigned* wmax = wsget<unsigned>(ctx, "sl_wmax", (size_t)LP);
-    launch_sl_wrows(U, Q1, d_off, K, maxI, LP, P, S, xn, grad_scale, sk, Wf, wmax, s);
+    float* bmax = wsget<float>(ctx, "sl_bmax", (size_t)sl_wrows_blocks(K, maxI) * LP);
+    launch_sl_wrows(U, Q1, d_off, K, maxI, LP, P, S, xn, grad_scale, sk, Wf, bmax, wmax, s);
     if (ctx->sk_tc) {
       const int64_t Npad = round_up64(N, 64);
       ctx->sk_poff2 = ctx->sk_off2;
@@ -1203,9 +1286,10 @@ dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, float* gra
       uint16_t* Ws = wsget<uint16_t>(ctx, "sl_Ws", (size_t)3 * LPN * Npad);
       if (N % 64) CK(cudaMemsetAsync(Ws + (N / 64) * 3 * LPN * 64, 0, (size_t)3 * LPN * 64 * 2, s));
       launch_sl_wsplit(Wf, N, LP, LPN, wmax, dtype, Ws, s);
-      const int nJb = (Jp + project_tc_cols(LPN) - 1) / project_tc_cols(LPN);
+      // W's split has the standard layout: parts LPN rows apart, N = 3 LPN
+      const int nJb = (Jp + project_tc_cols(3 * LPN) - 1) / project_tc_cols(3 * LPN);
       double* xp = wsget<double>(ctx, "sl_xpart2", (size_t)np * nJb * kProjNormWarps);
-      const bool ok = launch_project_tc(X, dtype, ctx->sk_ldx, N, d_off2, d_poff2, np, J, Jp, Ws, Npad, LPN, LP, GP,
+      const bool ok = launch_project_tc(X, dtype, ctx->sk_ldx, N, d_off2, d_poff2, np, J, Jp, Ws, Npad, 3 * LPN, LPN, LP, GP,
                                         xp, nJb, false, ctx->num_sms, ctx->d_status, s);
       require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
     } else {

@@ -47,6 +47,9 @@ struct dpar2_ctx {
   cudaMemPool_t pool = nullptr;
   int live_comps = 0;
   bool closing = false;
+  // autotuned choices (projection schedule) per problem shape
+  std::map<std::string, int> tuned;
+  std::string pj_lists_key;  // problem shape whose projection work lists are on the device
   // pinned host staging for the small index tables a call copies to the device
   // (asynchronous copies; a call's regions are reused by the next call, after
   // the synchronisation every call ends with)
@@ -90,16 +93,25 @@ int tc_lpn(int ell);  // MMA N width of the sketch: 32 or 64
 void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s);
 bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const void* omT16, int Jpad,
                       int LPN, int LP, float* Y, int num_sms, int* status, cudaStream_t s);
-// Q rows -> three 16-bit parts per slice, scaled by a power of two that
-// launch_project_tc divides out when called with qscale
-void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
-                   int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
+// Right operand of the tensor-core projection for sketch width l: MMA N (NS:
+// 48, 64, 96 or 192) and the row offset OFF between the three 16-bit parts
+// (part t of column c in row t OFF + c).
+void proj_layout(int ell, int* NS, int* OFF);
+// Q rows -> three 16-bit parts per slice in that layout, scaled by a power of
+// two that launch_project_tc divides out when called with qscale
+void launch_qsplit(const float* Q, int LP, int NS, int OFF, const int64_t* d_off, const int64_t* d_poff, int K,
+                   int64_t Npad, int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
 // X columns per work item of the tensor-core projection (nJb = ceil(Jp / cols))
-int project_tc_cols(int LPN);
+int project_tc_cols(int NS);
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
-                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
-                       float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status, cudaStream_t s,
-                       int sched = 0);  // 0: items round-robin over the CTAs; 1: teams of nJb CTAs per slice
+                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int NS, int OFF,
+                       int LP, float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status,
+                       cudaStream_t s, const int* lptr = nullptr, const int* items = nullptr, int nlists = 0);
+// Work lists of the tensor-core projection (items k nJb + jb): longest slices
+// first, each onto the least-loaded of `nlists` CTAs.  Host side; lptr gets
+// nlists + 1 entries, items K nJb.
+void project_lpt_lists(const int64_t* row_offsets, int K, int nJb, int nlists, std::vector<int>& lptr,
+                       std::vector<int>& items);
 
 // per-slice right operand (three 16-bit parts, [k][3 LPN][Jpad]); ntiles = sum_k ceil(I_k / 128)
 bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const int64_t* d_off,
@@ -114,10 +126,12 @@ void launch_sl_loss(const float* M1, const float* M2, const double* GB, const do
 // or FP32 [k][Jpad][LP]), each row times a power of two (rscale: K x LP)
 void launch_sl_rowsplit(const float* B1, int K, int Jp, int J, int Jpad, int ell, int LP, int LPN, dpar2_dtype dt,
                         void* out16, float* out32, float* rscale, cudaStream_t s);
-// W rows (FP32, N x LP) and the largest |W| per column (wmax[LP], zeroed by the call)
+// W rows (FP32, N x LP) and the largest |W| per column (wmax[LP]); bmax: scratch of
+// sl_wrows_blocks(K, maxI) x LP floats
+int64_t sl_wrows_blocks(int K, int64_t maxI);
 void launch_sl_wrows(const float* U, const float* Q1, const int64_t* d_off, int K, int64_t maxI, int LP,
                      const float* P, const float* S, const double* xn, double gscale, const float* rs, float* W,
-                     unsigned* wmax, cudaStream_t s);
+                     float* bmax, unsigned* wmax, cudaStream_t s);
 void launch_sl_wsplit(const float* W, int64_t N, int LP, int LPN, const unsigned* wmax, dpar2_dtype dt, void* out16,
                       cudaStream_t s);
 void launch_sl_gradsum(const float* part, int np, int LP, int Jp, int J, int ell, const unsigned* wmax, float* grad,
@@ -174,6 +188,7 @@ struct AlsBufs {
   float* Upol;        // K x R x R
   float* Pi;          // K x R x R  (P_k Z_k^T F^(k) E)
   float* Prot = nullptr;  // K x R x R right rotations P_k of the last Q-step (warm start), or null
+  const int* rank = nullptr;  // K stage-1 ranks (bound the rank of T_k in the Q-step), or null
   double* Psi;        // R x R  D^T V
   double* VtV;        // R x R
   double* HtH;        // R x R

@@ -62,16 +62,27 @@ __device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int
   }
 }
 
-// Two-phase reduction out[e] = sum_b part[b * pstride + e] (e < n, n <= T) by
-// the threads [t0, t0 + T) of the block: every entry's partials are split over
-// tpe = T / n threads, each of which keeps 16 loads in flight and sums them
-// with compensation in FP32 (phase 1, into red); after a barrier the tpe
-// sub-sums of an entry are added in a fixed order in FP64 (phase 2).
+// Two-phase reduction out[e] = sum_b part[b * pstride + e] (e < n) by the
+// threads [t0, t0 + T) of the block: for n <= T every entry's partials are
+// split over tpe = T / n threads, each of which keeps 16 loads in flight and
+// sums them with compensation in FP32 (phase 1, into red); after a barrier the
+// tpe sub-sums of an entry are added in a fixed order in FP64 (phase 2).  For
+// n > T each thread sums whole entries in phase 1 (large R).
 constexpr int kRedMax = 1024;
 __device__ inline void par_reduce_load(const float* __restrict__ part, int nparts, int pstride, int n, int t0, int T,
-                                       double* red) {
+                                       double* red, double* out) {
   const int t = threadIdx.x - t0;
   if (t < 0 || t >= T) return;
+  if (n > T) {
+    // more entries than threads: thread t sums entries t, t + T, ... over all
+    // partials itself (same order for every entry) and writes them to out
+    for (int e = t; e < n; e += T) {
+      float s = 0.f, c = 0.f;
+      for (int b = 0; b < nparts; ++b) neumaier(s, c, part[(int64_t)b * pstride + e]);
+      out[e] = (double)s + (double)c;
+    }
+    return;
+  }
   const int tpe = max(1, T / n);
   const int e = t / tpe, sub = t - e * tpe;
   double v = 0.0;
@@ -90,9 +101,11 @@ __device__ inline void par_reduce_load(const float* __restrict__ part, int npart
   }
   red[t] = v;
 }
+// Second phase (after a barrier): entry t = sum of its threads' partial sums.
+// Nothing to do when n > T (the first phase wrote out directly).
 __device__ inline void par_reduce_combine(int n, int t0, int T, const double* red, double* out) {
   const int t = threadIdx.x - t0;
-  if (t < 0 || t >= T) return;
+  if (t < 0 || t >= T || n > T) return;
   const int tpe = max(1, T / n);
   if (t >= n) return;  // thread t combines entry t
   const double* r = red + t * tpe;
@@ -222,7 +235,7 @@ __device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol
 __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double* __restrict__ Psi,
                         const float* __restrict__ W, const float* __restrict__ H, float* __restrict__ Upol,
                         float* __restrict__ Pi, float* __restrict__ part, int pstride, int* __restrict__ status,
-                        int want_g1) {
+                        int want_g1, const int* __restrict__ rank) {
   extern __shared__ __align__(16) float sm[];
   const int ld = R + 1, RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -263,21 +276,31 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
     __syncwarp();
     const int sw = warp_onesided_jacobi(Tm, Vm, R, ld, tol, 30);
     if (sw > 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
-    // sigma_i = ||T(:, i)||; Upol = sum_{sigma_i > 0} T(:, i) V(:, i)^T / sigma_i
-    // (the final columns are mutually orthogonal however small)
+    // sigma_i = ||T(:, i)||; Upol = sum T(:, i) V(:, i)^T / sigma_i over the
+    // rank(F~_k) = r_k largest sigma_i > 0 (the rest are rounding noise of zero
+    // singular values; the kept final columns are mutually orthogonal however
+    // small).  Fk doubles as the kept-column factors 1 / sigma_i.
     for (int i = lane; i < R; i += 32) {
       float s = 0.f;
       for (int a = 0; a < R; ++a) s = fmaf(Tm[a * ld + i], Tm[a * ld + i], s);
       A1[i] = sqrtf(s);
     }
     __syncwarp();
+    const int rk = rank ? rank[k] : R;
+    float* kinv = Up;  // R factors, overwritten below only after use
+    for (int i = lane; i < R; i += 32) {
+      const float sg = A1[i];
+      int above = 0;
+      for (int j = 0; j < R; ++j) above += (A1[j] > sg || (A1[j] == sg && j < i)) ? 1 : 0;
+      kinv[i] = (sg > 0.f && above < rk) ? 1.f / sg : 0.f;
+    }
+    __syncwarp();
+    for (int i = lane; i < R; i += 32) A1[i] = kinv[i];
+    __syncwarp();
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e % R;
       float s = 0.f;
-      for (int i = 0; i < R; ++i) {
-        const float sg = A1[i];
-        if (sg > 0.f) s = fmaf(Tm[a * ld + i] / sg, Vm[b * ld + i], s);
-      }
+      for (int i = 0; i < R; ++i) s = fmaf(Tm[a * ld + i] * A1[i], Vm[b * ld + i], s);
       Up[e] = s;
     }
     __syncwarp();
@@ -597,7 +620,7 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
   __shared__ double red[kRedMax];
   const int T = blockDim.x;
   if (it > 0) {
-    par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red);
+    par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red, W3);
     __syncthreads();
     par_reduce_combine(RR + 2, 0, T, red, W3);
     __syncthreads();
@@ -617,7 +640,7 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
     const bool f = warp_spd_factor<double>(Gm, R, ush);
     if (threadIdx.x == 0) ok = f;
   }
-  par_reduce_load(part, nq, pstride, RR, 32, T - 32, red);
+  par_reduce_load(part, nq, pstride, RR, 32, T - 32, red, G1);
   __syncthreads();
   par_reduce_combine(RR, 32, T - 32, red, G1);
   __syncthreads();
@@ -675,7 +698,7 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
     const bool f = warp_spd_factor<double>(Gm, R, ush);
     if (threadIdx.x == 0) ok = f;
   }
-  par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red);
+  par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red, g);
   __syncthreads();
   par_reduce_combine(RR, 32, T - 32, red, g);
   __syncthreads();
@@ -961,7 +984,7 @@ void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
   const int R = b.R, nw = als_warps(R);
   if (launch_qstep_reg(b, b.part, 2 * R * R + 2, 0, s)) return;
   k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part,
-                                                     2 * R * R + 2, b.status, 0);
+                                                     2 * R * R + 2, b.status, 0, b.rank);
 }
 
 // One iteration = 5 launches: Q-step (+ Lemma 1 partials), H update (closing
@@ -975,7 +998,7 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   float* p3 = b.part + (size_t)2 * b.pr * ps;
   if (!launch_qstep_reg(b, p1, ps, 1, s))
     k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
-                                                       b.status, 1);
+                                                       b.status, 1, b.rank);
   int insh = 0;
   const size_t psm = update_smem(R, &insh);
   k_update_h<<<1, 1024, psm, s>>>(R, p1, b.nq, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small,

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
                                                    const float* __restrict__ H, float* __restrict__ Upol,
                                                    float* __restrict__ Pi, float* __restrict__ part, int pstride,
                                                    int* __restrict__ status, int want_g1,
-                                                   float* __restrict__ Prot) {
+                                                   float* __restrict__ Prot, const int* __restrict__ rank) {
   constexpr int G = 32 / R;  // problems per warp
   constexpr int RR = R * R;
   constexpr int M = R + (R & 1);  // round-robin players (one dummy when R is odd)
@@ -220,15 +220,25 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
         if (i < Ra) Prot[k * RaRa + i * Ra + c] = v[i];
     }
 
-    // ---- polar factor Upol = sum_i z_i v_i^T over sigma_i > 0.  The final
-    // columns are mutually orthogonal however small, so every nonzero one is
-    // kept (an FP32-level cut would drop directions of ill-conditioned T_k
-    // that an FP64 SVD resolves); only zero (padded) columns are left out.
+    // ---- polar factor Upol = sum_i z_i v_i^T over the rank(F~_k) largest
+    // sigma_i > 0.  rank(T_k) <= rank(F~_k) = the slice's stage-1 rank r_k, so
+    // the other R - r_k final columns are rounding noise of a zero singular
+    // value (a slice with I_k < R) and are left out; of the r_k kept ones every
+    // nonzero column counts, however small (the final columns are mutually
+    // orthogonal, and an FP32-level cut would drop directions of ill-conditioned
+    // T_k that an FP64 SVD resolves).  Padded columns are zero.
     float s2 = 0.f;
 #pragma unroll
     for (int i = 0; i < R; ++i) s2 = fmaf(t[i], t[i], s2);
     const float sg = sqrtf(s2);
-    const float inv = sg > 0.f ? 1.f / sg : 0.f;
+    const int rk = (act && rank) ? rank[k] : Ra;
+    int above = 0;  // columns of this problem ahead of column c in sigma order
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float sj = __shfl_sync(FULL, sg, (g * R + j) & 31);
+      above += (sj > sg || (sj == sg && j < c)) ? 1 : 0;
+    }
+    const float inv = (sg > 0.f && above < rk) ? 1.f / sg : 0.f;
     __syncwarp();
     if (lane_act) {
 #pragma unroll
@@ -327,7 +337,7 @@ static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaSt
     attr = true;
   }
   k_qstep_reg<R><<<b.nq, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                             b.status, want_g1, b.Prot);
+                                             b.status, want_g1, b.Prot, b.rank);
 }
 
 template <int R>

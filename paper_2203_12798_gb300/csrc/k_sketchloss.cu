@@ -147,6 +147,22 @@ __device__ __forceinline__ void split3<__half>(float v, __half* o0, __half* o1, 
 // [k][3 LPN][Jpad] (row t LPN + i holds part t of B1 row i); otherwise FP32
 // [k][Jpad][LP].  One warp per row of B1, reading it twice (max, then split).
 template <typename H>
+__device__ __forceinline__ uint2 split4(float4 v, uint2* mid, uint2* lo) {
+  H h[4], m[4], l[4];
+  split3<H>(v.x, &h[0], &m[0], &l[0]);
+  split3<H>(v.y, &h[1], &m[1], &l[1]);
+  split3<H>(v.z, &h[2], &m[2], &l[2]);
+  split3<H>(v.w, &h[3], &m[3], &l[3]);
+  uint2 a, b, c;
+  memcpy(&a, h, 8);
+  memcpy(&b, m, 8);
+  memcpy(&c, l, 8);
+  *mid = b;
+  *lo = c;
+  return a;
+}
+
+template <typename H>
 __global__ void __launch_bounds__(256) k_sl_rowsplit(const float* __restrict__ B1, int K, int Jp, int J, int Jpad,
                                                      int ell, int LP, int LPN, H* __restrict__ out16,
                                                      float* __restrict__ out32, float* __restrict__ rscale) {
@@ -157,18 +173,35 @@ __global__ void __launch_bounds__(256) k_sl_rowsplit(const float* __restrict__ B
   const int k = (int)(gw / rows), i = (int)(gw % rows);
   const float* b = B1 + ((int64_t)k * LP + i) * Jp;
   const bool live = i < ell;
+  // four columns per lane: B1 rows (pitch Jp, a multiple of 4) and the 16-bit
+  // rows (pitch Jpad, a multiple of 32) are 16- and 8-byte aligned
+  auto load4 = [&](int j) -> float4 {
+    if (!live || j >= J) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j + 3 < J) return *reinterpret_cast<const float4*>(b + j);
+    return make_float4(b[j], j + 1 < J ? b[j + 1] : 0.f, j + 2 < J ? b[j + 2] : 0.f, 0.f);
+  };
   float mx = 0.f;
-  if (live)
-    for (int j = lane; j < J; j += 32) mx = fmaxf(mx, fabsf(b[j]));
+  for (int j = 4 * lane; j < J; j += 128) {
+    const float4 v = load4(j);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const float r = range_scale(mx);
   if (i < LP && lane == 0) rscale[(int64_t)k * LP + i] = r;
   if (out16) {
     H* o = out16 + (int64_t)k * 3 * LPN * Jpad;
-    for (int j = lane; j < Jpad; j += 32) {
-      const float v = (live && j < J) ? b[j] * r : 0.f;
-      split3<H>(v, o + (int64_t)i * Jpad + j, o + (int64_t)(LPN + i) * Jpad + j, o + (int64_t)(2 * LPN + i) * Jpad + j);
+    for (int j = 4 * lane; j < Jpad; j += 128) {
+      float4 v = load4(j);
+      v.x *= r;
+      v.y *= r;
+      v.z *= r;
+      v.w *= r;
+      uint2 mid, lo;
+      const uint2 hi = split4<H>(v, &mid, &lo);
+      *reinterpret_cast<uint2*>(o + (int64_t)i * Jpad + j) = hi;
+      *reinterpret_cast<uint2*>(o + (int64_t)(LPN + i) * Jpad + j) = mid;
+      *reinterpret_cast<uint2*>(o + (int64_t)(2 * LPN + i) * Jpad + j) = lo;
     }
   } else {
     for (int j = lane; j < Jpad; j += 32) out32[((int64_t)k * Jpad + j) * LP + i] = (live && j < J) ? b[j] * r : 0.f;
@@ -178,18 +211,19 @@ __global__ void __launch_bounds__(256) k_sl_rowsplit(const float* __restrict__ B
 // ----------------------------------------------------------- W rows ----
 // W_k = c_k (V_k diag(r_k)^-1 P_k - Q1_k S_k) row by row, V_k = X_k B1_k^T diag(r_k)
 // from pass 3 (so V_k diag(r_k)^-1 P_k = X_k Mk), c_k = -2 g / (K ||X_k||^2); FP32
-// rows N x LP, and the largest |W| of every column (FP32 bit patterns:
-// order-preserving unsigned for |.|) into wmax[c].  P and S are read from
-// shared memory four columns at a time.  Grid (ceil(maxI / 128), K).
+// rows N x LP, and each block's largest |W| of every column into
+// bmax[block][c] (k_sl_colmax reduces them).  P and S are read from shared
+// memory four columns at a time.  Grid (ceil(maxI / 128), K).
 template <int LP>
 __global__ void __launch_bounds__(128) k_sl_wrows(const float* __restrict__ U, const float* __restrict__ Q1,
                                                   const int64_t* __restrict__ off, const float* __restrict__ P,
                                                   const float* __restrict__ S, const double* __restrict__ xn,
                                                   double gscale, int K, const float* __restrict__ rs,
-                                                  float* __restrict__ W, unsigned* __restrict__ wmax) {
+                                                  float* __restrict__ W, float* __restrict__ bmax) {
   __shared__ __align__(16) float ps[LP * LP];
   __shared__ __align__(16) float ss[LP * LP];
   __shared__ float inv[LP];
+  __shared__ float red[4][LP];
   const int k = blockIdx.y;
   for (int e = threadIdx.x; e < LP * LP; e += 128) {
     ps[e] = P[(int64_t)k * LP * LP + e];
@@ -244,7 +278,31 @@ __global__ void __launch_bounds__(128) k_sl_wrows(const float* __restrict__ U, c
     float m = fabsf(w[cc]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f && m < 3.0e38f) atomicMax(wmax + cc, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][cc] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < LP) {
+    const float m = fmaxf(fmaxf(red[0][threadIdx.x], red[1][threadIdx.x]), fmaxf(red[2][threadIdx.x], red[3][threadIdx.x]));
+    bmax[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * LP + threadIdx.x] = m;
+  }
+}
+
+// wmax[c] = max over the nb block maxima of column c (FP32 bit pattern of a
+// non-negative float: atomicMax on it is order-independent).  Each block
+// reduces a strided share of the rows, then one atomic per column.
+__global__ void k_sl_colmax(const float* __restrict__ bmax, int64_t nb, int LP, unsigned* __restrict__ wmax) {
+  __shared__ float red[1024];
+  const int c = threadIdx.x % LP, lanes = blockDim.x / LP;
+  float m = 0.f;
+  if (threadIdx.x < lanes * LP)
+    for (int64_t b = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x / LP); b < nb; b += (int64_t)gridDim.x * lanes)
+      m = fmaxf(m, bmax[b * LP + c]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x < LP) {
+    float t = 0.f;
+    for (int i = 0; i < lanes; ++i) t = fmaxf(t, red[i * LP + threadIdx.x]);
+    if (t > 0.f && t < 3.0e38f) atomicMax(wmax + threadIdx.x, __float_as_uint(t));
   }
 }
 
@@ -321,17 +379,20 @@ void launch_sl_rowsplit(const float* B1, int K, int Jp, int J, int Jpad, int ell
 
 template <int LP>
 static void sl_wrows_lp(const float* U, const float* Q1, const int64_t* d_off, int K, int64_t maxI, const float* P,
-                        const float* S, const double* xn, double gscale, const float* rs, float* W, unsigned* wmax,
+                        const float* S, const double* xn, double gscale, const float* rs, float* W, float* bmax,
                         cudaStream_t s) {
   dim3 grid((unsigned)std::max<int64_t>(1, (maxI + 127) / 128), (unsigned)K);
-  k_sl_wrows<LP><<<grid, 128, 0, s>>>(U, Q1, d_off, P, S, xn, gscale, K, rs, W, wmax);
+  k_sl_wrows<LP><<<grid, 128, 0, s>>>(U, Q1, d_off, P, S, xn, gscale, K, rs, W, bmax);
 }
+
+int64_t sl_wrows_blocks(int K, int64_t maxI) { return std::max<int64_t>(1, (maxI + 127) / 128) * K; }
 
 void launch_sl_wrows(const float* U, const float* Q1, const int64_t* d_off, int K, int64_t maxI, int LP,
                      const float* P, const float* S, const double* xn, double gscale, const float* rs, float* W,
-                     unsigned* wmax, cudaStream_t s) {
+                     float* bmax, unsigned* wmax, cudaStream_t s) {
+  DP2_LP_SWITCH(LP, (sl_wrows_lp<L>(U, Q1, d_off, K, maxI, P, S, xn, gscale, rs, W, bmax, s)));
   cudaMemsetAsync(wmax, 0, (size_t)LP * sizeof(unsigned), s);
-  DP2_LP_SWITCH(LP, (sl_wrows_lp<L>(U, Q1, d_off, K, maxI, P, S, xn, gscale, rs, W, wmax, s)));
+  k_sl_colmax<<<64, (1024 / LP) * LP, 0, s>>>(bmax, sl_wrows_blocks(K, maxI), LP, wmax);
 }
 
 void launch_sl_wsplit(const float* W, int64_t N, int LP, int LPN, const unsigned* wmax, dpar2_dtype dt, void* out16,

@@ -32,6 +32,11 @@
 //            epilogue adds: FP32 accuracy from 16-bit operands.
 #include <cuda.h>
 
+#include <algorithm>
+#include <functional>
+#include <queue>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -550,28 +555,45 @@ constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
 constexpr int PJ_NORM_WARPS = kProjNormWarps;          // warps 6 .. 6 + PJ_NORM_WARPS - 1
 constexpr int PJ_THREADS = 32 * (6 + PJ_NORM_WARPS);
 
-template <int LPN>
+template <int NS_>
 struct ProjSmem {
-  // HV column halves of PJ_BM columns per work item (two when their double-
-  // buffered accumulators fit the 512 TMEM columns): wider rows per TMA load
-  // and one Q tile per stage for both halves
-  static constexpr int HV = (4 * 3 * LPN <= 512) ? 2 : 1;
-  static constexpr int NS = 3 * LPN;               // hi / mid / lo splits
+  // NS = MMA N: the three 16-bit parts of the Q rows, part t of column c in
+  // row t OFF + c (OFF = l rounded up to 4, or 32 / 64), padded to 48, 64, 96
+  // or 192.  HV column halves of PJ_BM columns per work item, as many as let
+  // the double-buffered accumulators (2 HV NS columns) fit TMEM's 512: wider
+  // rows per TMA load, one Q tile per stage for all halves.
+  static constexpr int NS = NS_;
+  static constexpr int HV = NS <= 64 ? 4 : (NS <= 128 ? 2 : 1);
   static constexpr int A = HV * PJ_BM * PJ_BK * 2;  // 2 HV 64-column boxes of 64 rows, 8 KB each
   static constexpr int B = NS * PJ_BK * 2;
-  static constexpr int STAGES = HV == 2 ? 4 : PJ_STAGES;
+  static constexpr int FIT = (227 * 1024 - 1024 - 256) / (A + B);
+  static constexpr int STAGES = FIT > PJ_STAGES ? PJ_STAGES : FIT;
   static constexpr int BYTES = 1024 + STAGES * (A + B) + 256;
   static constexpr int COLS = HV * PJ_BM;          // columns of X per work item
 };
 
-template <int LPN>
+// 4 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (no wait)
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int NS>
 __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_constant__ CUtensorMap tmX,
                                                        const __grid_constant__ CUtensorMap tmQ,
                                                        const int64_t* __restrict__ off,
                                                        const int64_t* __restrict__ poff, int K, int J, int Jp,
-                                                       int LP, float* __restrict__ B1, double* __restrict__ xpart,
-                                                       int nJb, int bf16, int qscale, int sched, int* status) {
-  using S = ProjSmem<LPN>;
+                                                       int LP, int OFF, float* __restrict__ B1,
+                                                       double* __restrict__ xpart, int nJb, int bf16, int qscale,
+                                                       const int* __restrict__ lptr, const int* __restrict__ items,
+                                                       int* status) {
+  using S = ProjSmem<NS>;
   constexpr int ST = S::STAGES;
   constexpr uint32_t NCOL = 2 * S::HV * S::NS <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
@@ -585,19 +607,16 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Work items (slice k, column block jb), two schedules:
-  //   sched 0  items k nJb + jb dealt round-robin over the CTAs;
-  //   sched 1  teams of nJb CTAs: CTA b owns column block b % nJb of slices
-  //            team, team + nteam, ... (team = b / nJb), so the nJb items of a
-  //            slice run side by side with equal work (the host launches a
-  //            multiple of nJb CTAs).
-  const bool teams = sched == 1;
-  const int nteam = teams ? (int)gridDim.x / nJb : 1;
-  const int64_t it0 = teams ? (int64_t)(blockIdx.x / nJb) : (int64_t)blockIdx.x;
-  const int64_t its = teams ? nteam : (int64_t)gridDim.x;
-  const int64_t itn = teams ? ((int)(blockIdx.x / nJb) < nteam ? K : 0) : (int64_t)K * nJb;
-#define PJ_ITEM(it) const int k = teams ? (int)(it) : (int)((it) / nJb); \
-  const int jb = teams ? (int)(blockIdx.x % nJb) : (int)((it) % nJb); (void)jb
+  // Work items (slice k, column block jb) numbered k nJb + jb, two schedules:
+  //   lptr == null  dealt round-robin over the CTAs;
+  //   otherwise     CTA b takes items[lptr[b] .. lptr[b + 1]) in order (a
+  //                 schedule the host builds, e.g. longest slices first onto
+  //                 the least-loaded CTA).
+  const int64_t it0 = lptr ? (int64_t)lptr[blockIdx.x] : (int64_t)blockIdx.x;
+  const int64_t its = lptr ? 1 : (int64_t)gridDim.x;
+  const int64_t itn = lptr ? (int64_t)lptr[blockIdx.x + 1] : (int64_t)K * nJb;
+#define PJ_ITEM(it) const int64_t item_ = lptr ? (int64_t)items[it] : (it); \
+  const int k = (int)(item_ / nJb); const int jb = (int)(item_ % nJb); (void)jb
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -729,20 +748,49 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       for (int h = 0; h < S::HV; ++h) {
         const int j = jb * S::COLS + h * PJ_BM + q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + acc * S::HV * S::NS + h * S::NS;
-        for (int g = 0; g < LPN / 32; ++g) {
-          float v[32], w[32];
-          tmem_ld32(tl + g * 32, v);
-          tmem_ld32(tl + LPN + g * 32, w);
+        if constexpr (NS >= 96) {
+          // parts 32 or 64 columns apart (OFF = NS / 3): whole 32-column loads
+          for (int g = 0; g < OFF / 32; ++g) {
+            float v[32], w[32];
+            tmem_ld32(tl + g * 32, v);
+            tmem_ld32(tl + OFF + g * 32, w);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += w[i];
-          tmem_ld32(tl + 2 * LPN + g * 32, w);
+            for (int i = 0; i < 32; ++i) v[i] += w[i];
+            tmem_ld32(tl + 2 * OFF + g * 32, w);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += w[i];
-          if (j < Jp) {
-            float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
+            for (int i = 0; i < 32; ++i) v[i] += w[i];
+            if (j < Jp) {
+              float* dst = B1 + ((int64_t)k * LP + g * 32) * Jp + j;
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i] * inv;
+              for (int i = 0; i < 32; ++i)
+                if (g * 32 + i < LP) dst[(int64_t)i * Jp] = v[i] * inv;
+            }
+          }
+        } else {
+          // compact parts (OFF <= 21, a multiple of 4): the three parts of
+          // column c sit at c, OFF + c and 2 OFF + c, inside this half's NS columns
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {  // 16 output rows at a time
+            float a[16], b[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4)
+              if (16 * g + 4 * q4 < OFF) {
+                tmem_ld4(tl + 16 * g + 4 * q4, a + 4 * q4);
+                tmem_ld4(tl + OFF + 16 * g + 4 * q4, b + 4 * q4);
+              }
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] += b[i];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4)
+              if (16 * g + 4 * q4 < OFF) tmem_ld4(tl + 2 * OFF + 16 * g + 4 * q4, b + 4 * q4);
+            tmem_wait_ld();
+            if (j < Jp) {
+              float* dst = B1 + ((int64_t)k * LP + 16 * g) * Jp + j;
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (16 * g + i < LP) dst[(int64_t)i * Jp] = 16 * g + i < OFF ? (a[i] + b[i]) * inv : 0.f;
+            }
           }
         }
       }
@@ -823,18 +871,18 @@ __global__ void k_omega_t16(const float* __restrict__ om, int Jpad, int LP, int 
 }
 
 // Q1 rows (N x LP FP32) -> three exact-sum 16-bit parts, transposed to
-// (3 LPN) x Npad with every slice padded to a multiple of 64 rows.
-// Layout of the split: 64-row chunks of all 3 LPN columns stored contiguously,
-// element (p, c) at ((p / 64) 3 LPN + c) 64 + p % 64, so that one chunk (the B
-// operand of one projection stage) is a single contiguous 12 KB (LPN = 32) block.
+// NSQ x Npad with every slice padded to a multiple of 64 rows; part t of
+// column c is row t OFF + c (rows from 3 OFF on are zero).
+// Layout of the split: 64-row chunks of all NSQ rows stored contiguously,
+// element (p, r) at ((p / 64) NSQ + r) 64 + p % 64, so that one chunk (the B
+// operand of one projection stage) is a single contiguous NSQ x 128-byte block.
 // The last chunk of a slice holds the slice's last 64 rows (the projection
 // reads X there from the slice's end backwards), zeros where they repeat
 // rows of the chunk before it.
-__global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int64_t* __restrict__ off,
+__global__ void k_qsplit(const float* __restrict__ Q, int LP, int NSQ, int OFF, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ poff, int K, int64_t Npad, int bf16, void* out) {
   const int k = blockIdx.y;
   const int64_t p0 = poff[k], p1 = poff[k + 1], r0 = off[k], nr = off[k + 1] - r0;
-  const int NSQ = 3 * LPN;
   const int64_t last0 = p1 - p0 - PJ_BK;  // first padded row of the last chunk
   const float sc = qsplit_scale(nr);
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
@@ -846,7 +894,7 @@ __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int
       in = i >= last0;
     }
     const int64_t cb = (p / PJ_BK) * NSQ * PJ_BK + (p % PJ_BK);  // element (p, 0)
-    for (int c = 0; c < LPN; ++c) {
+    for (int c = 0; c < OFF; ++c) {
       const float qv = (in && c < LP) ? Q[(r0 + i) * LP + c] * sc : 0.f;
       if (bf16) {
         const __nv_bfloat16 h = __float2bfloat16_rn(qv);
@@ -855,8 +903,8 @@ __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int
         const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
         __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + cb;
         o[(int64_t)c * PJ_BK] = h;
-        o[(int64_t)(LPN + c) * PJ_BK] = m;
-        o[(int64_t)(2 * LPN + c) * PJ_BK] = l;
+        o[(int64_t)(OFF + c) * PJ_BK] = m;
+        o[(int64_t)(2 * OFF + c) * PJ_BK] = l;
       } else {
         const __half h = __float2half_rn(qv);
         const float r1 = qv - __half2float(h);
@@ -864,9 +912,13 @@ __global__ void k_qsplit(const float* __restrict__ Q, int LP, int LPN, const int
         const __half l = __float2half_rn(r1 - __half2float(m));
         __half* o = reinterpret_cast<__half*>(out) + cb;
         o[(int64_t)c * PJ_BK] = h;
-        o[(int64_t)(LPN + c) * PJ_BK] = m;
-        o[(int64_t)(2 * LPN + c) * PJ_BK] = l;
+        o[(int64_t)(OFF + c) * PJ_BK] = m;
+        o[(int64_t)(2 * OFF + c) * PJ_BK] = l;
       }
+    }
+    for (int r = 3 * OFF; r < NSQ; ++r) {  // padding rows of the chunk
+      if (bf16) reinterpret_cast<__nv_bfloat16*>(out)[cb + (int64_t)r * PJ_BK] = __float2bfloat16_rn(0.f);
+      else reinterpret_cast<__half*>(out)[cb + (int64_t)r * PJ_BK] = __float2half_rn(0.f);
     }
   }
 }
@@ -1000,12 +1052,74 @@ bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N,
   return true;
 }
 
-int project_tc_cols(int LPN) { return LPN == 32 ? tc::ProjSmem<32>::COLS : tc::ProjSmem<64>::COLS; }
+void project_lpt_lists(const int64_t* off, int K, int nJb, int nlists, std::vector<int>& lptr,
+                       std::vector<int>& items) {
+  std::vector<int> order(K);
+  for (int k = 0; k < K; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+  // an item costs its slice's rows plus one 64-row chunk of fixed overhead
+  using Load = std::pair<int64_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < nlists; ++c) heap.push({0, c});
+  std::vector<std::vector<int>> lists(nlists);
+  for (int k : order) {
+    const int64_t cost = off[k + 1] - off[k] + 64;
+    for (int jb = 0; jb < nJb; ++jb) {
+      Load l = heap.top();
+      heap.pop();
+      lists[l.second].push_back(k * nJb + jb);
+      heap.push({l.first + cost, l.second});
+    }
+  }
+  lptr.assign(nlists + 1, 0);
+  items.clear();
+  items.reserve((size_t)K * nJb);
+  for (int c = 0; c < nlists; ++c) {
+    items.insert(items.end(), lists[c].begin(), lists[c].end());
+    lptr[c + 1] = (int)items.size();
+  }
+}
+
+void proj_layout(int ell, int* NS, int* OFF) {
+  if (ell > 32) {
+    *NS = 192;
+    *OFF = 64;
+    return;
+  }
+  // compact (parts OFF = l rounded up to 4 apart) where that saves MMA width,
+  // else parts 32 rows apart
+  const int o = (ell + 3) / 4 * 4;
+  *OFF = 3 * o <= 64 ? o : 32;
+  *NS = 3 * o <= 48 ? 48 : (3 * o <= 64 ? 64 : 96);
+}
+
+int project_tc_cols(int NS) {
+  switch (NS) {
+    case 48: return tc::ProjSmem<48>::COLS;
+    case 64: return tc::ProjSmem<64>::COLS;
+    case 96: return tc::ProjSmem<96>::COLS;
+    default: return tc::ProjSmem<192>::COLS;
+  }
+}
+
+template <int NS>
+static void project_launch(const CUtensorMap& mx, const CUtensorMap& mq, int grid, const int64_t* d_off,
+                           const int64_t* d_poff, int K, int J, int Jp, int LP, int OFF, float* B1, double* xpart,
+                           int nJb, int bf, int qs, const int* lptr, const int* items, int* status, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_project_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<NS>::BYTES);
+    attr = true;
+  }
+  tc::k_project_tc<NS><<<grid, tc::PJ_THREADS, tc::ProjSmem<NS>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, OFF,
+                                                                           B1, xpart, nJb, bf, qs, lptr, items, status);
+}
 
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
-                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int LPN, int LP,
-                       float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status, cudaStream_t s,
-                       int sched) {
+                       const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int NS, int OFF,
+                       int LP, float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status,
+                       cudaStream_t s, const int* lptr, const int* items, int nlists) {
   const bool bf = dt == DPAR2_BF16;
   CUtensorMap mx, mq;
   // no L2 promotion: a box row (128 bytes) of X starts anywhere on a 16-byte
@@ -1014,29 +1128,15 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
   if (!make_map(&mx, X, bf, (uint64_t)J, (uint64_t)N, (uint64_t)ldx, 64, tc::PJ_BK,
                 (int)CU_TENSOR_MAP_L2_PROMOTION_NONE))
     return false;
-  if (!make_map3(&mq, Qs, bf, (uint64_t)tc::PJ_BK, (uint64_t)(3 * LPN), (uint64_t)(Npad / tc::PJ_BK))) return false;
-  int grid;
-  if (sched == 1) {  // teams of nJb CTAs, as many as fit the SMs and have slices
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms / nJb, K)) * nJb;
-  } else {
-    grid = (int)std::min<int64_t>((int64_t)K * nJb, num_sms);
-  }
-  if (LPN == 32) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc::k_project_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<32>::BYTES);
-      attr = true;
-    }
-    tc::k_project_tc<32><<<grid, tc::PJ_THREADS, tc::ProjSmem<32>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
-                                                                      nJb, bf ? 1 : 0, qscale ? 1 : 0, sched, status);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc::k_project_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<64>::BYTES);
-      attr = true;
-    }
-    tc::k_project_tc<64><<<grid, tc::PJ_THREADS, tc::ProjSmem<64>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, B1, xpart,
-                                                                      nJb, bf ? 1 : 0, qscale ? 1 : 0, sched, status);
+  if (!make_map3(&mq, Qs, bf, (uint64_t)tc::PJ_BK, (uint64_t)NS, (uint64_t)(Npad / tc::PJ_BK))) return false;
+  const int grid = lptr ? nlists : (int)std::min<int64_t>((int64_t)K * nJb, num_sms);
+  const int bfi = bf ? 1 : 0, qs = qscale ? 1 : 0;
+  switch (NS) {
+    case 48: project_launch<48>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
+    case 64: project_launch<64>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
+    case 96: project_launch<96>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
+    case 192: project_launch<192>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
+    default: return false;
   }
   return true;
 }
@@ -1047,10 +1147,10 @@ void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtyp
                                                                                      dt == DPAR2_BF16 ? 1 : 0, out);
 }
 
-void launch_qsplit(const float* Q, int LP, int LPN, const int64_t* d_off, const int64_t* d_poff, int K, int64_t Npad,
-                   int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s) {
+void launch_qsplit(const float* Q, int LP, int NS, int OFF, const int64_t* d_off, const int64_t* d_poff, int K,
+                   int64_t Npad, int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s) {
   dim3 grid((unsigned)std::max<int64_t>(1, (maxPad + 127) / 128), K);
-  tc::k_qsplit<<<grid, 128, 0, s>>>(Q, LP, LPN, d_off, d_poff, K, Npad, dt == DPAR2_BF16 ? 1 : 0, out);
+  tc::k_qsplit<<<grid, 128, 0, s>>>(Q, LP, NS, OFF, d_off, d_poff, K, Npad, dt == DPAR2_BF16 ? 1 : 0, out);
 }
 
 }  // namespace dp2

@@ -162,6 +162,26 @@ def test_power_iteration_matches_oracle(api, ctx, dtype, q):
     assert abs(rel_sq_err(Xs, g1) - rel_sq_err(Xs, r1)) <= 1e-5
 
 
+def test_projection_schedules_agree(api, ctx):
+    # round-robin work items, longest-first work lists and the autotuned
+    # choice compute every (slice, column block) item the same way
+    rng = np.random.default_rng(5)
+    I = np.concatenate([rng.integers(20, 200, 60), [1500, 900, 3000]])
+    off = torch.zeros(len(I) + 1, dtype=torch.int64)
+    off[1:] = torch.from_numpy(np.cumsum(I))
+    d = synth.plain_parafac2(K=len(I), J=300, R=10, seed=31, offsets=off)
+    Xd = padded(d["X"].cuda().float(), 300, torch.bfloat16)
+    om = synth.gaussian_matrix(300, 20, seed=2).cuda()
+    om2 = synth.gaussian_matrix(len(I) * 10, 20, seed=3).cuda()
+    outs = []
+    for sch in (0, 1, -1, -1):
+        c = ctx.compress(Xd, off, R=10, p=10, omega=om, omega2=om2, J=300, schedule=sch)
+        outs.append(c.tensors())
+    for t in outs[1:]:
+        for name in ("A", "M", "D", "Ft", "xnorm2"):
+            assert torch.equal(t[name], outs[0][name]), name
+
+
 def test_per_slice_launches_match_grouped(api, ctx):
     d = synth.plain_parafac2(K=20, Imin=50, Imax=200, J=64, R=10, seed=11)
     c1, Xs, _, _ = _run(api, ctx, d, 64, 10, 10, torch.float32)
@@ -213,6 +233,21 @@ def test_fit_matches_oracle(api, ctx, dtype):
     for k in range(0, 64, 7):
         Q = A[o[k]:o[k + 1]] @ Up[k]
         np.testing.assert_allclose(Q.T @ Q, np.eye(10), atol=5e-5)
+
+
+@pytest.mark.parametrize("R", [32, 40, 50])
+def test_large_rank_fit_matches_oracle(api, ctx, R):
+    # ranks past one warp's width (R^2 partial sums beyond the reducing
+    # threads, Q-step in shared memory for R > 32), sketch widths up to 60
+    J, p = 160, 10
+    d = synth.plain_parafac2(K=30, Imin=40, Imax=180, J=J, R=R, seed=1004)
+    comp, Xs, om, om2 = _run(api, ctx, d, J, R, p, torch.bfloat16)
+    V0 = synth.gaussian_matrix(J, R, seed=99, representable16=False).cuda()
+    res = ctx.fit(comp, max_iter=8, V0=V0)
+    ref = od.dpar2_als(od.compress(Xs, R, om, om2), V0.double().cpu().numpy(), max_iter=8)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert np.max(np.abs(np.array(res.losses) - np.array(ref["losses"]))) <= 5e-5 * tot
+    assert abs(res.fitness - od.fitness(Xs, ref["U"], ref["W"], ref["V"])) <= 1e-4
 
 
 def test_reconstruct_error_identity_and_qstep(api, ctx):
