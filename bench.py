@@ -35,7 +35,10 @@ METRIC = "DPar2 time-to-fit (s) & stage-1 HBM GB/s vs peak; chosen vs plain at Î
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # stage-1 kernels on this workload, from one ncu capture (profiles/), valid
 # only for the kernel source they were taken on (sha1 of k_tc.cu).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    "project": {"bytes": 16.83e9, "k_tc_sha1": "36da4d79be3a28e05103c3f2efc1d71b8695d531"},
+    "sketch": {"bytes": 13.70e9, "k_tc_sha1": "36da4d79be3a28e05103c3f2efc1d71b8695d531"},
+}
 WORKLOADS = {
     # FMA-shaped spectrogram magnitudes (the default, headline workload)
     "spectrogram": dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=10, q=0, seed=1002, iters=32),
@@ -179,7 +182,8 @@ def measured_traffic(kernel: str, args):
     import hashlib
 
     t = MEASURED_TRAFFIC.get(kernel)
-    if not t or args.K != WORKLOAD["K"] or args.dtype != "bf16":
+    if (not t or WORKLOAD["name"] != "spectrogram" or args.K != 8000 or WORKLOAD["R"] != 10 or WORKLOAD["q"] != 0
+            or args.dtype != "bf16"):
         return None
     src = open(os.path.join(ROOT, "paper_2203_12798_gb300", "csrc", "k_tc.cu"), "rb").read()
     return t["bytes"] if hashlib.sha1(src).hexdigest() == t["k_tc_sha1"] else None
