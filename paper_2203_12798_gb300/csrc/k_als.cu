@@ -178,7 +178,12 @@ __global__ void k_atb_fin(int nb, int nn, const float* __restrict__ part, double
 // the right, accumulated into V (starts at I).  Parallel (round-robin)
 // ordering; lane i < m/2 owns one column pair per step.  Returns sweeps used
 // (> max_sweeps when not converged).
-__device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol, int max_sweeps) {
+// Convergence is judged on the rk largest columns (by norm at the start of a
+// sweep; n <= 64): with rank(T) <= rk the other columns shrink to rounding
+// noise and keep rotating among themselves without passing the test.  cn:
+// n floats of warp scratch.
+__device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol, int max_sweeps, int rk,
+                                    float* cn) {
   const int lane = threadIdx.x & 31;
   const int m = n + (n & 1);
   for (int e = lane; e < n * n; e += 32) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.f : 0.f;
@@ -186,6 +191,29 @@ __device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     float worst = 0.f;
+    unsigned long long topm = ~0ull;  // columns in the rk largest
+    if (rk < n) {
+      for (int c = lane; c < n; c += 32) {
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s = fmaf(T[i * ld + c], T[i * ld + c], s);
+        cn[c] = s;
+      }
+      __syncwarp();
+      bool in0 = false, in1 = false;
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        bool in = false;
+        if (c < n) {
+          int above = 0;
+          for (int j = 0; j < n; ++j) above += (cn[j] > cn[c] || (cn[j] == cn[c] && j < c)) ? 1 : 0;
+          in = above < rk;
+        }
+        if (h == 0) in0 = in;
+        else in1 = in;
+      }
+      topm = ((unsigned long long)__ballot_sync(0xffffffffu, in1) << 32) | __ballot_sync(0xffffffffu, in0);
+      __syncwarp();
+    }
     for (int r = 0; r < m - 1; ++r) {
       for (int pi = lane; pi < m / 2; pi += 32) {
         int p, q;
@@ -207,7 +235,7 @@ __device__ int warp_onesided_jacobi(float* T, float* V, int n, int ld, float tol
         }
         if (a == 0.f || b == 0.f) continue;
         const float rel = fabsf(g) * rsqrtf(a) * rsqrtf(b);
-        worst = fmaxf(worst, rel);
+        if ((topm >> p) & (topm >> q) & 1ull) worst = fmaxf(worst, rel);
         if (rel <= tol) continue;
         const float zeta = (b - a) / (2.f * g);
         const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -274,7 +302,8 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
       Tm[i * ld + b] = s;
     }
     __syncwarp();
-    const int sw = warp_onesided_jacobi(Tm, Vm, R, ld, tol, 30);
+    const int rk = rank ? min(rank[k], R) : R;  // one slice per warp: uniform in the warp
+    const int sw = warp_onesided_jacobi(Tm, Vm, R, ld, tol, 30, rk, A1);
     if (sw > 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
     // sigma_i = ||T(:, i)||; Upol = sum T(:, i) V(:, i)^T / sigma_i over the
     // rank(F~_k) = r_k largest sigma_i > 0 (the rest are rounding noise of zero
@@ -286,7 +315,6 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
       A1[i] = sqrtf(s);
     }
     __syncwarp();
-    const int rk = rank ? rank[k] : R;
     float* kinv = Up;  // R factors, overwritten below only after use
     for (int i = lane; i < R; i += 32) {
       const float sg = A1[i];

@@ -141,12 +141,26 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
       for (int i = 0; i < R; ++i) v[i] = (i == c) ? 1.f : 0.f;
     }
 
-    // ---- one-sided Jacobi, parallel round-robin ordering
+    // ---- one-sided Jacobi, parallel round-robin ordering.  Convergence is
+    // judged on the r_k largest columns only (r_k = the slice's stage-1 rank
+    // >= rank(T_k)): the other R - r_k columns shrink to rounding noise of a
+    // zero singular value and keep rotating among themselves without ever
+    // passing the orthogonality test; the polar factor leaves them out.
+    // (r_k differs between the problems of a warp: the ranking below runs in
+    // every lane, only its use depends on r_k)
+    const int rk = (act && rank) ? min(rank[k], Ra) : Ra;
     int sweep = 0;
     for (; sweep < 30; ++sweep) {
       float na = 0.f;
 #pragma unroll
       for (int i = 0; i < R; ++i) na = fmaf(t[i], t[i], na);
+      int above = 0;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const float nj = __shfl_sync(FULL, na, (g * R + j) & 31);
+        above += (nj > na || (nj == na && j < c)) ? 1 : 0;
+      }
+      const bool top = rk >= R || above < rk;
       bool rotated = false;
       for (int rr = 0; rr < M - 1; ++rr) {
         int p;
@@ -160,6 +174,8 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
         const int src = pair ? g * R + p : lane;
         const bool lo = c < p;
         const float nb = __shfl_sync(FULL, na, src);
+        const int ptop = __shfl_sync(FULL, top ? 1 : 0, src);  // every lane shuffles
+        const bool both_top = top && ptop != 0;
         const float a = lo ? na : nb, b = lo ? nb : na;
         if constexpr (R <= 12) {
           // partner columns held in registers
@@ -173,7 +189,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
 #pragma unroll
           for (int i = 0; i < R; ++i) gm = fmaf(t[i], tp[i], gm);
           if (pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol) {
-            rotated = true;
+            rotated |= both_top;
             const float zeta = (b - a) / (2.f * gm);
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
@@ -193,7 +209,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
           const bool rot = pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol;
           float cs = 1.f, sg = 0.f, tt = 0.f;
           if (rot) {
-            rotated = true;
+            rotated |= both_top;
             const float zeta = (b - a) / (2.f * gm);
             tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             cs = rsqrtf(fmaf(tt, tt, 1.f));
@@ -231,7 +247,6 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
 #pragma unroll
     for (int i = 0; i < R; ++i) s2 = fmaf(t[i], t[i], s2);
     const float sg = sqrtf(s2);
-    const int rk = (act && rank) ? rank[k] : Ra;
     int above = 0;  // columns of this problem ahead of column c in sigma order
 #pragma unroll
     for (int j = 0; j < R; ++j) {

@@ -296,7 +296,11 @@ struct JacobiRound {
   float c[32], s[32];
 };
 
-__device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sweeps, JacobiRound& rd) {
+// Only planes touching one of the `want` largest diagonal entries (at the
+// start of a sweep) count towards convergence: the others mix directions
+// outside the wanted leading eigenpairs, which for a rank-deficient A are
+// rounding noise of zero eigenvalues that never pass the test (n <= 64).
+__device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sweeps, JacobiRound& rd, int want) {
   const int lane = threadIdx.x & 31;
   const int ld = n + 1;
   const int m = n + (n & 1);  // players (one dummy when n is odd)
@@ -309,8 +313,28 @@ __device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sw
   __syncwarp();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
+    unsigned long long topm = ~0ull;  // indices of the `want` largest diagonal entries
+    if (want < n) {
+      bool in0 = false, in1 = false;
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        bool in = false;
+        if (c < n) {
+          const float dc = A[c * ld + c];
+          int above = 0;
+          for (int j = 0; j < n; ++j) {
+            const float dj = A[j * ld + j];
+            above += (dj > dc || (dj == dc && j < c)) ? 1 : 0;
+          }
+          in = above < want;
+        }
+        if (h == 0) in0 = in;
+        else in1 = in;
+      }
+      topm = ((unsigned long long)__ballot_sync(0xffffffffu, in1) << 32) | __ballot_sync(0xffffffffu, in0);
+    }
     for (int r = 0; r < m - 1; ++r) {
-      bool rot = false;
+      bool rot = false, counts = false;
       if (lane < half) {
         int p, q;
         if (lane == 0) {
@@ -331,6 +355,7 @@ __device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sw
             c = rsqrtf(fmaf(t, t, 1.f));
             s = t * c;
             rot = true;
+            counts = ((topm >> p) | (topm >> q)) & 1ull;
           }
         }
         rd.p[lane] = p;
@@ -339,7 +364,7 @@ __device__ bool warp_jacobi_eig(float* A, float* V, int n, float tol, int max_sw
         rd.s[lane] = rot ? s : 0.f;
       }
       if (!__any_sync(0xffffffffu, rot)) continue;
-      any = true;
+      any |= __any_sync(0xffffffffu, counts);
       __syncwarp();
       // rows: A <- J^T A, every (plane, column) item
       for (int t = lane; t < half * n; t += 32) {
@@ -427,7 +452,7 @@ __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, co
     A[c * ld + a] = v;
   }
   __syncwarp();
-  const bool ok = warp_jacobi_eig(A, V, n, 1e-7f, 40, rd);
+  const bool ok = warp_jacobi_eig(A, V, n, 1e-7f, 40, rd, R < n ? R : n);
   if (!ok && lane == 0) set_status(status, ST_SWEEP_CAP);
   __syncwarp();
   if (lane == 0) {
