@@ -399,12 +399,19 @@ def main_learned(args):
     om = om_g.clone().requires_grad_(True)
     opt = torch.optim.Adam([om], lr=args.lr)
 
+    total = args.warmup + args.steps
+    step_no = [0]
+
     def train_step():
+        # Adam with a cosine learning-rate decay over the whole run
+        for grp in opt.param_groups:
+            grp["lr"] = args.lr * 0.5 * (1.0 + math.cos(math.pi * step_no[0] / total))
+        step_no[0] += 1
         opt.zero_grad(set_to_none=True)
         loss = SketchLoss.apply(om, Xtr, otr, ctx)
         loss.backward()
         opt.step()
-        return loss
+        return loss.detach()
 
     losses = []
     for _ in range(args.warmup):
@@ -470,7 +477,7 @@ def main_learned(args):
            "ms_per_step": step_ms, "higher_is_better": False, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": f"spectrogram-like |PARAFAC2+noise| train K={w['Ktr']} / held-out K={w['Kev']} "
                                   f"I_k~U{{{w['Imin']}..{w['Imax']}}} J={J} R={R} l={ell} (one generator instance)",
-                      "optimizer": f"Adam lr={args.lr}", "x_dtype": args.dtype},
+                      "optimizer": f"Adam lr={args.lr}, cosine decay over {args.warmup + args.steps} steps", "x_dtype": args.dtype},
            "train": {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "loss_first": losses[0], "loss_last": losses[-1],
                      "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
                      "algorithmic_bytes_per_step": 4 * xbytes, "steps_total": len(losses)},

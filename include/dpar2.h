@@ -213,7 +213,10 @@ DPAR2_API dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpa
 /* Copy `rows` rows of J elements of `dtype` from host memory (rows packed,
  * row stride J; pinned memory gives asynchronous, full-bandwidth copies) into
  * the device layout dpar2_compress reads (row stride ldx elements, X_dev
- * 16-byte aligned).  Columns J..ldx-1 of X_dev are set to zero.  One 2-D copy. */
+ * 16-byte aligned).  Columns J..ldx-1 of X_dev are set to zero.  ldx == J: one
+ * copy; otherwise contiguous chunks through four device staging buffers (4 x ~128 MB
+ * of context scratch) on two copy streams, each re-pitched on the device while the
+ * next ones copy. */
 DPAR2_API dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* X_host, int64_t rows, int J, dpar2_dtype dtype,
                                          void* X_dev, int64_t ldx, void* stream);
 

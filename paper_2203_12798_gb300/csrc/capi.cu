@@ -77,7 +77,9 @@ void ctx_release(dpar2_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& kv : ctx->ws) {
     if (!kv.second.p || kv.first == "__work_stream") continue;
-    if (kv.first == "__event") cudaEventDestroy(reinterpret_cast<cudaEvent_t>(kv.second.p));
+    if (kv.first == "__event" || kv.first.rfind("__copy_ev", 0) == 0)
+      cudaEventDestroy(reinterpret_cast<cudaEvent_t>(kv.second.p));
+    else if (kv.first.rfind("__copy_stream", 0) == 0) cudaStreamDestroy(reinterpret_cast<cudaStream_t>(kv.second.p));
     else cudaFree(kv.second.p);
     kv.second.p = nullptr;
   }
@@ -394,8 +396,55 @@ dpar2_status dpar2_upload_rows(dpar2_ctx* ctx, const void* Xh, int64_t rows, int
   const size_t es = dtype_size(dtype);
   return guarded(ctx, stream, [&](cudaStream_t s) {
     if (rows == 0) return;
-    if (ldx > J) CK(cudaMemset2DAsync(static_cast<char*>(Xd) + J * es, ldx * es, 0, (ldx - J) * es, rows, s));
-    CK(cudaMemcpy2DAsync(Xd, ldx * es, Xh, J * es, J * es, rows, cudaMemcpyHostToDevice, s));
+    const size_t rowb = (size_t)J * es;
+    if (ldx == J) {
+      CK(cudaMemcpyAsync(Xd, Xh, (size_t)rows * rowb, cudaMemcpyHostToDevice, s));
+      return;
+    }
+    // Packed rows -> pitched rows: contiguous copies of ~128 MB chunks into four
+    // device staging buffers, alternating between two copy streams (two copy
+    // engines in flight), each chunk re-pitched on the work stream by a kernel
+    // (a 2-D copy of short rows moves far below the link's bandwidth).  Chunk
+    // c + 4 waits for the kernel that read buffer c % 4.
+    constexpr int NB = 4, NCS = 2;
+    const int64_t crow = std::max<int64_t>(1, (int64_t)((128u << 20) / rowb));
+    uint8_t* stage = wsget<uint8_t>(ctx, "up_stage", NB * (size_t)crow * rowb);
+    cudaStream_t cs[NCS];
+    for (int i = 0; i < NCS; ++i) {
+      auto& e = ctx->ws[std::string("__copy_stream") + char('0' + i)];
+      if (!e.p) {
+        cudaStream_t x;
+        CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        e.p = reinterpret_cast<void*>(x);
+      }
+      cs[i] = reinterpret_cast<cudaStream_t>(e.p);
+    }
+    cudaEvent_t ev[2 * NB + 1];  // copied[b], used[b], start
+    for (int i = 0; i < 2 * NB + 1; ++i) {
+      auto& e = ctx->ws[std::string("__copy_ev") + char('a' + i)];
+      if (!e.p) {
+        cudaEvent_t x;
+        CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        e.p = reinterpret_cast<void*>(x);
+      }
+      ev[i] = reinterpret_cast<cudaEvent_t>(e.p);
+    }
+    CK(cudaEventRecord(ev[2 * NB], s));  // the copies start after the work stream's prior work
+    for (int i = 0; i < NCS; ++i) CK(cudaStreamWaitEvent(cs[i], ev[2 * NB], 0));
+    int64_t c = 0;
+    for (int64_t r0 = 0; r0 < rows; r0 += crow, ++c) {
+      const int b = (int)(c % NB);
+      cudaStream_t q = cs[c % NCS];
+      const int64_t nr = std::min<int64_t>(crow, rows - r0);
+      if (c >= NB) CK(cudaStreamWaitEvent(q, ev[NB + b], 0));  // kernel done with buffer b
+      CK(cudaMemcpyAsync(stage + (size_t)b * crow * rowb, static_cast<const uint8_t*>(Xh) + (size_t)r0 * rowb,
+                         (size_t)nr * rowb, cudaMemcpyHostToDevice, q));
+      CK(cudaEventRecord(ev[b], q));
+      CK(cudaStreamWaitEvent(s, ev[b], 0));
+      launch_repitch(stage + (size_t)b * crow * rowb, nr, J, (int)es, static_cast<uint8_t*>(Xd) + (size_t)r0 * ldx * es,
+                     ldx, s);
+      CK(cudaEventRecord(ev[NB + b], s));
+    }
   });
 }
 

@@ -74,6 +74,8 @@ void launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t n, float* out, i
 void launch_philox_words(uint64_t seed, uint32_t stream_id, int64_t n, uint32_t* out, cudaStream_t s);
 void launch_pad_omega(const float* om, int J, int ell, int Jpad, int LP, dpar2_dtype dt, float* out,
                       cudaStream_t s);
+// packed rows (J elements of es bytes) -> rows of pitch ldx elements, pad columns zeroed
+void launch_repitch(const void* src, int64_t rows, int J, int es, void* dst, int64_t ldx, cudaStream_t s);
 
 // ---- stage 1, CUDA-core path ----
 void launch_sketch_generic(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int J, const float* om_pad,

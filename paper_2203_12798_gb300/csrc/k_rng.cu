@@ -7,6 +7,8 @@
 // (n/4 lo, n/4 hi, stream_id, 0) and key (seed lo, seed hi).  Gaussians come
 // from Box-Muller on the word pairs (0,1) and (2,3) with uniforms
 // u = (word + 0.5) / 2^32.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -78,6 +80,25 @@ __global__ void k_pad_omega(const float* __restrict__ om, int J, int ell, int Jp
   }
 }
 
+// Packed rows (J elements of es bytes each) -> rows of ldx elements, the
+// columns J .. ldx - 1 zeroed; one warp per row, 2- or 4-byte elements.
+__global__ void k_repitch(const uint8_t* __restrict__ src, int64_t rows, int J, int es, uint8_t* __restrict__ dst,
+                          int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    if (es == 2) {
+      const uint16_t* sr = reinterpret_cast<const uint16_t*>(src) + r * J;
+      uint16_t* dr = reinterpret_cast<uint16_t*>(dst) + r * ldx;
+      for (int64_t j = lane; j < ldx; j += 32) dr[j] = j < J ? sr[j] : (uint16_t)0;
+    } else {
+      const uint32_t* sr = reinterpret_cast<const uint32_t*>(src) + r * J;
+      uint32_t* dr = reinterpret_cast<uint32_t*>(dst) + r * ldx;
+      for (int64_t j = lane; j < ldx; j += 32) dr[j] = j < J ? sr[j] : 0u;
+    }
+  }
+}
+
 static int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 65535 * 4 ? 65535 * 4 : g));
@@ -89,6 +110,12 @@ void launch_gaussian(uint64_t seed, uint32_t sid, int64_t n, float* out, int r16
 void launch_philox_words(uint64_t seed, uint32_t sid, int64_t n, uint32_t* out, cudaStream_t s) {
   k_philox_words<<<grid_for((n + 3) / 4, 256), 256, 0, s>>>(seed, sid, n, out);
 }
+void launch_repitch(const void* src, int64_t rows, int J, int es, void* dst, int64_t ldx, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((rows + 7) / 8, 65535);
+  k_repitch<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(static_cast<const uint8_t*>(src), rows, J, es,
+                                                                   static_cast<uint8_t*>(dst), ldx);
+}
+
 void launch_pad_omega(const float* om, int J, int ell, int Jpad, int LP, dpar2_dtype dt, float* out,
                       cudaStream_t s) {
   k_pad_omega<<<grid_for((int64_t)Jpad * LP, 256), 256, 0, s>>>(om, J, ell, Jpad, LP, (int)dt, out);

@@ -345,3 +345,20 @@ def test_invalid_arguments_rejected(api, ctx):
     with pytest.raises(api.Dpar2Error) as e:
         ctx.compress(Xu, d["offsets"], R=4, p=4, J=33)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("rows,J,dtype", [(1000, 77, torch.bfloat16), (37, 64, torch.float32),
+                                          (140_000, 2049, torch.bfloat16)])
+def test_upload_rows_repitches_exactly(api, ctx, rows, J, dtype):
+    # packed host rows -> pitched device rows (pad columns zero); the last case
+    # spans several staging chunks (~256 MB each)
+    g = torch.Generator().manual_seed(rows)
+    Xh = torch.randn(rows, J, generator=g).to(dtype).pin_memory()
+    es = Xh.element_size()
+    ld = (J + 16 // es - 1) // (16 // es) * (16 // es)
+    Xd = torch.full((rows, ld), 7.0, dtype=dtype, device="cuda")
+    ctx.upload(Xh, Xd)
+    torch.cuda.synchronize()
+    assert torch.equal(Xd[:, :J].cpu(), Xh)
+    if ld > J:
+        assert bool((Xd[:, J:] == 0).all())
