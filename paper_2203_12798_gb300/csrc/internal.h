@@ -154,6 +154,8 @@ void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, doub
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s);
 // register-resident variant (one-sided Jacobi on the Cholesky factor); false for LP > 32
+bool launch_eig_wide(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
+                     int* status, cudaStream_t s);
 bool launch_eig_reg(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s);
 void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
@@ -212,6 +214,8 @@ int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
 // register-resident Q-step (lane = column); false when R has no instantiation (R > 32)
 bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
+bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
+int qstep_wide_blocks(int K, int R, int cap);
 // blocks of the Q-step launch for K slices at rank R (one wave of resident blocks when it fits)
 int qstep_blocks(int K, int R, int nblk);
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);

@@ -372,12 +372,13 @@ int qstep_blocks(int K, int R, int nblk) {
   if (R <= 16) return qblocks<16>(K);
   if (R <= 24) return qblocks<24>(K);
   if (R <= 32) return qblocks<32>(K);
+  if (R <= 64) return qstep_wide_blocks(K, R, nblk);
   return nblk;  // shared-memory Q-step on the Lemma 2 / 3 grid
 }
 
 // Launches the register-resident Q-step when the rank has an instantiation
-// (exact for R in {10, 20, 30}, zero-padded to 8, 16, 24 or 32 otherwise);
-// returns false for R > 32.
+// (exact for R in {10, 20, 30}, zero-padded to 8, 16, 24 or 32 otherwise;
+// the warp-pair kernel for 32 < R <= 64); returns false for R > 64.
 bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
   switch (b.R) {
     case 10: qreg<10>(b, part, pstride, want_g1, s); return true;
@@ -389,7 +390,7 @@ bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, c
   else if (b.R <= 16) qreg<16>(b, part, pstride, want_g1, s);
   else if (b.R <= 24) qreg<24>(b, part, pstride, want_g1, s);
   else if (b.R <= 32) qreg<32>(b, part, pstride, want_g1, s);
-  else return false;
+  else return launch_qstep_wide(b, part, pstride, want_g1, s);
   return true;
 }
 

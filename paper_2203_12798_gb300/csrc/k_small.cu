@@ -896,6 +896,7 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
     attr = true;
   }
   if (launch_eig_reg(G, M2, K, ell, LP, R, T, lam, status, s)) return;
+  if (launch_eig_wide(G, M2, K, ell, LP, R, T, lam, status, s)) return;
   k_eig_top<<<K, 32, smem, s>>>(G, M2, ell, LP, R, T, lam, status);
 }
 
