@@ -15,6 +15,13 @@
 // exchange columns with shuffles and compute the same rotation from the same
 // operands.  Column norms are carried along with the rotations (Hestenes'
 // update a' = a - t g, b' = b + t g) and recomputed at every sweep start.
+//
+// Convergence: pairs with |g| / sqrt(a b) <= tol are not rotated.  Rotating a
+// pair perturbs the inner products of its columns with the others by the
+// rotation angle times those inner products, so a sweep whose largest ratio
+// is r leaves ratios of about sqrt(N) r^2; once r <= rstop = sqrt(tol /
+// sqrt(N)) that is at the tolerance and the iteration ends without the sweep
+// that would only confirm it.
 #include "common.cuh"
 #include "internal.h"
 
@@ -83,12 +90,16 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) k_eig_reg(int K, const double*
 #pragma unroll
   for (int i = 0; i < N; ++i) t[i] = (act && i >= lane) ? A[lane * N + i] : 0.f;
   const float tol = 1.2e-7f * (float)N;
+  // a sweep whose largest ratio |g| / sqrt(a b) is r leaves ratios of about
+  // sqrt(N) r^2 behind: below rstop that is below tol, and the sweep that
+  // would only confirm it is skipped
+  const float rstop = sqrtf(tol * rsqrtf((float)N));
   int sweep = 0;
   for (; sweep < 40; ++sweep) {
     float na = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) na = fmaf(t[i], t[i], na);
-    bool rotated = false;
+    float rmax = 0.f;
     for (int rr = 0; rr < N - 1; ++rr) {
       int p;
       if (lane == 0) {
@@ -108,8 +119,9 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) k_eig_reg(int K, const double*
 #pragma unroll
       for (int i = 0; i < N; ++i) gm = fmaf(t[i], tp[i], gm);
       const float a = lo ? na : nb, b = lo ? nb : na;
-      if (act && a > 0.f && b > 0.f && fabsf(gm) > tol * sqrtf(a) * sqrtf(b)) {
-        rotated = true;
+      const float rel = (act && a > 0.f && b > 0.f) ? fabsf(gm) / (sqrtf(a) * sqrtf(b)) : 0.f;
+      rmax = fmaxf(rmax, rel);
+      if (rel > tol) {
         const float zeta = (b - a) / (2.f * gm);
         const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
@@ -119,7 +131,7 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) k_eig_reg(int K, const double*
         na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
       }
     }
-    if (!__any_sync(FULL, rotated)) break;
+    if (warp_max(rmax) <= rstop) break;
   }
   if (sweep == 40 && lane == 0) set_status(status, ST_SWEEP_CAP);
 

@@ -16,9 +16,9 @@
 // once and every column is back where it started.  A move is two shuffles
 // per row (the top row shifts up a lane, the bottom row down a lane).
 //
-// Convergence: a sweep with no rotation that touches one of the `want` =
-// min(R, l) largest columns (ranked by norm at the sweep start) ends the
-// iteration; only those eigenvectors are used.
+// Convergence: judged on the pairs that touch one of the `want` = min(R, l)
+// largest columns (ranked by norm at the sweep start; only those
+// eigenvectors are used), by the rule of k_eig_reg.
 #include "common.cuh"
 #include "internal.h"
 
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(32 * EIGW_WARPS) k_eig_wide(int K, const doubl
   }
   const int want = R < ell ? R : ell;
   const float tol = 1.2e-7f * (float)N;
+  const float rstop = sqrtf(tol * rsqrtf((float)N));  // as in k_eig_reg
   int sweep = 0;
   for (; sweep < 40; ++sweep) {
     float na = 0.f, nb = 0.f;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(32 * EIGW_WARPS) k_eig_wide(int K, const doubl
       ab += (xb > nb || (xb == nb && j < lane)) ? 1 : 0;
     }
     int ft = (act && at < want) ? 1 : 0, fb = (act && ab < want) ? 1 : 0;
-    bool counted = false;
+    float rmax = 0.f;  // largest ratio over pairs touching a wanted column
     for (int rr = 0; rr < N - 1; ++rr) {
       float g0 = 0.f, g1 = 0.f;
 #pragma unroll
@@ -148,8 +149,9 @@ __global__ void __launch_bounds__(32 * EIGW_WARPS) k_eig_wide(int K, const doubl
         g1 = fmaf(top[i + 1], bot[i + 1], g1);
       }
       const float gm = g0 + g1;
-      if (act && na > 0.f && nb > 0.f && fabsf(gm) > tol * sqrtf(na) * sqrtf(nb)) {
-        counted |= (ft | fb) != 0;
+      const float rel = (act && na > 0.f && nb > 0.f) ? fabsf(gm) / (sqrtf(na) * sqrtf(nb)) : 0.f;
+      if (ft | fb) rmax = fmaxf(rmax, rel);
+      if (rel > tol) {
         const float zeta = (nb - na) / (2.f * gm);
         const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(32 * EIGW_WARPS) k_eig_wide(int K, const doubl
       ring_move<N>(na, nb, lane);
       ring_move<N>(ft, fb, lane);
     }
-    if (!__any_sync(FULL, counted)) break;
+    if (warp_max(rmax) <= rstop) break;
   }
   if (sweep == 40 && lane == 0) set_status(status, ST_SWEEP_CAP);
 

@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
   }
   __syncthreads();
   const float tol = fmaxf(1e-6f, (float)Ra * 1.2e-7f);
+  // a sweep whose largest kept-pair ratio |g| / sqrt(a b) is r leaves ratios
+  // of about sqrt(R) r^2 behind: below rstop that is below tol, and the
+  // sweep that would only confirm it is skipped
+  const float rstop = sqrtf(tol * rsqrtf((float)Ra));
   const int RaRa = Ra * Ra;
   float acc[R];
 #pragma unroll
@@ -141,8 +145,8 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
       for (int i = 0; i < R; ++i) v[i] = (i == c) ? 1.f : 0.f;
     }
 
-    // ---- one-sided Jacobi, parallel round-robin ordering.  Convergence is
-    // judged on the r_k largest columns only (r_k = the slice's stage-1 rank
+    // ---- one-sided Jacobi, parallel round-robin ordering.  Convergence (the
+    // rstop rule of k_eig_reg) is judged on the r_k largest columns only (r_k = the slice's stage-1 rank
     // >= rank(T_k)): the other R - r_k columns shrink to rounding noise of a
     // zero singular value and keep rotating among themselves without ever
     // passing the orthogonality test; the polar factor leaves them out.
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
         above += (nj > na || (nj == na && j < c)) ? 1 : 0;
       }
       const bool top = rk >= R || above < rk;
-      bool rotated = false;
+      float rmax = 0.f;  // largest ratio over pairs of kept columns
       for (int rr = 0; rr < M - 1; ++rr) {
         int p;
         if (c == 0) {
@@ -188,8 +192,9 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
           float gm = 0.f;
 #pragma unroll
           for (int i = 0; i < R; ++i) gm = fmaf(t[i], tp[i], gm);
-          if (pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol) {
-            rotated |= both_top;
+          const float rel = (pair && a > 0.f && b > 0.f) ? fabsf(gm) * rsqrtf(a) * rsqrtf(b) : 0.f;
+          if (both_top) rmax = fmaxf(rmax, rel);
+          if (rel > tol) {
             const float zeta = (b - a) / (2.f * gm);
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
@@ -206,10 +211,11 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
           float gm = 0.f;
 #pragma unroll
           for (int i = 0; i < R; ++i) gm = fmaf(t[i], __shfl_sync(FULL, t[i], src), gm);
-          const bool rot = pair && a > 0.f && b > 0.f && fabsf(gm) * rsqrtf(a) * rsqrtf(b) > tol;
+          const float rel = (pair && a > 0.f && b > 0.f) ? fabsf(gm) * rsqrtf(a) * rsqrtf(b) : 0.f;
+          if (both_top) rmax = fmaxf(rmax, rel);
+          const bool rot = rel > tol;
           float cs = 1.f, sg = 0.f, tt = 0.f;
           if (rot) {
-            rotated |= both_top;
             const float zeta = (b - a) / (2.f * gm);
             tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             cs = rsqrtf(fmaf(tt, tt, 1.f));
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
           }
         }
       }
-      if (!__any_sync(FULL, rotated)) break;
+      if (warp_max(rmax) <= rstop) break;
     }
     if (sweep == 30 && lane == 0) set_status(status, ST_SWEEP_CAP);
     if (Prot && act && c < Ra) {

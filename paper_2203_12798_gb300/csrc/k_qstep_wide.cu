@@ -19,8 +19,9 @@
 //
 // Warm start as in k_qstep_reg: V0 = Prot_k (the previous Q-step's right
 // rotations) after one Newton-Schulz step V0 <- V0 (3 I - V0^T V0) / 2; the
-// sweeps start from T_k V0.  Convergence is judged on the r_k largest columns
-// (r_k = the slice's stage-1 rank), and the polar factor keeps those columns.
+// sweeps start from T_k V0.  Convergence (the rstop rule of k_eig_reg) is
+// judged on the r_k largest columns (r_k = the slice's stage-1 rank), and the
+// polar factor keeps those columns.
 // Ranks without an instantiation run zero-padded (zero columns of T never
 // rotate).
 #include "common.cuh"
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
   for (int e = pt; e < RR; e += 64) slot[e] = 0.f;
   __syncthreads();
   const float tol = fmaxf(1e-6f, (float)Ra * 1.2e-7f);
+  const float rstop = sqrtf(tol * rsqrtf((float)Ra));  // as in k_qstep_reg
   const int RaRa = Ra * Ra;
   const bool act = lane < HP;
   const int j0 = lane, j1 = HP + lane;  // the columns this lane starts with
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
           ab += (xb > nb || (xb == nb && j < lane)) ? 1 : 0;
         }
         int ft = (act && at < rk) ? 1 : 0, fb = (act && ab < rk) ? 1 : 0;
-        bool rotated = false;
+        float rmax = 0.f;  // largest ratio over pairs of kept columns
         float2* rb = rot + (size_t)(sweep & 1) * (R - 1) * HP;
         for (int rr = 0; rr < R - 1; ++rr) {
           float g0 = 0.f, g1 = 0.f;
@@ -198,8 +200,9 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
           }
           const float gm = g0 + g1;
           float cs = 1.f, sn = 0.f;
-          if (act && na > 0.f && nb > 0.f && fabsf(gm) * rsqrtf(na) * rsqrtf(nb) > tol) {
-            rotated |= (ft & fb) != 0;
+          const float rel = (act && na > 0.f && nb > 0.f) ? fabsf(gm) * rsqrtf(na) * rsqrtf(nb) : 0.f;
+          if (ft & fb) rmax = fmaxf(rmax, rel);
+          if (rel > tol) {
             const float zeta = (nb - na) / (2.f * gm);
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             cs = rsqrtf(fmaf(tt, tt, 1.f));
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
           ring_step<HP>(na, nb, lane);
           ring_step<HP>(ft, fb, lane);
         }
-        const bool conv = !__any_sync(FULL, rotated);
+        const bool conv = warp_max(rmax) <= rstop;
         const bool stop = conv || sweep + 1 >= QW_SWEEPS;
         if (lane == 0) {
           ctrl[sweep & 1] = stop ? 1 : 0;
