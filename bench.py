@@ -36,8 +36,8 @@ METRIC = "DPar2 time-to-fit (s) & stage-1 HBM GB/s vs peak; chosen vs plain at Î
 # stage-1 kernels on this workload, from one ncu capture (profiles/), valid
 # only for the kernel source they were taken on (sha1 of k_tc.cu).
 MEASURED_TRAFFIC = {
-    "project": {"bytes": 16.83e9, "k_tc_sha1": "36da4d79be3a28e05103c3f2efc1d71b8695d531"},
-    "sketch": {"bytes": 13.70e9, "k_tc_sha1": "36da4d79be3a28e05103c3f2efc1d71b8695d531"},
+    "project": {"bytes": 15.96e9, "k_tc_sha1": "c04bab0b0ecd9ae6748f84cf9e7f6d106ce8d1b5"},
+    "sketch": {"bytes": 13.75e9, "k_tc_sha1": "c04bab0b0ecd9ae6748f84cf9e7f6d106ce8d1b5"},
 }
 WORKLOADS = {
     # FMA-shaped spectrogram magnitudes (the default, headline workload)
@@ -220,7 +220,8 @@ def main_ours(args):
     w = WORKLOAD
     tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}[args.dtype]
     es = torch.empty((), dtype=tdt).element_size()
-    ld = (w["J"] + 16 // es - 1) // (16 // es) * (16 // es)
+    # rows padded to 32 bytes: the projection's column blocks then start on DRAM sector boundaries
+    ld = (w["J"] + 32 // es - 1) // (32 // es) * (32 // es)
     d = generate(w, args.K, device="cuda", out_dtype=tdt, ld=ld)
     X, off = d["X"], d["offsets"]
     N = int(off[-1])
@@ -387,7 +388,7 @@ def main_learned(args):
     tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}[args.dtype]
     es = torch.empty((), dtype=tdt).element_size()
     J, R, ell = w["J"], w["R"], w["R"] + w["p"]
-    ld = (J + 16 // es - 1) // (16 // es) * (16 // es)
+    ld = (J + 32 // es - 1) // (32 // es) * (32 // es)
     d = synth.spectrogram_like(K=w["Ktr"] + w["Kev"], Imin=w["Imin"], Imax=w["Imax"], J=J, R=R, seed=w["seed"],
                                device="cuda", out_dtype=tdt, ld=ld)
     off = d["offsets"]

@@ -143,7 +143,9 @@ DPAR2_API dpar2_status dpar2_philox_words(dpar2_ctx* ctx, uint64_t seed, uint32_
  *   X            device, sum(I_k) rows of ldx elements of `dtype`; X_k is rows
  *                offsets[k] .. offsets[k+1]-1, columns 0..J-1.  ldx >= J and
  *                ldx * sizeof(dtype) must be a multiple of 16 bytes, X 16-byte
- *                aligned.  Read only; must stay valid until the call returns.
+ *                aligned (a multiple of 32 bytes is faster: every 512-column
+ *                block of a row then starts on a DRAM sector boundary).  Read
+ *                only; must stay valid until the call returns.
  *   opt          R, p, q, seed, schedule, flags are used.  Requires R <= J,
  *                R + p <= min(J, 64).
  *   omega        device J x (R+p) float32 test matrix of stage 1, or NULL for

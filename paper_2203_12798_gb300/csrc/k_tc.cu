@@ -661,11 +661,13 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         mbar_arrive_expect_tx(&full[s], S::A + S::B);
         uint8_t* a = sA + s * S::A;
         // the last chunk ends at the slice's last row (it overlaps the chunk
-        // before it, whose rows its Q rows zero) instead of reading past it
+        // before it, whose rows its Q rows zero) instead of reading past it;
+        // the chunk before it is kept in L2 for that second read
         const int row = (int)(c + 1 < nch ? r0 + (int64_t)c * PJ_BK : r1 - PJ_BK);
+        const uint64_t pol = (c + 2 == nch && (r1 - r0) % PJ_BK != 0) ? pol_q : pol_x;
 #pragma unroll
         for (int bx = 0; bx < 2 * S::HV; ++bx)
-          tma_load_2d_hint(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, row, pol_x);
+          tma_load_2d_hint(a + bx * 8192, &tmX, &full[s], jb * S::COLS + 64 * bx, row, pol);
         tma_load_3d_hint(sB + s * S::B, &tmQ, &full[s], 0, 0, (int)(p0 / PJ_BK + c), pol_q);
         inflight = true;
         if (++s == ST) {
