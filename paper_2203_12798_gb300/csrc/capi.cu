@@ -837,12 +837,14 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.Pi = wsget<float>(ctx, "Pi", (size_t)K * RR);
     b.Prot = (opt->flags & DPAR2_FLAG_COLD_QSTEP) ? nullptr : wsget<float>(ctx, "Prot", (size_t)K * RR);
     b.rank = static_cast<const int*>(comp->rank1.p);
-    double* d6 = wsget<double>(ctx, "als_d", (size_t)6 * RR);
+    double* d6 = wsget<double>(ctx, "als_d", (size_t)7 * RR);
     b.Psi = d6;
     b.VtV = d6 + RR;
     b.HtH = d6 + 2 * RR;
     b.WtW = d6 + 3 * RR;
     b.Ginv = d6 + 4 * RR;
+    b.InvH = d6 + 5 * RR;
+    b.InvV = d6 + 6 * RR;
     b.nblk = als_blocks(K, R, ctx->num_sms);
     b.nq = qstep_blocks(K, R, b.nblk);
     b.pr = std::max(b.nblk, b.nq);

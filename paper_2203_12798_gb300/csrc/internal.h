@@ -181,6 +181,21 @@ constexpr int kAtbBlocks = 64;
 void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, float* part, cudaStream_t s);
 
 // ---- ALS (Alg. 3 repeat loop) ----
+// Work of pre_solve (small_solve.cuh): Inv = (A o B)^+ with A = W^T W, reduced
+// first from the W-update partials part3 when part3 is non-null and it > 0.
+struct PreSolve {
+  int R = 0;
+  const float* part3 = nullptr;
+  int nparts = 0, pstride = 0, it = 0;
+  double* WtW = nullptr;
+  const double* B = nullptr;
+  double* loss = nullptr;
+  double* Inv = nullptr;
+  double* L = nullptr;  // R x R work arrays of the pseudoinverse fallback
+  double* V = nullptr;
+  int* status = nullptr;
+};
+
 struct AlsBufs {
   int K, J, R;
   const float* D;     // J x R
@@ -198,6 +213,8 @@ struct AlsBufs {
   double* HtH;        // R x R
   double* WtW;        // R x R
   double* Ginv;       // R x R  (V^T V * H^T H)^+
+  double* InvH = nullptr;  // R x R  (W^T W * V^T V)^+ from the Q-step's extra block, or null
+  double* InvV = nullptr;  // R x R  (W^T W * H^T H)^+ from the Lemma 2 grid's extra block, or null
   float* part;        // 3 regions x pr x (2 R^2 + 2) block partials
   double* loss;       // max_iter history (device)
   double* small;      // scratch, 8 R^2 + 8 doubles
@@ -213,8 +230,10 @@ void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);
 int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
 // register-resident Q-step (lane = column); false when R has no instantiation (R > 32)
-bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
-bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s);
+bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s,
+                      const PreSolve* pre = nullptr);
+bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s,
+                       const PreSolve* pre = nullptr);
 int qstep_wide_blocks(int K, int R, int cap);
 // blocks of the Q-step launch for K slices at rank R (one wave of resident blocks when it fits)
 int qstep_blocks(int K, int R, int nblk);

@@ -18,27 +18,24 @@
 // FP64 Jacobi eigendecomposition if a pivot fails).
 #include "common.cuh"
 #include "internal.h"
+#include "small_solve.cuh"
 
 namespace dp2 {
 
 constexpr int ALS_WARPS = 16;
 
-__device__ inline void neumaier(float& s, float& c, float v) {
-  const float t = s + v;
-  c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
-  s = t;
-}
-
 // out[e] = sum_b part[b * pstride + e] for e < n.  The whole block cooperates:
 // every entry's partials are split over tpe threads (8 loads in flight per
 // thread, compensated fp32 sums), then combined in a fixed order in FP64.
+// Thread t takes entry e0 + t mod per and every tpe-th partial from t / per
+// on, so that a warp reads consecutive entries of one partial (coalesced).
 __device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int pstride, int n, double* out) {
   __shared__ double red[1024];
   const int T = blockDim.x, t = threadIdx.x;
   const int tpe = max(1, T / n), per = T / tpe;
   for (int e0 = 0; e0 < n; e0 += per) {
-    const int e = e0 + t / tpe, sub = t % tpe;
-    const bool act = t < per * tpe && e < n;
+    const int e = e0 + t % per, sub = t / per;
+    const bool act = sub < tpe && e < n;
     float s = 0.f, c = 0.f;
     if (act) {
       int b = sub;
@@ -55,69 +52,13 @@ __device__ void block_reduce_parts(const float* __restrict__ part, int nblk, int
     __syncthreads();
     if (act && sub == 0) {
       double a = 0.0;
-      for (int q = 0; q < tpe; ++q) a += red[t + q];
+      for (int q = 0; q < tpe; ++q) a += red[q * per + t];
       out[e] = a;
     }
     __syncthreads();
   }
 }
 
-// Two-phase reduction out[e] = sum_b part[b * pstride + e] (e < n) by the
-// threads [t0, t0 + T) of the block: for n <= T every entry's partials are
-// split over tpe = T / n threads, each of which keeps 16 loads in flight and
-// sums them with compensation in FP32 (phase 1, into red); after a barrier the
-// tpe sub-sums of an entry are added in a fixed order in FP64 (phase 2).  For
-// n > T each thread sums whole entries in phase 1 (large R).
-constexpr int kRedMax = 1024;
-__device__ inline void par_reduce_load(const float* __restrict__ part, int nparts, int pstride, int n, int t0, int T,
-                                       double* red, double* out) {
-  const int t = threadIdx.x - t0;
-  if (t < 0 || t >= T) return;
-  if (n > T) {
-    // more entries than threads: thread t sums entries t, t + T, ... over all
-    // partials itself (same order for every entry) and writes them to out
-    for (int e = t; e < n; e += T) {
-      float s = 0.f, c = 0.f;
-      for (int b = 0; b < nparts; ++b) neumaier(s, c, part[(int64_t)b * pstride + e]);
-      out[e] = (double)s + (double)c;
-    }
-    return;
-  }
-  const int tpe = max(1, T / n);
-  const int e = t / tpe, sub = t - e * tpe;
-  double v = 0.0;
-  if (e < n) {
-    float s = 0.f, c = 0.f;
-    int b = sub;
-    for (; b + 15 * tpe < nparts; b += 16 * tpe) {
-      float x[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = part[(int64_t)(b + u * tpe) * pstride + e];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) neumaier(s, c, x[u]);
-    }
-    for (; b < nparts; b += tpe) neumaier(s, c, part[(int64_t)b * pstride + e]);
-    v = (double)s + (double)c;
-  }
-  red[t] = v;
-}
-// Second phase (after a barrier): entry t = sum of its threads' partial sums.
-// Nothing to do when n > T (the first phase wrote out directly).
-__device__ inline void par_reduce_combine(int n, int t0, int T, const double* red, double* out) {
-  const int t = threadIdx.x - t0;
-  if (t < 0 || t >= T || n > T) return;
-  const int tpe = max(1, T / n);
-  if (t >= n) return;  // thread t combines entry t
-  const double* r = red + t * tpe;
-  double a = 0.0, b = 0.0;
-  int q = 0;
-  for (; q + 1 < tpe; q += 2) {
-    a += r[q];
-    b += r[q + 1];
-  }
-  if (q < tpe) a += r[q];
-  out[t] = a + b;
-}
 
 // out (n x n, FP64) = A^T B for A, B (rows x n, fp32, row-major): every block
 // stages tiles of ATB_ROWS rows of its row chunk in shared memory and
@@ -365,9 +306,15 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
 
 // --------------------------------------------------------- Lemma 2 partial --
 // part[blk] (R x R): g(m, r) += W(k, r) sum_i Pi_k(i, m) H(i, r).
+// With pre_on the grid's last block runs pre_solve (the V update's factor).
 __global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __restrict__ W,
-                     const float* __restrict__ H, float* __restrict__ part, int pstride) {
+                     const float* __restrict__ H, float* __restrict__ part, int pstride, PreSolve pre, int pre_on) {
   extern __shared__ __align__(16) float sm[];
+  if (pre_on && blockIdx.x == gridDim.x - 1) {
+    pre_solve(pre, reinterpret_cast<double*>(sm));
+    return;
+  }
+  const int nb = gridDim.x - pre_on;
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* hs = sm;
@@ -377,7 +324,7 @@ __global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __
   for (int e = threadIdx.x; e < nw * RR; e += blockDim.x) slots[e] = 0.f;
   __syncthreads();
   float* slot = slots + warp * RR;
-  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
+  for (int k = blockIdx.x * nw + warp; k < K; k += nb * nw) {
     for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
     __syncwarp();
     const float* wk = W + (int64_t)k * R;
@@ -486,140 +433,12 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
   }
 }
 
-// -------------------------------------------------------- FP64 small solves --
-// Symmetric FP64 Jacobi eigendecomposition (cyclic, one thread) for the
-// pseudoinverse fallback: A <- diag, V eigenvectors.
-__device__ void jacobi_eig_f64(double* A, double* V, int n) {
-  for (int i = 0; i < n * n; ++i) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        tot += A[i * n + j] * A[i * n + j];
-        if (i != j) off += A[i * n + j] * A[i * n + j];
-      }
-    if (off <= 1e-30 * tot) return;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p * n + q];
-        if (apq == 0.0) continue;
-        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A[k * n + p], akq = A[k * n + q];
-          A[k * n + p] = c * akp - s * akq;
-          A[k * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A[p * n + k], aqk = A[q * n + k];
-          A[p * n + k] = c * apk - s * aqk;
-          A[q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[k * n + p], vkq = V[k * n + q];
-          V[k * n + p] = c * vkp - s * vkq;
-          V[k * n + q] = s * vkp + c * vkq;
-        }
-      }
-  }
-}
-
-// Inv <- A^+ for symmetric PSD A (n x n, FP64), computed by the whole block:
-// Cholesky A = R^T R by warp 0 and Inv = R^-1 R^-T, or the eigen
-// pseudoinverse (MATLAB tolerance n eps ||A||) when a pivot is not above
-// 1e-300.  sh: shared workspace of spd_pinv_smem(n) bytes; L, V: n x n work
-// arrays of the fallback.
-__host__ __device__ inline size_t spd_pinv_smem(int n) {
-  return (size_t)(2 * n * n + n) * sizeof(double) + (size_t)(n * (n + 1) / 2) * sizeof(unsigned short);
-}
-// the same in doubles, rounded up
-__host__ __device__ inline size_t spd_pinv_words(int n) { return (spd_pinv_smem(n) + 7) / 8; }
 // shared memory of the H / V updates: the pseudoinverse workspace plus 5 R^2 + 2
 // doubles of intermediates when that fits in 160 KB (R <= 48), else the workspace only
 inline size_t update_smem(int R, int* inshared) {
   const size_t full = (spd_pinv_words(R) + 5 * (size_t)R * R + 2) * sizeof(double);
   *inshared = full <= 160 * 1024;
   return *inshared ? full : spd_pinv_smem(R);
-}
-
-// Warp 0: Cholesky A = R^T R and R^-1 (in T precision) into the workspace sh;
-// returns (in warp 0) whether every pivot was above 1e-300 (FP64) / the FP32
-// rounding level of A's diagonal (FP32).
-template <typename T>
-__device__ bool warp_spd_factor(const double* A, int n, T* sh) {
-  T* Rm = sh;
-  T* Mi = Rm + n * n;
-  T* rinv = Mi + n * n;
-  unsigned short* pairs = reinterpret_cast<unsigned short*>(rinv + n);
-  T md = T(0);
-  for (int e = threadIdx.x; e < n * n; e += 32) {
-    Rm[e] = (T)A[e];
-    Mi[e] = T(0);
-    if (e / n == e % n) md = fmax(md, Rm[e]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-  warp_pair_table(pairs, n);
-  const T thr = sizeof(T) == 8 ? T(1e-300) : T(64 * 1.2e-7) * md;
-  const int nd = warp_chol_upper<T>(Rm, n, thr, false, rinv, pairs);
-  if (nd == 0) warp_tri_inv<T>(Rm, n, rinv, Mi);
-  return nd == 0;
-}
-
-// Whole block, after warp_spd_factor and a barrier: Inv = R^-1 R^-T, or (ok
-// false) the eigen pseudoinverse (MATLAB tolerance n eps ||A||) of A.
-template <typename T, typename OutT>
-__device__ void block_spd_finish(bool ok, const double* A, OutT* Inv, double* L, double* V, int n, const T* sh,
-                                 int* status) {
-  const T* Mi = sh + n * n;
-  if (ok) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int a = e / n, b = e - a * n;
-      T s = T(0);
-      for (int i = max(a, b); i < n; ++i) s = fma(Mi[a * n + i], Mi[b * n + i], s);
-      Inv[e] = (OutT)s;
-    }
-    __syncthreads();
-    return;
-  }
-  if (threadIdx.x == 0) {
-    set_status(status, ST_PINV);
-    for (int e = 0; e < n * n; ++e) L[e] = A[e];
-    jacobi_eig_f64(L, V, n);
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(L[i * n + i]));
-    const double tol = n * 2.220446049250313e-16 * mx;
-    for (int a = 0; a < n; ++a)
-      for (int b = 0; b < n; ++b) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) {
-          const double l = L[i * n + i];
-          if (l > tol) s += V[a * n + i] * V[b * n + i] / l;
-        }
-        Inv[a * n + b] = (OutT)s;
-      }
-  }
-  __syncthreads();
-}
-
-// Inv <- A^+ for symmetric PSD A (n x n), computed by the whole block.
-template <typename T, typename OutT>
-__device__ void block_spd_pinv(const double* A, OutT* Inv, double* L, double* V, int n, T* sh, int* status) {
-  __shared__ int ok;
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<T>(A, n, sh);
-    if (threadIdx.x == 0) ok = f;
-  }
-  __syncthreads();
-  block_spd_finish<T, OutT>(ok != 0, A, Inv, L, V, n, sh, status);
-}
-
-// Scale factors 1 / ||column r|| for the R columns whose squared norms are
-// n2[r] (1 for a zero column); flags a non-finite norm.
-__device__ inline double inv_norm(double n2, int* status) {
-  if (!isfinite(n2)) set_status(status, ST_NONFINITE);
-  return n2 > 0.0 ? rsqrt_nr(n2) : 1.0;
 }
 
 // --------------------------------------------------------------- H update --
@@ -631,7 +450,8 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
                                                   double* __restrict__ WtW, const double* __restrict__ VtV,
                                                   float* __restrict__ H, double* __restrict__ HtH,
                                                   double* __restrict__ loss, double* __restrict__ scratch,
-                                                  int* __restrict__ status, int inshared) {
+                                                  int* __restrict__ status, int inshared,
+                                                  const double* __restrict__ InvPre) {
   extern __shared__ __align__(16) double ush[];
   __shared__ double scl[kMaxR];
   const int RR = R * R;
@@ -647,6 +467,13 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
   __shared__ int ok;
   __shared__ double red[kRedMax];
   const int T = blockDim.x;
+  if (InvPre) {
+    // W^T W, the loss and (W^T W * V^T V)^+ come from the Q-step's extra block
+    par_reduce_load(part, nq, pstride, RR, 0, T, red, G1);
+    __syncthreads();
+    par_reduce_combine(RR, 0, T, red, G1);
+    __syncthreads();
+  } else {
   if (it > 0) {
     par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red, W3);
     __syncthreads();
@@ -673,10 +500,12 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
   par_reduce_combine(RR, 32, T - 32, red, G1);
   __syncthreads();
   block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
+  }
+  const double* Iv = InvPre ? InvPre : Inv;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int i = e / R, r = e - i * R;
     double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(G1[i * R + m], Inv[m * R + r], s);
+    for (int m = 0; m < R; ++m) s = fma(G1[i * R + m], Iv[m * R + r], s);
     Hn[e] = s;
   }
   __syncthreads();
@@ -705,7 +534,8 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
                                                   const double* __restrict__ DtD, float* __restrict__ CV,
                                                   double* __restrict__ Psi, double* __restrict__ VtV,
                                                   double* __restrict__ Ginv, double* __restrict__ scratch,
-                                                  int* __restrict__ status, int inshared) {
+                                                  int* __restrict__ status, int inshared,
+                                                  const double* __restrict__ InvPre) {
   extern __shared__ __align__(16) double ush[];
   __shared__ double scl[kMaxR];
   const int RR = R * R;
@@ -719,6 +549,13 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
   __shared__ int ok;
   __shared__ double red[kRedMax];
   const int T = blockDim.x;
+  if (InvPre) {
+    // (W^T W * H^T H)^+ comes from the Lemma 2 grid's extra block
+    par_reduce_load(part, nblk, pstride, RR, 0, T, red, g);
+    __syncthreads();
+    par_reduce_combine(RR, 0, T, red, g);
+    __syncthreads();
+  } else {
   for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
   __syncthreads();
   // warp 0 factors (W^T W * H^T H) while the other threads reduce the Lemma 2 partials
@@ -731,10 +568,12 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
   par_reduce_combine(RR, 32, T - 32, red, g);
   __syncthreads();
   block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
+  }
+  const double* Iv = InvPre ? InvPre : Inv;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int i = e / R, r = e - i * R;
     double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(g[i * R + m], Inv[m * R + r], s);
+    for (int m = 0; m < R; ++m) s = fma(g[i * R + m], Iv[m * R + r], s);
     C[e] = s;
   }
   __syncthreads();
@@ -1015,25 +854,50 @@ void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
                                                      2 * R * R + 2, b.status, 0, b.rank);
 }
 
-// One iteration = 5 launches: Q-step (+ Lemma 1 partials), H update (closing
-// the previous iteration's W^T W and e), Lemma 2 partials, V update, Lemma 3
-// + W update (+ W^T W and e partials).  Partials use three separate regions.
+// One iteration = 5 launches: Q-step (+ Lemma 1 partials; its extra block
+// closes the previous iteration's W^T W and e and factors the H update's
+// matrix), H update, Lemma 2 partials (extra block: the V update's factor),
+// V update, Lemma 3 + W update (+ W^T W and e partials).  Partials use three
+// separate regions.
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   const int R = b.R, RR = R * R, nw = als_warps(R);
   const int ps = 2 * RR + 2;
   float* p1 = b.part;
   float* p2 = b.part + (size_t)b.pr * ps;
   float* p3 = b.part + (size_t)2 * b.pr * ps;
-  if (!launch_qstep_reg(b, p1, ps, 1, s))
+  // the H update's factor (closing the previous iteration's W^T W and loss)
+  // in the Q-step's extra block, the V update's in the Lemma 2 grid's
+  const bool pre = b.InvH && b.InvV;
+  PreSolve ph, pv;
+  ph.R = pv.R = R;
+  ph.part3 = it > 0 ? p3 : nullptr;
+  ph.nparts = b.nblk;
+  ph.pstride = ps;
+  ph.it = it;
+  ph.WtW = pv.WtW = b.WtW;
+  ph.B = b.VtV;
+  pv.B = b.HtH;
+  ph.loss = b.loss;
+  ph.Inv = b.InvH;
+  pv.Inv = b.InvV;
+  ph.L = pv.L = b.small;
+  ph.V = pv.V = b.small + RR;
+  ph.status = pv.status = b.status;
+  bool preh = pre;
+  if (!launch_qstep_reg(b, p1, ps, 1, s, pre ? &ph : nullptr)) {
     k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
                                                        b.status, 1, b.rank);
+    preh = false;
+  }
   int insh = 0;
   const size_t psm = update_smem(R, &insh);
   k_update_h<<<1, 1024, psm, s>>>(R, p1, b.nq, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small,
-                                 b.status, insh);
-  k_g2<<<b.nblk, nw * 32, (size_t)(RR + nw * RR + nw * RR) * 4, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps);
+                                 b.status, insh, preh ? b.InvH : nullptr);
+  size_t g2sm = (size_t)(RR + nw * RR + nw * RR) * 4;
+  if (pre) g2sm = std::max(g2sm, pre_solve_words(R, nw * 32) * sizeof(double));
+  k_g2<<<b.nblk + (pre ? 1 : 0), nw * 32, g2sm, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps, pv, pre ? 1 : 0);
   k_update_v<<<1, 1024, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
-                               b.status, insh);
+                               b.status, insh, pre ? b.InvV : nullptr);
   k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
       b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, p3, ps);
 }

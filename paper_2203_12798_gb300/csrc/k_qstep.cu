@@ -25,6 +25,7 @@
 // across iterations).  The polar factor does not depend on the start.
 #include "common.cuh"
 #include "internal.h"
+#include "small_solve.cuh"
 
 namespace dp2 {
 
@@ -34,13 +35,19 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
                                                    const float* __restrict__ H, float* __restrict__ Upol,
                                                    float* __restrict__ Pi, float* __restrict__ part, int pstride,
                                                    int* __restrict__ status, int want_g1,
-                                                   float* __restrict__ Prot, const int* __restrict__ rank) {
+                                                   float* __restrict__ Prot, const int* __restrict__ rank,
+                                                   PreSolve pre, int pre_on) {
   constexpr int G = 32 / R;  // problems per warp
   constexpr int RR = R * R;
   constexpr int M = R + (R & 1);  // round-robin players (one dummy when R is odd)
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ float ps[RR], hs[RR];
-  extern __shared__ float sm[];  // [nw][G][3 RR] group scratch, then [nw][G][RR] G1 slots
+  extern __shared__ __align__(16) float sm[];  // [nw][G][3 RR] group scratch, then [nw][G][RR] G1 slots
+  if (pre_on && blockIdx.x == gridDim.x - 1) {  // the H update's factor (pre_solve)
+    pre_solve(pre, reinterpret_cast<double*>(sm));
+    return;
+  }
+  const int nb = gridDim.x - pre_on;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / R, c = lane - g * R;
   const bool lane_act = g < G;
@@ -66,7 +73,7 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
 #pragma unroll
   for (int i = 0; i < R; ++i) acc[i] = 0.f;
 
-  for (int64_t kb = ((int64_t)blockIdx.x * nw + warp) * G; kb < K; kb += (int64_t)gridDim.x * nw * G) {
+  for (int64_t kb = ((int64_t)blockIdx.x * nw + warp) * G; kb < K; kb += (int64_t)nb * nw * G) {
     const int64_t k = kb + g;
     const bool act = lane_act && k < K;
     // F~_k, column c
@@ -347,18 +354,24 @@ static int qreg_nw() {
 }
 
 template <int R>
-static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s, const PreSolve* pre) {
   constexpr int G = 32 / R;
   const size_t per_warp = (size_t)G * 4 * R * R * sizeof(float);
   const int nw = qreg_nw<R>();
-  const size_t smem = nw * per_warp;
+  size_t smem = nw * per_warp;
+  PreSolve p0;
+  const int on = pre ? 1 : 0;
+  if (pre) {
+    p0 = *pre;
+    smem = std::max(smem, pre_solve_words(b.R, nw * 32) * sizeof(double));
+  }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_qstep_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     attr = true;
   }
-  k_qstep_reg<R><<<b.nq, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                             b.status, want_g1, b.Prot, b.rank);
+  k_qstep_reg<R><<<b.nq + on, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
+                                                  b.status, want_g1, b.Prot, b.rank, p0, on);
 }
 
 template <int R>
@@ -385,18 +398,18 @@ int qstep_blocks(int K, int R, int nblk) {
 // Launches the register-resident Q-step when the rank has an instantiation
 // (exact for R in {10, 20, 30}, zero-padded to 8, 16, 24 or 32 otherwise;
 // the warp-pair kernel for 32 < R <= 64); returns false for R > 64.
-bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s, const PreSolve* pre) {
   switch (b.R) {
-    case 10: qreg<10>(b, part, pstride, want_g1, s); return true;
-    case 20: qreg<20>(b, part, pstride, want_g1, s); return true;
-    case 30: qreg<30>(b, part, pstride, want_g1, s); return true;
+    case 10: qreg<10>(b, part, pstride, want_g1, s, pre); return true;
+    case 20: qreg<20>(b, part, pstride, want_g1, s, pre); return true;
+    case 30: qreg<30>(b, part, pstride, want_g1, s, pre); return true;
     default: break;
   }
-  if (b.R <= 8) qreg<8>(b, part, pstride, want_g1, s);
-  else if (b.R <= 16) qreg<16>(b, part, pstride, want_g1, s);
-  else if (b.R <= 24) qreg<24>(b, part, pstride, want_g1, s);
-  else if (b.R <= 32) qreg<32>(b, part, pstride, want_g1, s);
-  else return launch_qstep_wide(b, part, pstride, want_g1, s);
+  if (b.R <= 8) qreg<8>(b, part, pstride, want_g1, s, pre);
+  else if (b.R <= 16) qreg<16>(b, part, pstride, want_g1, s, pre);
+  else if (b.R <= 24) qreg<24>(b, part, pstride, want_g1, s, pre);
+  else if (b.R <= 32) qreg<32>(b, part, pstride, want_g1, s, pre);
+  else return launch_qstep_wide(b, part, pstride, want_g1, s, pre);
   return true;
 }
 

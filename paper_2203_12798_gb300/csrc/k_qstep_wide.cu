@@ -26,6 +26,7 @@
 // rotate).
 #include "common.cuh"
 #include "internal.h"
+#include "small_solve.cuh"
 
 namespace dp2 {
 
@@ -63,7 +64,8 @@ template <int R>
 __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
     int K, int Ra, const float* __restrict__ Ft, const double* __restrict__ Psi, const float* __restrict__ W,
     const float* __restrict__ H, float* __restrict__ Upol, float* __restrict__ Pi, float* __restrict__ part,
-    int pstride, int* __restrict__ status, int want_g1, float* __restrict__ Prot, const int* __restrict__ rank) {
+    int pstride, int* __restrict__ status, int want_g1, float* __restrict__ Prot, const int* __restrict__ rank,
+    PreSolve pre, int pre_on) {
   static_assert(R % 2 == 0 && R > 32 && R <= 64, "32 < R <= 64, even");
   constexpr int HP = R / 2;  // column pairs
   constexpr int LD = qw_ld<R>();
@@ -71,6 +73,11 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
   constexpr int NP = qw_pairs<R>();
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) float sm[];
+  if (pre_on && blockIdx.x == gridDim.x - 1) {  // the H update's factor (pre_solve)
+    pre_solve(pre, reinterpret_cast<double*>(sm));
+    return;
+  }
+  const int nb = gridDim.x - pre_on;
   float* ps = sm;            // Psi (R x LD)
   float* hs = ps + R * LD;   // H
   const int pair = threadIdx.x >> 6, pt = threadIdx.x & 63, lane = threadIdx.x & 31;
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
   const bool act = lane < HP;
   const int j0 = lane, j1 = HP + lane;  // the columns this lane starts with
 
-  for (int64_t k = (int64_t)blockIdx.x * NP + pair; k < K; k += (int64_t)gridDim.x * NP) {
+  for (int64_t k = (int64_t)blockIdx.x * NP + pair; k < K; k += (int64_t)nb * NP) {
     // ---- F~_k, V0, W(k, :)
     for (int e = pt; e < RR; e += 64) {
       const int i = e / R, c = e % R;
@@ -380,15 +387,18 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
 }
 
 template <int R>
-static void qwide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+static void qwide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s, const PreSolve* pre) {
   constexpr int NP = qw_pairs<R>();
+  PreSolve p0;
+  const int on = pre ? 1 : 0;
+  if (pre) p0 = *pre;  // pre_solve_words(R, 64 NP) fits the Q-step's shared memory for R <= 64
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_qstep_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qw_smem<R>());
     attr = true;
   }
-  k_qstep_wide<R><<<b.nq, 64 * NP, qw_smem<R>(), s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                                        b.status, want_g1, b.Prot, b.rank);
+  k_qstep_wide<R><<<b.nq + on, 64 * NP, qw_smem<R>(), s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part,
+                                                             pstride, b.status, want_g1, b.Prot, b.rank, p0, on);
 }
 
 // Blocks: one slice per pair of warps, at most `cap` blocks (the blocks loop
@@ -409,13 +419,13 @@ int qstep_wide_blocks(int K, int R, int cap) {
   return qwide_blocks<64>(K, cap);
 }
 
-bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s) {
+bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s, const PreSolve* pre) {
   if (b.R <= 32 || b.R > 64) return false;
-  if (b.R == 40) qwide<40>(b, part, pstride, want_g1, s);
-  else if (b.R == 50) qwide<50>(b, part, pstride, want_g1, s);
-  else if (b.R <= 48) qwide<48>(b, part, pstride, want_g1, s);
-  else if (b.R <= 56) qwide<56>(b, part, pstride, want_g1, s);
-  else qwide<64>(b, part, pstride, want_g1, s);
+  if (b.R == 40) qwide<40>(b, part, pstride, want_g1, s, pre);
+  else if (b.R == 50) qwide<50>(b, part, pstride, want_g1, s, pre);
+  else if (b.R <= 48) qwide<48>(b, part, pstride, want_g1, s, pre);
+  else if (b.R <= 56) qwide<56>(b, part, pstride, want_g1, s, pre);
+  else qwide<64>(b, part, pstride, want_g1, s, pre);
   return true;
 }
 
