@@ -69,9 +69,13 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
   // sweep that would only confirm it is skipped
   const float rstop = sqrtf(tol * rsqrtf((float)Ra));
   const int RaRa = Ra * Ra;
-  float acc[R];
+  // Lemma 1 partial of this group, column c owned by lane c (accumulated in
+  // shared memory: no registers held across the sweeps)
+  float* gslot = slots + (size_t)(warp * G + (lane_act ? g : 0)) * RR;
+  if (lane_act) {
 #pragma unroll
-  for (int i = 0; i < R; ++i) acc[i] = 0.f;
+    for (int i = 0; i < R; ++i) gslot[i * R + c] = 0.f;
+  }
 
   for (int64_t kb = ((int64_t)blockIdx.x * nw + warp) * G; kb < K; kb += (int64_t)nb * nw * G) {
     const int64_t k = kb + g;
@@ -82,8 +86,12 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
       for (int i = 0; i < R; ++i) Fs[i * R + c] = (act && i < Ra && c < Ra) ? Ft[k * RaRa + i * Ra + c] : 0.f;
     }
     float wk[R];
+    float wc = 0.f;  // W(k, c), picked without indexing wk by the lane's column
 #pragma unroll
-    for (int r = 0; r < R; ++r) wk[r] = (act && r < Ra) ? W[k * Ra + r] : 0.f;
+    for (int r = 0; r < R; ++r) {
+      wk[r] = (act && r < Ra) ? W[k * Ra + r] : 0.f;
+      if (r == c) wc = wk[r];
+    }
     __syncwarp();
     // A1 = F~_k Psi, column c
     float t[R];
@@ -316,22 +324,19 @@ __global__ void __launch_bounds__(R <= 12 ? 192 : 256, R <= 12 ? 3 : 1) k_qstep_
       }
       __syncwarp();
       // Lemma 1: G1(i, c) += W(k, c) (Pi Psi)(i, c)
-      const float wc = act ? wk[c] : 0.f;
+      if (lane_act) {
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        float s = 0.f;
+        for (int i = 0; i < R; ++i) {
+          float s = 0.f;
 #pragma unroll
-        for (int m = 0; m < R; ++m) s = fmaf(Ps[i * R + m], ps[m * R + c], s);
-        acc[i] = fmaf(wc, s, acc[i]);
+          for (int m = 0; m < R; ++m) s = fmaf(Ps[i * R + m], ps[m * R + c], s);
+          gslot[i * R + c] = fmaf(wc, s, gslot[i * R + c]);
+        }
       }
     }
     __syncwarp();
   }
   if (!want_g1) return;
-  if (lane_act) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) slots[(size_t)(warp * G + g) * RR + i * R + c] = acc[i];
-  }
   __syncthreads();
   for (int e = threadIdx.x; e < RaRa; e += blockDim.x) {
     const int i = e / Ra, cc = e % Ra;
