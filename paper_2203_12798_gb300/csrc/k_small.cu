@@ -202,16 +202,21 @@ __global__ void k_reduce_rows_f64(const double* __restrict__ part, int K, int n,
 constexpr int GB_THREADS = 256;
 
 template <int LP, int TE>  // TE = ceil(l / 4) tiles carry data (rows >= l of B1 are zero)
-__global__ void __launch_bounds__(GB_THREADS, 3) k_gram_b1(const float* __restrict__ B1, int Jp, int J, int ell,
+__global__ void __launch_bounds__(GB_THREADS, 4) k_gram_b1(const float* __restrict__ B1, int Jp, int J, int ell,
                                                         double* __restrict__ G) {
   constexpr int CR = 4 * TE;                   // rows of B1 staged
-  constexpr int GB_CJ = CR <= 32 ? 128 : 64;  // columns per chunk (static shared memory <= 48 KB)
+  // columns per chunk: as many as keep the staging buffer within 48 KB of
+  // static shared memory (more loads in flight per thread)
+  constexpr int GB_CJ = CR <= 24 ? 256 : (CR <= 48 ? 128 : 64);
   constexpr int NT = TE * (TE + 1) / 2;
   constexpr int NG = GB_THREADS / NT > 0 ? GB_THREADS / NT : 1;
   constexpr int PER = CR * GB_CJ / GB_THREADS;  // chunk elements per thread
   static_assert(CR * GB_CJ % GB_THREADS == 0, "chunk split");
-  __shared__ __align__(16) float bs[GB_CJ][CR + 4];
-  __shared__ float red[NG > 1 ? NG : 1][CR][CR + 1];
+  constexpr int BS_FLOATS = GB_CJ * (CR + 4), RED_FLOATS = (NG > 1 ? NG : 1) * CR * (CR + 1);
+  // the block reduction reuses the staging buffer after the last chunk
+  __shared__ __align__(16) float smem_[BS_FLOATS > RED_FLOATS ? BS_FLOATS : RED_FLOATS];
+  float (*bs)[CR + 4] = reinterpret_cast<float (*)[CR + 4]>(smem_);
+  float (*red)[CR][CR + 1] = reinterpret_cast<float (*)[CR][CR + 1]>(smem_);
   const int k = blockIdx.x, tid = threadIdx.x;
   const int grp = tid / NT, tt = tid % NT;
   int ta = 0, tb = 0;
