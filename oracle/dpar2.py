@@ -8,7 +8,7 @@ Notation follows the paper: slices X_k (I_k x J), target rank R, test matrix
 Omega (J x (R+s)), stage-1 factors A_k B_k C_k^T, stage-2 factors D E F^T with
 R x R blocks F^(k), PARAFAC2 factors Q_k, H, S_k = diag(W(k,:)), V.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
   * randomized SVD keeps min(R, rank) components; singular values of B at or
     below max(I,J) * eps * sigma_1 count as zero, and their columns of A, C
     and entries of B are set to zero (A stays column-orthonormal on the rest);
