@@ -474,32 +474,32 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
     par_reduce_combine(RR, 0, T, red, G1);
     __syncthreads();
   } else {
-  if (it > 0) {
-    par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red, W3);
-    __syncthreads();
-    par_reduce_combine(RR + 2, 0, T, red, W3);
-    __syncthreads();
-    for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
-      if (e < RR) WtW[e] = W3[e];
-      else {
-        const double v = W3[RR] + W3[RR + 1];
-        loss[it - 1] = v;
-        if (!isfinite(v)) set_status(status, ST_NONFINITE);
+    if (it > 0) {
+      par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red, W3);
+      __syncthreads();
+      par_reduce_combine(RR + 2, 0, T, red, W3);
+      __syncthreads();
+      for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
+        if (e < RR) WtW[e] = W3[e];
+        else {
+          const double v = W3[RR] + W3[RR + 1];
+          loss[it - 1] = v;
+          if (!isfinite(v)) set_status(status, ST_NONFINITE);
+        }
       }
     }
-  }
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = (it > 0 ? W3[e] : WtW[e]) * VtV[e];
-  __syncthreads();
-  // warp 0 factors (W^T W * V^T V) while the other threads reduce the Lemma 1 partials
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<double>(Gm, R, ush);
-    if (threadIdx.x == 0) ok = f;
-  }
-  par_reduce_load(part, nq, pstride, RR, 32, T - 32, red, G1);
-  __syncthreads();
-  par_reduce_combine(RR, 32, T - 32, red, G1);
-  __syncthreads();
-  block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = (it > 0 ? W3[e] : WtW[e]) * VtV[e];
+    __syncthreads();
+    // warp 0 factors (W^T W * V^T V) while the other threads reduce the Lemma 1 partials
+    if (threadIdx.x < 32) {
+      const bool f = warp_spd_factor<double>(Gm, R, ush);
+      if (threadIdx.x == 0) ok = f;
+    }
+    par_reduce_load(part, nq, pstride, RR, 32, T - 32, red, G1);
+    __syncthreads();
+    par_reduce_combine(RR, 32, T - 32, red, G1);
+    __syncthreads();
+    block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
   }
   const double* Iv = InvPre ? InvPre : Inv;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -556,18 +556,18 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
     par_reduce_combine(RR, 0, T, red, g);
     __syncthreads();
   } else {
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
-  __syncthreads();
-  // warp 0 factors (W^T W * H^T H) while the other threads reduce the Lemma 2 partials
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<double>(Gm, R, ush);
-    if (threadIdx.x == 0) ok = f;
-  }
-  par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red, g);
-  __syncthreads();
-  par_reduce_combine(RR, 32, T - 32, red, g);
-  __syncthreads();
-  block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
+    __syncthreads();
+    // warp 0 factors (W^T W * H^T H) while the other threads reduce the Lemma 2 partials
+    if (threadIdx.x < 32) {
+      const bool f = warp_spd_factor<double>(Gm, R, ush);
+      if (threadIdx.x == 0) ok = f;
+    }
+    par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red, g);
+    __syncthreads();
+    par_reduce_combine(RR, 32, T - 32, red, g);
+    __syncthreads();
+    block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
   }
   const double* Iv = InvPre ? InvPre : Inv;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
