@@ -229,7 +229,8 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);
 int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
-// register-resident Q-step (lane = column); false when R has no instantiation (R > 32)
+// register-resident Q-step (R <= 32: lane = column; 32 < R <= 64: the warp-pair
+// kernel); false for R > 64.  `pre`: run pre_solve in an extra block
 bool launch_qstep_reg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s,
                       const PreSolve* pre = nullptr);
 bool launch_qstep_wide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaStream_t s,

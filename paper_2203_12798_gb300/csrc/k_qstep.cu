@@ -397,7 +397,7 @@ int qstep_blocks(int K, int R, int nblk) {
   if (R <= 24) return qblocks<24>(K);
   if (R <= 32) return qblocks<32>(K);
   if (R <= 64) return qstep_wide_blocks(K, R, nblk);
-  return nblk;  // shared-memory Q-step on the Lemma 2 / 3 grid
+  return nblk;  // R > 64: the shared-memory Q-step on the Lemma 2 / 3 grid
 }
 
 // Launches the register-resident Q-step when the rank has an instantiation
