@@ -124,6 +124,12 @@ DPAR2_API const char* dpar2_last_error(const dpar2_ctx* ctx);
 #define DPAR2_INFO_SWEEP_CAP 8
 #define DPAR2_INFO_PINV 16
 DPAR2_API int dpar2_last_info(const dpar2_ctx* ctx);
+/* Number of kernels this library has launched since it was loaded, over all
+ * contexts and threads (kernels run from a CUDA graph count once per graph
+ * launch).  The paper has no counterpart; for accounting, e.g. launches per
+ * fit: read it before and after the calls of interest, with no other thread
+ * using the library meanwhile. */
+DPAR2_API long long dpar2_kernel_launches(void);
 
 /* Fill out[0..n) (device, float32) with the Gaussian stream (seed, stream_id):
  * Philox4x32-10 (Salmon et al. SC'11) with counter (n/4 lo, n/4 hi, stream_id, 0)
@@ -161,6 +167,36 @@ DPAR2_API dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_
                             int64_t ldx, dpar2_dtype dtype, const dpar2_options* opt, const float* omega,
                             const float* omega2, dpar2_comp** out, void* stream);
 
+/* The same two-stage compression for a tensor held in host memory (Sec. III-B;
+ * every slice is compressed from its own rows by Alg. 1, so stage 1 can run
+ * chunk by chunk).  The slices are cut into chunks of whole slices of about
+ * chunk_bytes of X; each chunk is copied to the device once, on a copy stream
+ * of the context, while the previous chunk's stage 1 runs, so X crosses the
+ * host link once and the copies hide the stage-1 work.  X need not fit in
+ * device memory unless X_dev is given.
+ *   X_host       host, sum(I_k) rows of J elements of `dtype`, packed (row
+ *                stride J).  Pinned (page-locked) memory gives asynchronous,
+ *                full-rate copies; pageable memory works but copies slowly.
+ *                Read only; must stay valid until the call returns.
+ *   X_dev        device buffer of sum(I_k) rows of ldx elements that receives X
+ *                (columns J..ldx-1 zero), for later calls that read X again
+ *                (dpar2_reconstruct_error's streamed mode); or NULL: two chunk
+ *                buffers of the context are used and X is not kept.  ldx: as for
+ *                dpar2_compress (ignored when X_dev is NULL).
+ *   chunk_bytes  target bytes of X per chunk (0: 512 MB); a chunk holds at
+ *                least one slice.  Context scratch: two staging buffers of the
+ *                largest chunk (unless ldx == J) and, without X_dev, two chunk
+ *                buffers of it.
+ * Other arguments, outputs and errors as dpar2_compress.  The result is the
+ * compression dpar2_compress computes from the same X (the same kernels per
+ * slice; chunks of fewer than 256 slices sum the CholeskyQR Grams of their
+ * slices in a different order, a difference at rounding level).  Only the
+ * DPAR2_PH_COMPRESS phase time is recorded. */
+DPAR2_API dpar2_status dpar2_compress_host(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets,
+                                           const void* X_host, dpar2_dtype dtype, const dpar2_options* opt,
+                                           const float* omega, const float* omega2, void* X_dev, int64_t ldx,
+                                           size_t chunk_bytes, dpar2_comp** out, void* stream);
+
 /* ALS iterations on the compressed slices (Alg. 3 repeat loop, Sec. III-C..E).
  *   comp          from dpar2_compress
  *   opt           R must equal the compression's R; max_iter, tol, seed, flags used
@@ -196,9 +232,11 @@ DPAR2_API dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp*
  * fixed array of DPAR2_NOALLOC_SCRATCH_BYTES (18 MiB) in the library's device
  * image, one per device, enough for K R^2 <= 4,194,304 (for example K = 8000
  * slices at R <= 22); larger problems are rejected with DPAR2_ERR_INVALID_ARG
- * before anything is launched.  The first call on a device looks up the
- * array's address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  No scratch word has to start at zero: every word a call
+ * before anything is launched.  Every call looks up the array's address on
+ * the context's device (cudaGetSymbolAddress, which allocates nothing), so a
+ * device context that was reset between calls is handled; the first call on
+ * a device may also load the library's device code there, so make that first
+ * call before any stream capture.  No scratch word has to start at zero: every word a call
  * reads is written earlier in the same call.  All calls on a device share the
  * one array, so calls that overlap in time (other host threads, other
  * contexts on the same device) race on it and must be serialised by the

@@ -55,6 +55,10 @@ SIGNATURES = {
     "dpar2_philox_words": (ctypes.c_int, [VP, ctypes.c_uint64, ctypes.c_uint32, I64, VP, VP]),
     "dpar2_compress": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP, I64,
                                       ctypes.c_int, ctypes.POINTER(Options), VP, VP, ctypes.POINTER(VP), VP]),
+    "dpar2_compress_host": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP,
+                                           ctypes.c_int, ctypes.POINTER(Options), VP, VP, VP, I64, ctypes.c_size_t,
+                                           ctypes.POINTER(VP), VP]),
+    "dpar2_kernel_launches": (ctypes.c_longlong, []),
     "dpar2_fit": (ctypes.c_int, [VP, VP, ctypes.POINTER(Options), VP, VP, VP, VP, VP, VP, DP,
                                  ctypes.POINTER(ctypes.c_int), DP, VP]),
     "dpar2_reconstruct_error": (ctypes.c_int, [VP, VP, VP, I64, ctypes.c_int, VP, VP, VP, VP, DP, DP, VP]),
@@ -90,6 +94,11 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched since it was loaded (all contexts)."""
+    return int(lib().dpar2_kernel_launches())
 
 
 def _stream():
@@ -184,6 +193,26 @@ class Context:
         self._check(lib().dpar2_compress(self._h, K, J, offp, _ptr(X), X.stride(0), _DT[X.dtype],
                                          ctypes.byref(opt), _ptr(omega), _ptr(omega2), ctypes.byref(h),
                                          _stream()))
+        return Compressed(self, h, off)
+
+    def compress_host(self, Xh: torch.Tensor, offsets, R=10, p=10, q=0, seed=0, omega=None, omega2=None, flags=0,
+                      X_dev=None, chunk_bytes=0, schedule=-1) -> "Compressed":
+        """Xh: host tensor (sum I_k) x J of float32/bfloat16/float16, packed rows
+        (pin_memory() for asynchronous copies); X_dev: optional CUDA tensor
+        (sum I_k) x ldx receiving X."""
+        assert not Xh.is_cuda and Xh.dim() == 2 and Xh.is_contiguous()
+        J = Xh.shape[1]
+        off = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
+        K = off.numel() - 1
+        opt = Options()
+        lib().dpar2_options_default(ctypes.byref(opt))
+        opt.R, opt.p, opt.q, opt.seed, opt.flags, opt.schedule = R, p, q, seed, flags, schedule
+        h = ctypes.c_void_p()
+        offp = ctypes.cast(off.data_ptr(), ctypes.POINTER(ctypes.c_int64))
+        ldx = X_dev.stride(0) if X_dev is not None else 0
+        self._check(lib().dpar2_compress_host(self._h, K, J, offp, ctypes.c_void_p(Xh.data_ptr()), _DT[Xh.dtype],
+                                              ctypes.byref(opt), _ptr(omega), _ptr(omega2), _ptr(X_dev), ldx,
+                                              chunk_bytes, ctypes.byref(h), _stream()))
         return Compressed(self, h, off)
 
     def fit(self, comp: "Compressed", max_iter=32, tol=-1.0, seed=0, V0=None, want_U=False, want_upol=True,

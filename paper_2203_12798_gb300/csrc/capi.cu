@@ -4,9 +4,9 @@
 // library; the host only validates, allocates, launches and reads back the
 // status word and the requested scalars.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,6 +14,14 @@
 #include "internal.h"
 
 using namespace dp2;
+
+namespace dp2 {
+// Kernels enqueued by this library since it was loaded (all contexts and
+// threads).  Launches recorded into a CUDA graph are taken back out when the
+// capture ends and counted again each time the graph is launched.
+std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace dp2
 
 namespace {
 
@@ -281,6 +289,330 @@ __global__ void k_sum_f64(const double* __restrict__ v, int n, double* __restric
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
+// Stage 1 of the compression (Alg. 1 for every slice; the first loop of
+// Alg. 3) on the slices k0 .. k0 + Kc - 1, whose rows start at X (row 0 is
+// the first row of slice k0, row pitch ldx): the sketch, CholeskyQR2 (and the
+// power iterations), the projection with ||X_k||^2, the small SVDs, the
+// blocks C_k B_k of M and A_k.  off: host offsets of those slices relative to
+// their first row (Kc + 1), d_off the same on the device.  Writes the
+// compression's A rows, B_k, M blocks, ||X_k||^2 and ranks of these slices;
+// scratch is the context's (sized for this range).  Every slice is computed
+// the same way whatever range it is part of, except for the Gram row splits
+// of ranges shorter than 256 slices (a different summation order).
+void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, dpar2_dtype dtype,
+                  const dpar2_options* opt, int k0, int Kc, const int64_t* off, const int64_t* d_off,
+                  const float* om_pad, bool timed, cudaStream_t s) {
+  const int J = comp->J, R = comp->R, ell = comp->ell, LP = comp->LP;
+  const int Jp = round_up(J, 4), Jpad = round_up(J, 32);
+  const int64_t N = off[Kc];
+  int64_t maxI = 0;
+  for (int k = 0; k < Kc; ++k) maxI = std::max<int64_t>(maxI, off[k + 1] - off[k]);
+  const size_t es = dtype_size(dtype);
+  int* rank1 = static_cast<int*>(comp->rank1.p) + k0;
+  double* xn2 = static_cast<double*>(comp->xnorm2.p) + k0;
+  float* Bk = static_cast<float*>(comp->Bk.p) + (size_t)k0 * R;
+  float* Mb = static_cast<float*>(comp->M.p) + (size_t)k0 * J * R;
+  float* Aout = static_cast<float*>(comp->A.p) + (size_t)comp->h_offsets[k0] * R;
+  auto tb = [&](int ph) { if (timed) tbegin(ctx, s, ph); };
+  auto te = [&](int ph) { if (timed) tend(ctx, s, ph); };
+  // ---- sketch Y = X Omega (pass 1 over X) ----
+  float* Y = wsget<float>(ctx, "Y", (size_t)N * LP);
+  float* M2 = wsget<float>(ctx, "M2", (size_t)Kc * LP * LP);
+  float* B1 = wsget<float>(ctx, "B1", (size_t)Kc * LP * Jp);
+  const int nJb = project_blocks(Jp, LP);
+  double* xpart = wsget<double>(ctx, "xpart", (size_t)Kc * nJb);
+  // tensor-core path: 16-bit X, all slices in one persistent launch
+  const bool use_tc = dtype != DPAR2_F32 && !(opt->flags & (DPAR2_FLAG_GENERIC | DPAR2_FLAG_PER_SLICE)) &&
+                      tc_available();
+  const int LPN = tc_lpn(ell);
+  void* omT16 = nullptr;
+  if (use_tc) {
+    omT16 = wsget<uint16_t>(ctx, "omT16", (size_t)LPN * Jpad);
+    launch_omega_t16(om_pad, Jpad, LP, LPN, dtype, omT16, s);
+  }
+  tb(DPAR2_PH_SKETCH);
+  bool sketched = false;
+  if (use_tc)
+    sketched = launch_sketch_tc(X, dtype, ldx, N, J, omT16, Jpad, LPN, LP, Y, ctx->num_sms, ctx->d_status, s);
+  if (sketched) {
+  } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+    for (int k = 0; k < Kc; ++k) {
+      const int64_t r0 = off[k], nk = off[k + 1] - r0;
+      launch_sketch_generic(static_cast<const char*>(X) + r0 * ldx * es, dtype, ldx, nk, J, om_pad, LP,
+                            Y + r0 * LP, s);
+    }
+  } else {
+    launch_sketch_generic(X, dtype, ldx, N, J, om_pad, LP, Y, s);
+  }
+  te(DPAR2_PH_SKETCH);
+  tb(DPAR2_PH_QR);
+  cholqr2(ctx, Y, d_off, Kc, maxI, ell, LP, M2, rank1, s, "s1");
+  // tensor-core projection operands: Q1 split into three exact-sum 16-bit
+  // parts, slices padded to 64 rows; one partial ||X_k||^2 per (slice,
+  // column block, norm warp)
+  std::vector<int64_t> hp, htoff;
+  int64_t maxPad = 0;
+  ProjSched pj;  // the projection's slice-to-CTA schedule (choice -1: tune on this call)
+  const std::string tkey = tune_key(Kc, J, ell, dtype, N, maxI);
+  int64_t* d_poff = nullptr;
+  void* Qs = nullptr;
+  double* xp = nullptr;
+  int PNS = 0, POFF = 0;  // layout of the projection's Q operand
+  proj_layout(ell, &PNS, &POFF);
+  const int nJb_tc = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
+  if (use_tc) {
+    hp.assign(Kc + 1, 0);
+    for (int k = 0; k < Kc; ++k) {
+      const int64_t pk = round_up64(off[k + 1] - off[k], 64);
+      hp[k + 1] = hp[k] + pk;
+      maxPad = std::max(maxPad, pk);
+    }
+    d_poff = wsget<int64_t>(ctx, "poff", (size_t)Kc + 1);
+    h2d_i64(ctx, d_poff, hp.data(), (Kc + 1), s);
+    Qs = wsget<uint16_t>(ctx, "Qs", (size_t)PNS * hp[Kc]);
+    xp = wsget<double>(ctx, "xpart_tc", (size_t)Kc * nJb_tc * kProjNormWarps);
+    int choice = opt->schedule;
+    if (choice < 0) {
+      auto it = ctx->tuned.find(tkey);
+      if (it != ctx->tuned.end()) choice = it->second;
+    }
+    pj = proj_sched(ctx, choice > 1 ? 0 : choice, off, Kc, nJb_tc, tkey, s);
+    if (choice < 0) pj.choice = -1;
+  }
+  // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
+  int64_t* d_toff = nullptr;
+  if (use_tc && opt->q > 0) {
+    htoff.assign(Kc + 1, 0);
+    for (int k = 0; k < Kc; ++k) htoff[k + 1] = htoff[k] + (off[k + 1] - off[k] + 127) / 128;
+    d_toff = wsget<int64_t>(ctx, "toff", (size_t)Kc + 1);
+    h2d_i64(ctx, d_toff, htoff.data(), (Kc + 1), s);
+  }
+  for (int it = 0; it < opt->q; ++it) {
+    if (use_tc) {
+      // B1 = Q1^T X, then Y_k = X_k B1_k^T on the tensor cores: X_k X_k^T Q_k =
+      // X_k B1_k^T M2_k up to the upper-triangular M2_k (and the power-of-two
+      // row scales of the operand), which leave the next CholeskyQR2's Q unchanged
+      launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, Kc, hp[Kc], maxPad, dtype, Qs, s);
+      bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, hp[Kc], PNS, POFF, LP, B1, xp, nJb_tc, true,
+                                  ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
+      require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+      void* Ms = wsget<uint16_t>(ctx, "Ms", (size_t)Kc * 3 * LPN * Jpad);
+      launch_sl_rowsplit(B1, Kc, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr,
+                         wsget<float>(ctx, "Ms_scale", (size_t)Kc * LP), s);
+      ok = launch_sketch_seg_tc(X, dtype, ldx, N, J, d_off, d_toff, htoff[Kc], Kc, Ms, Jpad, LPN, LP, Y,
+                                ctx->num_sms, ctx->d_status, s);
+      require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
+    } else {
+      DP2_COUNTED(k_apply_m2<<<dim3((unsigned)((maxI + 127) / 128), Kc), 128, 0, s>>>(Y, d_off, LP, M2));
+      launch_project_generic(X, dtype, ldx, d_off, Kc, J, Jp, Y, LP, B1, nullptr, nullptr, s);
+      float* omk = wsget<float>(ctx, "omk", (size_t)Kc * Jpad * LP);
+      DP2_COUNTED(k_b1_to_omk<<<4096, 256, 0, s>>>(B1, Kc, ell, LP, J, Jp, Jpad, omk));
+      launch_sketch_generic_per_slice(X, dtype, ldx, d_off, Kc, (int)maxI, J, omk, Jpad, LP, Y, s);
+    }
+    cholqr2(ctx, Y, d_off, Kc, maxI, ell, LP, M2, rank1, s, "s1");
+  }
+
+  te(DPAR2_PH_QR);
+  // ---- projection B1 = Q1^T X (pass 2 over X) and ||X_k||^2 ----
+  int nJb_used = nJb;
+  bool projected = false;
+  if (use_tc) {
+    const int64_t Npad = hp[Kc];
+    launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, Kc, Npad, maxPad, dtype, Qs, s);
+    tb(DPAR2_PH_PROJECT);
+    if (pj.choice < 0) {
+      // autotune: time both schedules on this call's projection (identical
+      // results) and keep the faster for this problem shape
+      cudaEvent_t ev[3];
+      for (auto& e : ev) CK(cudaEventCreate(&e));
+      const ProjSched cand[2] = {proj_sched(ctx, 0, off, Kc, nJb_tc, tkey, s),
+                                 proj_sched(ctx, 1, off, Kc, nJb_tc, tkey, s)};
+      CK(cudaEventRecord(ev[0], s));
+      for (int c = 0; c < 2; ++c) {
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
+                                      true, ctx->num_sms, ctx->d_status, s, cand[c].lptr, cand[c].items,
+                                      cand[c].nlists);
+        CK(cudaEventRecord(ev[c + 1], s));
+      }
+      CK(cudaEventSynchronize(ev[2]));
+      float t0 = 0.f, t1 = 0.f;
+      CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));
+      CK(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+      for (auto& e : ev) cudaEventDestroy(e);
+      ctx->tuned[tkey] = t1 < t0 ? 1 : 0;
+    } else {
+      projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
+                                    true, ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
+    }
+    if (projected) {
+      xpart = xp;
+      nJb_used = nJb_tc * kProjNormWarps;
+    }
+  } else {
+    tb(DPAR2_PH_PROJECT);
+  }
+  if (projected) {
+  } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
+    for (int k = 0; k < Kc; ++k)
+      launch_project_generic(X, dtype, ldx, d_off + k, 1, J, Jp, Y, LP, B1 + (size_t)k * LP * Jp,
+                             xpart + (size_t)k * nJb, nullptr, s);
+  } else {
+    launch_project_generic(X, dtype, ldx, d_off, Kc, J, Jp, Y, LP, B1, xpart, nullptr, s);
+  }
+  te(DPAR2_PH_PROJECT);
+  tb(DPAR2_PH_SMALL);
+  launch_reduce_rows_f64(xpart, Kc, nJb_used, xn2, s);
+
+  // ---- small SVD of B = M2^T B1 -> C_k B_k blocks of M, T_k, A_k ----
+  double* GB = wsget<double>(ctx, "GB", (size_t)Kc * LP * LP);
+  float* T = wsget<float>(ctx, "T", (size_t)Kc * LP * R);
+  launch_gram_b1(B1, Jp, J, Kc, ell, LP, GB, s);
+  launch_eig_top(GB, M2, Kc, ell, LP, R, T, nullptr, ctx->d_status, s);
+  launch_mblock(B1, Jp, J, Kc, ell, LP, R, T, Bk, Mb,
+                rank1, 1e-5f, s);
+  launch_seg_product(Y, LP, LP, T, (int64_t)LP * R, R, Aout, R, d_off, Kc, maxI, s);
+
+  te(DPAR2_PH_SMALL);
+}
+
+// Stage 2 of the compression (Sec. III-B, the randomized SVD of
+// M = [C_1 B_1 ... C_K B_K], J x KR): D, E, F~_k = F^(k) E and D^T D of the
+// compression from its M blocks.
+void stage2_all(dpar2_ctx* ctx, dpar2_comp* comp, const dpar2_options* opt, const float* omega2, cudaStream_t s) {
+  const int K = comp->K, J = comp->J, R = comp->R, ell = comp->ell, LP = comp->LP;
+  // ---- stage 2: randomized SVD of M (J x KR) ----
+  tbegin(ctx, s, DPAR2_PH_STAGE2);
+  const int64_t KR = (int64_t)K * R;
+  const float* om2 = omega2;
+  if (!om2) {
+    float* g = wsget<float>(ctx, "omega2", (size_t)KR * ell);
+    launch_gaussian(opt->seed, 1, KR * ell, g, 1, s);
+    om2 = g;
+  }
+  float* om2p = wsget<float>(ctx, "om2_pad", (size_t)KR * LP);
+  launch_pad_omega(om2, (int)KR, ell, (int)KR, LP, DPAR2_F32, om2p, s);
+  const int kchunk = s2_sketch_chunk(K, J, ctx->num_sms);
+  const int nch = (K + kchunk - 1) / kchunk;
+  float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nch * J * LP);
+  float* Y2 = wsget<float>(ctx, "Y2", (size_t)J * LP);
+  launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, om2p, LP, Y2p, kchunk, s);
+  launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+  int64_t* off2 = wsget<int64_t>(ctx, "off2", 4);
+  const int64_t h_off2[4] = {0, (int64_t)J, 0, KR};
+  h2d_i64(ctx, off2, h_off2, sizeof(h_off2) / sizeof(int64_t), s);
+  float* M2s = wsget<float>(ctx, "M2s", (size_t)LP * LP);
+  cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
+  for (int it = 0; it < opt->q; ++it) {
+    // Y2 <- M (M^T Q2): reuse the stage-2 kernels with Omega2 := M^T Q2
+    DP2_COUNTED(k_apply_m2<<<dim3((unsigned)((J + 127) / 128), 1), 128, 0, s>>>(Y2, off2, LP, M2s));
+    float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
+    launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
+    launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, B2p, LP, Y2p, kchunk, s);
+    launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+    cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
+  }
+  float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
+  launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
+  double* G2 = wsget<double>(ctx, "G2", (size_t)LP * LP);
+  {
+    const int ns = gram_splits(1, KR);
+    double* Gp = wsget<double>(ctx, "G2p", (size_t)ns * LP * LP);
+    launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, true, s);
+  }
+  float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
+  launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
+  launch_seg_product(Y2, LP, LP, T2, 0, R, static_cast<float*>(comp->D.p), R, off2, 1, J, s);
+  launch_seg_product(B2p, LP, LP, T2, 0, R, static_cast<float*>(comp->Ft.p), R, off2 + 2, 1, KR, s);
+  {
+    double* epart = wsget<double>(ctx, "en_part", (size_t)kEnormBlocks * R);
+    float* ekeep = wsget<float>(ctx, "en_keep", (size_t)R);
+    int* endrop = wsget<int>(ctx, "en_ndrop", 1);
+    launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
+                    static_cast<float*>(comp->E.p), 1e-6f, epart, ekeep, endrop, s);
+  }
+  launch_atb(J, R, static_cast<const float*>(comp->D.p), static_cast<const float*>(comp->D.p),
+             static_cast<double*>(comp->DtD.p), wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * R * R), s);
+  tend(ctx, s, DPAR2_PH_STAGE2);
+}
+
+// Argument checks of dpar2_compress / dpar2_compress_host (host only, before
+// any launch).  device_x: X is device memory that must be 16-byte aligned.
+dpar2_status check_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X, int64_t ldx,
+                            dpar2_dtype dtype, const dpar2_options* opt, dpar2_comp** out, bool device_x) {
+  try {
+    require(out != nullptr, DPAR2_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    require(opt && X && row_offsets, DPAR2_ERR_INVALID_ARG, "opt, X and row_offsets must be non-null");
+    require(dtype == DPAR2_F32 || dtype == DPAR2_BF16 || dtype == DPAR2_F16, DPAR2_ERR_INVALID_ARG, "bad dtype");
+    require(K >= 1 && J >= 1, DPAR2_ERR_SHAPE, "K and J must be >= 1");
+    require(opt->R >= 1 && opt->R <= kMaxR && opt->R <= J, DPAR2_ERR_SHAPE, "need 1 <= R <= min(J, 64)");
+    require(opt->p >= 0 && opt->R + opt->p <= std::min(J, kMaxEll), DPAR2_ERR_SHAPE, "need R + p <= min(J, 64)");
+    require(opt->q >= 0 && opt->q <= 8, DPAR2_ERR_INVALID_ARG, "need 0 <= q <= 8");
+    require(ldx >= J, DPAR2_ERR_SHAPE, "ldx < J");
+    require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
+            "ldx * sizeof(dtype) must be a multiple of 16 bytes");
+    if (device_x)
+      require((reinterpret_cast<uintptr_t>(X) & 15) == 0, DPAR2_ERR_INVALID_ARG, "X must be 16-byte aligned");
+    require(row_offsets[0] == 0, DPAR2_ERR_SHAPE, "row_offsets[0] must be 0");
+    for (int k = 0; k < K; ++k)
+      require(row_offsets[k + 1] > row_offsets[k], DPAR2_ERR_SHAPE, "every slice needs I_k >= 1 rows");
+    return DPAR2_OK;
+  } catch (const Fail& f) {
+    ctx->err = f.msg;
+    return f.st;
+  }
+}
+
+// A new compression object for K slices (buffers from the context's pool),
+// its device offsets copied.
+dpar2_comp* new_comp(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const dpar2_options* opt,
+                     cudaStream_t s) {
+  const int R = opt->R, ell = opt->R + opt->p, LP = round_up(ell, 8);
+  const int64_t N = row_offsets[K];
+  int64_t maxI = 0;
+  for (int k = 0; k < K; ++k) maxI = std::max<int64_t>(maxI, row_offsets[k + 1] - row_offsets[k]);
+  dpar2_comp* comp = new dpar2_comp();
+  comp->owner = ctx;
+  ++ctx->live_comps;
+  comp->K = K;
+  comp->J = J;
+  comp->R = R;
+  comp->ell = ell;
+  comp->LP = LP;
+  comp->N = N;
+  comp->maxI = maxI;
+  comp->h_offsets.assign(row_offsets, row_offsets + K + 1);
+  alloc(comp, comp->offsets, (K + 1) * sizeof(int64_t));
+  alloc(comp, comp->A, (size_t)N * R * 4);
+  alloc(comp, comp->Bk, (size_t)K * R * 4);
+  alloc(comp, comp->M, (size_t)K * J * R * 4);
+  alloc(comp, comp->D, (size_t)J * R * 4);
+  alloc(comp, comp->E, (size_t)R * 4);
+  alloc(comp, comp->Ft, (size_t)K * R * R * 4);
+  alloc(comp, comp->xnorm2, (size_t)K * 8);
+  alloc(comp, comp->rank1, (size_t)K * 4);
+  alloc(comp, comp->DtD, (size_t)R * R * 8);
+  h2d_i64(ctx, static_cast<int64_t*>(comp->offsets.p), row_offsets, (K + 1), s);
+  return comp;
+}
+
+// The stage-1 test matrix (Alg. 1: the caller's, or the Gaussian stream
+// (seed, 0) rounded to bf16-representable values), padded to Jpad x LP and
+// rounded to X's 16-bit type.
+const float* prepare_omega(dpar2_ctx* ctx, int J, int ell, int LP, dpar2_dtype dtype, const dpar2_options* opt,
+                           const float* omega, cudaStream_t s) {
+  const int Jpad = round_up(J, 32);
+  const float* om = omega;
+  if (!om) {
+    float* g = wsget<float>(ctx, "omega", (size_t)J * ell);
+    launch_gaussian(opt->seed, 0, (int64_t)J * ell, g, 1, s);
+    om = g;
+  }
+  float* om_pad = wsget<float>(ctx, "om_pad", (size_t)Jpad * LP);
+  launch_pad_omega(om, J, ell, Jpad, LP, dtype, om_pad, s);
+  return om_pad;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ ctx / comp ----
@@ -382,6 +714,7 @@ void dpar2_destroy(dpar2_ctx* ctx) {
 }
 
 const char* dpar2_last_error(const dpar2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+long long dpar2_kernel_launches(void) { return g_launches.load(); }
 int dpar2_last_info(const dpar2_ctx* ctx) {
   return (ctx && ctx->h_status) ? (*ctx->h_status & (ST_RANK_DROP | ST_SWEEP_CAP | ST_PINV)) : 0;
 }
@@ -502,290 +835,119 @@ dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
                             dpar2_dtype dtype, const dpar2_options* opt, const float* omega, const float* omega2,
                             dpar2_comp** out, void* stream) {
   if (!ctx) return DPAR2_ERR_INVALID_ARG;
-  dpar2_comp* comp = nullptr;
-  auto chk = [&]() -> dpar2_status {
-    try {
-      require(out != nullptr, DPAR2_ERR_INVALID_ARG, "out is null");
-      *out = nullptr;
-      require(opt && X && row_offsets, DPAR2_ERR_INVALID_ARG, "opt, X and row_offsets must be non-null");
-      require(dtype == DPAR2_F32 || dtype == DPAR2_BF16 || dtype == DPAR2_F16, DPAR2_ERR_INVALID_ARG, "bad dtype");
-      require(K >= 1 && J >= 1, DPAR2_ERR_SHAPE, "K and J must be >= 1");
-      require(opt->R >= 1 && opt->R <= kMaxR && opt->R <= J, DPAR2_ERR_SHAPE, "need 1 <= R <= min(J, 64)");
-      require(opt->p >= 0 && opt->R + opt->p <= std::min(J, kMaxEll), DPAR2_ERR_SHAPE, "need R + p <= min(J, 64)");
-      require(opt->q >= 0 && opt->q <= 8, DPAR2_ERR_INVALID_ARG, "need 0 <= q <= 8");
-      require(ldx >= J, DPAR2_ERR_SHAPE, "ldx < J");
-      require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
-              "ldx * sizeof(dtype) must be a multiple of 16 bytes");
-      require((reinterpret_cast<uintptr_t>(X) & 15) == 0, DPAR2_ERR_INVALID_ARG, "X must be 16-byte aligned");
-      require(row_offsets[0] == 0, DPAR2_ERR_SHAPE, "row_offsets[0] must be 0");
-      for (int k = 0; k < K; ++k)
-        require(row_offsets[k + 1] > row_offsets[k], DPAR2_ERR_SHAPE, "every slice needs I_k >= 1 rows");
-      return DPAR2_OK;
-    } catch (const Fail& f) {
-      ctx->err = f.msg;
-      return f.st;
-    }
-  };
-  dpar2_status st0 = chk();
+  dpar2_status st0 = check_compress(ctx, K, J, row_offsets, X, ldx, dtype, opt, out, true);
   if (st0 != DPAR2_OK) return st0;
-
+  dpar2_comp* comp = nullptr;
   dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
-    const int R = opt->R, ell = opt->R + opt->p, LP = round_up(ell, 8);
-    const int Jp = round_up(J, 4), Jpad = round_up(J, 32);
-    const int64_t N = row_offsets[K];
-    int64_t maxI = 0;
-    for (int k = 0; k < K; ++k) maxI = std::max<int64_t>(maxI, row_offsets[k + 1] - row_offsets[k]);
-    comp = new dpar2_comp();
-    comp->owner = ctx;
-    ++ctx->live_comps;
-    comp->K = K;
-    comp->J = J;
-    comp->R = R;
-    comp->ell = ell;
-    comp->LP = LP;
-    comp->N = N;
-    comp->maxI = maxI;
-    comp->h_offsets.assign(row_offsets, row_offsets + K + 1);
-    alloc(comp, comp->offsets, (K + 1) * sizeof(int64_t));
-    alloc(comp, comp->A, (size_t)N * R * 4);
-    alloc(comp, comp->Bk, (size_t)K * R * 4);
-    alloc(comp, comp->M, (size_t)K * J * R * 4);
-    alloc(comp, comp->D, (size_t)J * R * 4);
-    alloc(comp, comp->E, (size_t)R * 4);
-    alloc(comp, comp->Ft, (size_t)K * R * R * 4);
-    alloc(comp, comp->xnorm2, (size_t)K * 8);
-    alloc(comp, comp->rank1, (size_t)K * 4);
-    alloc(comp, comp->DtD, (size_t)R * R * 8);
-    int64_t* d_off = static_cast<int64_t*>(comp->offsets.p);
-    h2d_i64(ctx, d_off, row_offsets, (K + 1), s);
-    const size_t es = dtype_size(dtype);
-
-    // ---- test matrix Omega (Alg. 1, "generate a Gaussian test matrix") ----
-    const float* om = omega;
-    if (!om) {
-      float* g = wsget<float>(ctx, "omega", (size_t)J * ell);
-      launch_gaussian(opt->seed, 0, (int64_t)J * ell, g, 1, s);
-      om = g;
-    }
+    comp = new_comp(ctx, K, J, row_offsets, opt, s);
     tbegin(ctx, s, DPAR2_PH_COMPRESS);
-    float* om_pad = wsget<float>(ctx, "om_pad", (size_t)Jpad * LP);
-    launch_pad_omega(om, J, ell, Jpad, LP, dtype, om_pad, s);
-
-    // ---- sketch Y = X Omega (pass 1 over X) ----
-    float* Y = wsget<float>(ctx, "Y", (size_t)N * LP);
-    float* M2 = wsget<float>(ctx, "M2", (size_t)K * LP * LP);
-    float* B1 = wsget<float>(ctx, "B1", (size_t)K * LP * Jp);
-    const int nJb = project_blocks(Jp, LP);
-    double* xpart = wsget<double>(ctx, "xpart", (size_t)K * nJb);
-    // tensor-core path: 16-bit X, all slices in one persistent launch
-    const bool use_tc = dtype != DPAR2_F32 && !(opt->flags & (DPAR2_FLAG_GENERIC | DPAR2_FLAG_PER_SLICE)) &&
-                        tc_available();
-    const int LPN = tc_lpn(ell);
-    void* omT16 = nullptr;
-    if (use_tc) {
-      omT16 = wsget<uint16_t>(ctx, "omT16", (size_t)LPN * Jpad);
-      launch_omega_t16(om_pad, Jpad, LP, LPN, dtype, omT16, s);
-    }
-    tbegin(ctx, s, DPAR2_PH_SKETCH);
-    bool sketched = false;
-    if (use_tc)
-      sketched = launch_sketch_tc(X, dtype, ldx, N, J, omT16, Jpad, LPN, LP, Y, ctx->num_sms, ctx->d_status, s);
-    if (sketched) {
-    } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
-      for (int k = 0; k < K; ++k) {
-        const int64_t r0 = row_offsets[k], nk = row_offsets[k + 1] - r0;
-        launch_sketch_generic(static_cast<const char*>(X) + r0 * ldx * es, dtype, ldx, nk, J, om_pad, LP,
-                              Y + r0 * LP, s);
-      }
-    } else {
-      launch_sketch_generic(X, dtype, ldx, N, J, om_pad, LP, Y, s);
-    }
-    tend(ctx, s, DPAR2_PH_SKETCH);
-    tbegin(ctx, s, DPAR2_PH_QR);
-    cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
-    // tensor-core projection operands: Q1 split into three exact-sum 16-bit
-    // parts, slices padded to 64 rows; one partial ||X_k||^2 per (slice,
-    // column block, norm warp)
-    std::vector<int64_t> hp, htoff;
-    int64_t maxPad = 0;
-    ProjSched pj;  // the projection's slice-to-CTA schedule (choice -1: tune on this call)
-    const std::string tkey = tune_key(K, J, ell, dtype, N, maxI);
-    int64_t* d_poff = nullptr;
-    void* Qs = nullptr;
-    double* xp = nullptr;
-    int PNS = 0, POFF = 0;  // layout of the projection's Q operand
-    proj_layout(ell, &PNS, &POFF);
-    const int nJb_tc = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
-    if (use_tc) {
-      hp.assign(K + 1, 0);
-      for (int k = 0; k < K; ++k) {
-        const int64_t pk = round_up64(row_offsets[k + 1] - row_offsets[k], 64);
-        hp[k + 1] = hp[k] + pk;
-        maxPad = std::max(maxPad, pk);
-      }
-      d_poff = wsget<int64_t>(ctx, "poff", (size_t)K + 1);
-      h2d_i64(ctx, d_poff, hp.data(), (K + 1), s);
-      Qs = wsget<uint16_t>(ctx, "Qs", (size_t)PNS * hp[K]);
-      xp = wsget<double>(ctx, "xpart_tc", (size_t)K * nJb_tc * kProjNormWarps);
-      int choice = opt->schedule;
-      if (choice < 0) {
-        auto it = ctx->tuned.find(tkey);
-        if (it != ctx->tuned.end()) choice = it->second;
-      }
-      pj = proj_sched(ctx, choice > 1 ? 0 : choice, row_offsets, K, nJb_tc, tkey, s);
-      if (choice < 0) pj.choice = -1;
-    }
-    // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
-    int64_t* d_toff = nullptr;
-    if (use_tc && opt->q > 0) {
-      htoff.assign(K + 1, 0);
-      for (int k = 0; k < K; ++k) htoff[k + 1] = htoff[k] + (row_offsets[k + 1] - row_offsets[k] + 127) / 128;
-      d_toff = wsget<int64_t>(ctx, "toff", (size_t)K + 1);
-      h2d_i64(ctx, d_toff, htoff.data(), (K + 1), s);
-    }
-    for (int it = 0; it < opt->q; ++it) {
-      if (use_tc) {
-        // B1 = Q1^T X, then Y_k = X_k B1_k^T on the tensor cores: X_k X_k^T Q_k =
-        // X_k B1_k^T M2_k up to the upper-triangular M2_k (and the power-of-two
-        // row scales of the operand), which leave the next CholeskyQR2's Q unchanged
-        launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, K, hp[K], maxPad, dtype, Qs, s);
-        bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, hp[K], PNS, POFF, LP, B1, xp, nJb_tc, true,
-                                    ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
-        require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
-        void* Ms = wsget<uint16_t>(ctx, "Ms", (size_t)K * 3 * LPN * Jpad);
-        launch_sl_rowsplit(B1, K, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr,
-                           wsget<float>(ctx, "Ms_scale", (size_t)K * LP), s);
-        ok = launch_sketch_seg_tc(X, dtype, ldx, N, J, d_off, d_toff, htoff[K], K, Ms, Jpad, LPN, LP, Y,
-                                  ctx->num_sms, ctx->d_status, s);
-        require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
-      } else {
-        k_apply_m2<<<dim3((unsigned)((maxI + 127) / 128), K), 128, 0, s>>>(Y, d_off, LP, M2);
-        launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, nullptr, nullptr, s);
-        float* omk = wsget<float>(ctx, "omk", (size_t)K * Jpad * LP);
-        k_b1_to_omk<<<4096, 256, 0, s>>>(B1, K, ell, LP, J, Jp, Jpad, omk);
-        launch_sketch_generic_per_slice(X, dtype, ldx, d_off, K, (int)maxI, J, omk, Jpad, LP, Y, s);
-      }
-      cholqr2(ctx, Y, d_off, K, maxI, ell, LP, M2, static_cast<int*>(comp->rank1.p), s, "s1");
-    }
-
-    tend(ctx, s, DPAR2_PH_QR);
-    // ---- projection B1 = Q1^T X (pass 2 over X) and ||X_k||^2 ----
-    int nJb_used = nJb;
-    bool projected = false;
-    if (use_tc) {
-      const int64_t Npad = hp[K];
-      launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, K, Npad, maxPad, dtype, Qs, s);
-      tbegin(ctx, s, DPAR2_PH_PROJECT);
-      if (pj.choice < 0) {
-        // autotune: time both schedules on this call's projection (identical
-        // results) and keep the faster for this problem shape
-        cudaEvent_t ev[3];
-        for (auto& e : ev) CK(cudaEventCreate(&e));
-        const ProjSched cand[2] = {proj_sched(ctx, 0, row_offsets, K, nJb_tc, tkey, s),
-                                   proj_sched(ctx, 1, row_offsets, K, nJb_tc, tkey, s)};
-        CK(cudaEventRecord(ev[0], s));
-        for (int c = 0; c < 2; ++c) {
-          projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
-                                        true, ctx->num_sms, ctx->d_status, s, cand[c].lptr, cand[c].items,
-                                        cand[c].nlists);
-          CK(cudaEventRecord(ev[c + 1], s));
-        }
-        CK(cudaEventSynchronize(ev[2]));
-        float t0 = 0.f, t1 = 0.f;
-        CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));
-        CK(cudaEventElapsedTime(&t1, ev[1], ev[2]));
-        for (auto& e : ev) cudaEventDestroy(e);
-        ctx->tuned[tkey] = t1 < t0 ? 1 : 0;
-      } else {
-        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, K, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
-                                      true, ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
-      }
-      if (projected) {
-        xpart = xp;
-        nJb_used = nJb_tc * kProjNormWarps;
-      }
-    } else {
-      tbegin(ctx, s, DPAR2_PH_PROJECT);
-    }
-    if (projected) {
-    } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
-      for (int k = 0; k < K; ++k)
-        launch_project_generic(X, dtype, ldx, d_off + k, 1, J, Jp, Y, LP, B1 + (size_t)k * LP * Jp,
-                               xpart + (size_t)k * nJb, nullptr, s);
-    } else {
-      launch_project_generic(X, dtype, ldx, d_off, K, J, Jp, Y, LP, B1, xpart, nullptr, s);
-    }
-    tend(ctx, s, DPAR2_PH_PROJECT);
-    tbegin(ctx, s, DPAR2_PH_SMALL);
-    launch_reduce_rows_f64(xpart, K, nJb_used, static_cast<double*>(comp->xnorm2.p), s);
-
-    // ---- small SVD of B = M2^T B1 -> C_k B_k blocks of M, T_k, A_k ----
-    double* GB = wsget<double>(ctx, "GB", (size_t)K * LP * LP);
-    float* T = wsget<float>(ctx, "T", (size_t)K * LP * R);
-    launch_gram_b1(B1, Jp, J, K, ell, LP, GB, s);
-    launch_eig_top(GB, M2, K, ell, LP, R, T, nullptr, ctx->d_status, s);
-    launch_mblock(B1, Jp, J, K, ell, LP, R, T, static_cast<float*>(comp->Bk.p), static_cast<float*>(comp->M.p),
-                  static_cast<int*>(comp->rank1.p), 1e-5f, s);
-    launch_seg_product(Y, LP, LP, T, (int64_t)LP * R, R, static_cast<float*>(comp->A.p), R, d_off, K, maxI, s);
-
-    tend(ctx, s, DPAR2_PH_SMALL);
+    const float* om_pad = prepare_omega(ctx, J, comp->ell, comp->LP, dtype, opt, omega, s);
+    // ---- stage 1 over all slices ----
+    stage1_range(ctx, comp, X, ldx, dtype, opt, 0, K, row_offsets, static_cast<const int64_t*>(comp->offsets.p),
+                 om_pad, true, s);
     // ---- stage 2: randomized SVD of M (J x KR) ----
-    tbegin(ctx, s, DPAR2_PH_STAGE2);
-    const int64_t KR = (int64_t)K * R;
-    const float* om2 = omega2;
-    if (!om2) {
-      float* g = wsget<float>(ctx, "omega2", (size_t)KR * ell);
-      launch_gaussian(opt->seed, 1, KR * ell, g, 1, s);
-      om2 = g;
-    }
-    float* om2p = wsget<float>(ctx, "om2_pad", (size_t)KR * LP);
-    launch_pad_omega(om2, (int)KR, ell, (int)KR, LP, DPAR2_F32, om2p, s);
-    const int kchunk = s2_sketch_chunk(K, J, ctx->num_sms);
-    const int nch = (K + kchunk - 1) / kchunk;
-    float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nch * J * LP);
-    float* Y2 = wsget<float>(ctx, "Y2", (size_t)J * LP);
-    launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, om2p, LP, Y2p, kchunk, s);
-    launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
-    int64_t* off2 = wsget<int64_t>(ctx, "off2", 4);
-    const int64_t h_off2[4] = {0, (int64_t)J, 0, KR};
-    h2d_i64(ctx, off2, h_off2, sizeof(h_off2) / sizeof(int64_t), s);
-    float* M2s = wsget<float>(ctx, "M2s", (size_t)LP * LP);
-    cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
-    for (int it = 0; it < opt->q; ++it) {
-      // Y2 <- M (M^T Q2): reuse the stage-2 kernels with Omega2 := M^T Q2
-      k_apply_m2<<<dim3((unsigned)((J + 127) / 128), 1), 128, 0, s>>>(Y2, off2, LP, M2s);
-      float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
-      launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
-      launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, B2p, LP, Y2p, kchunk, s);
-      launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
-      cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
-    }
-    float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
-    launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
-    double* G2 = wsget<double>(ctx, "G2", (size_t)LP * LP);
-    {
-      const int ns = gram_splits(1, KR);
-      double* Gp = wsget<double>(ctx, "G2p", (size_t)ns * LP * LP);
-      launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, true, s);
-    }
-    float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
-    launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
-    launch_seg_product(Y2, LP, LP, T2, 0, R, static_cast<float*>(comp->D.p), R, off2, 1, J, s);
-    launch_seg_product(B2p, LP, LP, T2, 0, R, static_cast<float*>(comp->Ft.p), R, off2 + 2, 1, KR, s);
-    {
-      double* epart = wsget<double>(ctx, "en_part", (size_t)kEnormBlocks * R);
-      float* ekeep = wsget<float>(ctx, "en_keep", (size_t)R);
-      int* endrop = wsget<int>(ctx, "en_ndrop", 1);
-      launch_s2_enorm(static_cast<float*>(comp->Ft.p), KR, R, static_cast<float*>(comp->D.p), J,
-                      static_cast<float*>(comp->E.p), 1e-6f, epart, ekeep, endrop, s);
-    }
-    launch_atb(J, R, static_cast<const float*>(comp->D.p), static_cast<const float*>(comp->D.p),
-               static_cast<double*>(comp->DtD.p), wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * R * R), s);
-    tend(ctx, s, DPAR2_PH_STAGE2);
+    stage2_all(ctx, comp, opt, omega2, s);
     tend(ctx, s, DPAR2_PH_COMPRESS);
     if (opt->flags & DPAR2_FLAG_DROP_M) {
       alloc(comp, comp->M, 0);  // stream-ordered after the kernels that read it
     }
+  });
+  if (st != DPAR2_OK) {
+    if (comp) dpar2_comp_free(comp);
+    return st;
+  }
+  *out = comp;
+  return DPAR2_OK;
+}
+
+// ------------------------------------------------- compress from host memory ----
+// Chunks of whole slices are copied host -> device on a copy stream, each
+// into its own staging buffer (two in turn); the work stream re-pitches a
+// chunk into its device rows and runs stage 1 on it while the next chunk
+// copies, so X crosses the host link once and the transfers hide the stage-1
+// work.  Stage 2 and everything after it need only the compressed factors.
+dpar2_status dpar2_compress_host(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, const void* X_host,
+                                 dpar2_dtype dtype, const dpar2_options* opt, const float* omega,
+                                 const float* omega2, void* X_dev, int64_t ldx, size_t chunk_bytes,
+                                 dpar2_comp** out, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  const size_t es = (dtype == DPAR2_F32) ? 4 : 2;
+  // device row pitch: the caller's, or rows padded to 32 bytes in the chunk buffers
+  const int64_t ldd = X_dev ? ldx : (int64_t)((J * es + 31) / 32 * 32 / es);
+  dpar2_status st0 = check_compress(ctx, K, J, row_offsets, X_dev ? X_dev : X_host, ldd, dtype, opt, out, X_dev != nullptr);
+  if (st0 != DPAR2_OK) return st0;
+  if (!X_host) {
+    ctx->err = "X_host must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  dpar2_comp* comp = nullptr;
+  dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
+    comp = new_comp(ctx, K, J, row_offsets, opt, s);
+    tbegin(ctx, s, DPAR2_PH_COMPRESS);
+    const float* om_pad = prepare_omega(ctx, J, comp->ell, comp->LP, dtype, opt, omega, s);
+    // chunks of whole slices, about chunk_bytes of X each
+    const size_t rowb = (size_t)J * es;
+    const size_t target = chunk_bytes ? chunk_bytes : ((size_t)512 << 20);
+    std::vector<int> cut{0};
+    for (int k = 0; k < K; ++k) {
+      const int64_t rows = row_offsets[k + 1] - row_offsets[cut.back()];
+      if (k + 1 < K && (size_t)rows * rowb >= target) cut.push_back(k + 1);
+    }
+    cut.push_back(K);
+    const int nc = (int)cut.size() - 1;
+    int64_t maxrows = 0;
+    for (int c = 0; c < nc; ++c) maxrows = std::max(maxrows, row_offsets[cut[c + 1]] - row_offsets[cut[c]]);
+    constexpr int NB = 2;
+    const bool direct = ldd == J;  // host rows already have the device pitch: no staging
+    uint8_t* stage = direct ? nullptr : wsget<uint8_t>(ctx, "hc_stage", (size_t)NB * maxrows * rowb);
+    uint8_t* cbuf = X_dev ? nullptr : wsget<uint8_t>(ctx, "hc_chunk", (size_t)NB * maxrows * ldd * es);
+    int64_t* d_coff = wsget<int64_t>(ctx, "hc_off", (size_t)NB * (K + 1));
+    auto& cse = ctx->ws["__copy_stream0"];
+    if (!cse.p) {
+      cudaStream_t x;
+      CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      cse.p = reinterpret_cast<void*>(x);
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cse.p);
+    cudaEvent_t ev[2 * NB + 1];  // copied[b], free[b], start
+    for (int i = 0; i < 2 * NB + 1; ++i) {
+      auto& e = ctx->ws[std::string("__copy_ev") + char('a' + i)];
+      if (!e.p) {
+        cudaEvent_t x;
+        CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        e.p = reinterpret_cast<void*>(x);
+      }
+      ev[i] = reinterpret_cast<cudaEvent_t>(e.p);
+    }
+    CK(cudaEventRecord(ev[2 * NB], s));  // copies start after the work stream's prior work
+    CK(cudaStreamWaitEvent(cs, ev[2 * NB], 0));
+    std::vector<int64_t> loc;
+    for (int c = 0; c < nc; ++c) {
+      const int b = c % NB, k0 = cut[c], Kc = cut[c + 1] - cut[c];
+      const int64_t r0 = row_offsets[k0], nr = row_offsets[cut[c + 1]] - r0;
+      uint8_t* dst = X_dev ? static_cast<uint8_t*>(X_dev) + (size_t)r0 * ldd * es : cbuf + (size_t)b * maxrows * ldd * es;
+      uint8_t* land = direct ? dst : stage + (size_t)b * maxrows * rowb;
+      // the landing buffer is free once the work stream re-pitched (staging) or
+      // compressed (direct into a chunk buffer) chunk c - NB
+      if (c >= NB) CK(cudaStreamWaitEvent(cs, ev[NB + b], 0));
+      CK(cudaMemcpyAsync(land, static_cast<const uint8_t*>(X_host) + (size_t)r0 * rowb, (size_t)nr * rowb,
+                         cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(ev[b], cs));
+      CK(cudaStreamWaitEvent(s, ev[b], 0));
+      if (!direct) {
+        launch_repitch(land, nr, J, (int)es, dst, ldd, s);
+        CK(cudaEventRecord(ev[NB + b], s));
+      }
+      loc.assign(Kc + 1, 0);
+      for (int k = 0; k <= Kc; ++k) loc[k] = row_offsets[k0 + k] - r0;
+      int64_t* d_loc = d_coff + (size_t)b * (K + 1);
+      h2d_i64(ctx, d_loc, loc.data(), Kc + 1, s);
+      stage1_range(ctx, comp, dst, ldd, dtype, opt, k0, Kc, loc.data(), d_loc, om_pad, false, s);
+      if (direct) CK(cudaEventRecord(ev[NB + b], s));
+    }
+    stage2_all(ctx, comp, opt, omega2, s);
+    tend(ctx, s, DPAR2_PH_COMPRESS);
+    if (opt->flags & DPAR2_FLAG_DROP_M) alloc(comp, comp->M, 0);
   });
   if (st != DPAR2_OK) {
     if (comp) dpar2_comp_free(comp);
@@ -860,12 +1022,16 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
       if (graph) {
         cudaGraph_t g;
         cudaGraphExec_t ge;
+        const long long c0 = g_launches.load();
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
         launch_als_finish(b, opt->max_iter - 1, s);
         CK(cudaStreamEndCapture(s, &g));
+        const long long captured = g_launches.load() - c0;
+        g_launches.fetch_sub(captured);
         CK(cudaGraphInstantiate(&ge, g, 0));
         CK(cudaGraphLaunch(ge, s));
+        g_launches.fetch_add(captured);
         cudaGraphExecDestroy(ge);  // freed when the launch completes
         cudaGraphDestroy(g);
       } else {
@@ -906,7 +1072,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
       launch_p_from_cv(K, R, b.CV, b.Ft, P, s);
       launch_fitness(K, R, P, b.Upol, H, W, b.VtV, static_cast<const double*>(comp->xnorm2.p), fpart, b.nblk,
                      fpart + b.nblk, s);
-      k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + b.nblk + 1);
+      DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + b.nblk + 1));
       tend(ctx, s, DPAR2_PH_OUTPUT);
       double h[2];
       CK(cudaMemcpyAsync(h, fpart + b.nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -986,7 +1152,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
       launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
                      s);
-      k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+      DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1));
     } else {
       // streamed mode: one pass over X projects it onto A_k (A_k^T X_k and
       // ||X_k||^2 measured, not taken from the compression) and A_k^T A_k is
@@ -1032,7 +1198,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       }
       launch_p_stream(K, J, Jp, R, LP, V, Bs, P, s);
       launch_fitness(K, R, P, up, H, W, VtV, xn, fpart, nblk, fpart + nblk, s, G, LP);
-      k_sum_f64<<<1, 256, 0, s>>>(xn, K, fpart + nblk + 1);
+      DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(xn, K, fpart + nblk + 1));
     }
     CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   });
@@ -1054,20 +1220,15 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DPAR2_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-std::mutex g_noalloc_mu;
-constexpr int kNoAllocDevices = 64;
-void* g_noalloc_base[kNoAllocDevices] = {};
-
-// Device address of the array on the current device (looked up once per device).
-void* noalloc_base(int dev) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  require(dev >= 0 && dev < kNoAllocDevices, DPAR2_ERR_INVALID_ARG, "device ordinal out of range");
-  if (!g_noalloc_base[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_base[dev] = p;
-  }
-  return g_noalloc_base[dev];
+// Device address of the array in the current device's context.  Looked up on
+// every call (cudaGetSymbolAddress allocates nothing) rather than cached, so a
+// context that was reset and re-created since the last call gets the address
+// of its own copy of the array.
+void* noalloc_base() {
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  require(p != nullptr, DPAR2_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
+  return p;
 }
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
@@ -1101,7 +1262,7 @@ dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpar2_comp* c
   }
   double res[2] = {0, 0};
   dpar2_status st = guarded(ctx, stream, [&](cudaStream_t s) {
-    unsigned char* base = static_cast<unsigned char*>(noalloc_base(ctx->device));
+    unsigned char* base = static_cast<unsigned char*>(noalloc_base());
     float* P = reinterpret_cast<float*>(base);
     double* Psi = reinterpret_cast<double*>(base + bP);
     double* VtV = Psi + RR;
@@ -1111,7 +1272,7 @@ dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpar2_comp* c
     launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
     launch_fitness(K, R, P, Upol, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
                    s);
-    k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1);
+    DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1));
     CK(cudaMemcpyAsync(res, fpart + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   });
   if (st == DPAR2_OK) {
@@ -1365,7 +1526,7 @@ dpar2_status dpar2_orthonormalize(dpar2_ctx* ctx, int64_t rows, int cols, float*
     h2d_i64(ctx, d_off, hoff, sizeof(hoff) / sizeof(int64_t), s);
     float* M2 = wsget<float>(ctx, "on_M2", (size_t)LP * LP);
     cholqr2(ctx, Y, d_off, 1, rows, cols, LP, M2, wsget<int>(ctx, "on_rank", 1), s, "on");
-    k_apply_m2<<<dim3((unsigned)((rows + 127) / 128), 1), 128, 0, s>>>(Y, d_off, LP, M2);
+    DP2_COUNTED(k_apply_m2<<<dim3((unsigned)((rows + 127) / 128), 1), 128, 0, s>>>(Y, d_off, LP, M2));
     CK(cudaMemcpy2DAsync(A, cols * sizeof(float), Y, LP * sizeof(float), cols * sizeof(float), rows,
                          cudaMemcpyDeviceToDevice, s));
   });

@@ -41,6 +41,11 @@ __device__ inline float warp_max(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ inline double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // Error-free product a*b = p + e (FMA-based TwoProduct, Ogita-Rump-Oishi 2005)
 // accumulated into a double-float (hi, lo) pair with Knuth's TwoSum.
@@ -243,6 +248,13 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n
 }  // namespace dp2
 
 // Dispatch a runtime sketch width LP (multiple of 8, <= 64) to a template constant L.
+// Every kernel launch of the library goes through DP2_COUNTED, which adds one
+// to the process-wide launch count (dpar2_kernel_launches) after enqueuing it.
+namespace dp2 {
+void note_launch();
+}
+#define DP2_COUNTED(...) ((__VA_ARGS__), ::dp2::note_launch())
+
 #define DP2_LP_SWITCH(LP, CALL)               \
   switch (LP) {                               \
     case 8: { constexpr int L = 8; CALL; } break;   \

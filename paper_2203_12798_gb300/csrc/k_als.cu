@@ -12,10 +12,14 @@
 //     R x R products (D^T D from stage 2).
 //   Lemma 3: G3(k, r) = H(:, r)^T Pi_k Psi(:, r);  W = G3 (V^T V * H^T H)^+.
 //   Convergence value (Sec. III-E): e = sum_k ||Pi_k D^T - H S_k V^T||^2
-//     = sum_k ||Pi_k||^2 - 2 sum_r W(k,r) G3(k,r) + W_k (H^T H * V^T V) W_k^T.
+//     = sum_k ||Pi_k - H S_k CV^T||^2 (D^T D = I), summed from the residual
+//     entries themselves.
 // Grid-wide sums are block partials reduced in a fixed order (deterministic).
-// The R x R Gram-Hadamard solves are FP64 (Cholesky; pseudoinverse from an
-// FP64 Jacobi eigendecomposition if a pivot fails).
+// The R x R Gram-Hadamard solves are FP64: Cholesky factorisations (with the
+// pseudoinverse from an FP64 Jacobi eigendecomposition if a pivot fails) for
+// the H and V updates; for the W update an FP32 factorisation refined to FP64
+// accuracy by Newton steps (FP64 Cholesky when the refinement's start is too
+// far off), applied to the FP32 right-hand sides G3 in FP64.
 #include "common.cuh"
 #include "internal.h"
 #include "small_solve.cuh"
@@ -305,7 +309,15 @@ __global__ void k_qstep(int K, int R, const float* __restrict__ Ft, const double
 }
 
 // --------------------------------------------------------- Lemma 2 partial --
-// part[blk] (R x R): g(m, r) += W(k, r) sum_i Pi_k(i, m) H(i, r).
+// part[blk] (R x R): g(m, r) += W(k, r) sum_i Pi_k(i, m) H(i, r), as
+// double-float sums: exact products (TwoProduct) added with TwoSum, the hi
+// floats in entries [0, R^2) of the partial and the lo floats in [R^2, 2 R^2).
+// The V update solves with (W^T W * H^T H), whose condition number reaches
+// 1e8 and more when H's columns become nearly parallel (the spectrogram
+// workload: 4e8); there a relative error of 2e-7 in g that no perturbation
+// of the Pi_k explains already derails the iteration, while FP32 dot products
+// of length R carry several 1e-7.  With double-float sums the right-hand side
+// is exact for the FP32 Pi_k, H and W it is formed from.
 // With pre_on the grid's last block runs pre_solve (the V update's factor).
 __global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __restrict__ W,
                      const float* __restrict__ H, float* __restrict__ part, int pstride, PreSolve pre, int pre_on) {
@@ -318,63 +330,81 @@ __global__ void k_g2(int K, int R, const float* __restrict__ Pi, const float* __
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* hs = sm;
-  float* slots = hs + RR;
-  float* pks = slots + nw * RR + warp * RR;
+  float* slots = hs + RR;                              // nw x 2 RR: hi then lo
+  float* pks = slots + 2 * nw * RR + warp * RR;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) hs[e] = H[e];
-  for (int e = threadIdx.x; e < nw * RR; e += blockDim.x) slots[e] = 0.f;
+  for (int e = threadIdx.x; e < 2 * nw * RR; e += blockDim.x) slots[e] = 0.f;
   __syncthreads();
-  float* slot = slots + warp * RR;
+  float* slot = slots + warp * 2 * RR;
   for (int k = blockIdx.x * nw + warp; k < K; k += nb * nw) {
     for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
     __syncwarp();
     const float* wk = W + (int64_t)k * R;
     for (int e = lane; e < RR; e += 32) {
       const int m = e / R, r = e % R;
-      float s = 0.f;
-      for (int i = 0; i < R; ++i) s = fmaf(pks[i * R + m], hs[i * R + r], s);
-      slot[e] += wk[r] * s;
+      DF d = {0.f, 0.f};
+      for (int i = 0; i < R; ++i) df_mac(d, pks[i * R + m], hs[i * R + r]);
+      // (d.hi + d.lo) * w as a double-float, added to the slot
+      const float w = wk[r];
+      const float p = d.hi * w;
+      DF t;
+      t.hi = p;
+      t.lo = fmaf(d.hi, w, -p) + d.lo * w;
+      const DF acc = df_add(DF{slot[e], slot[RR + e]}, t);
+      slot[e] = acc.hi;
+      slot[RR + e] = acc.lo;
     }
     __syncwarp();
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += slots[w * RR + e];
-    part[(int64_t)blockIdx.x * pstride + e] = s;
+    DF a = {0.f, 0.f};
+    for (int w = 0; w < nw; ++w) a = df_add(a, DF{slots[w * 2 * RR + e], slots[w * 2 * RR + RR + e]});
+    part[(int64_t)blockIdx.x * pstride + e] = a.hi;
+    part[(int64_t)blockIdx.x * pstride + RR + e] = a.lo;
   }
 }
 
 // --------------------------------------------------- Lemma 3 and W update --
-// W_k = G3_k Ginv with G3(k, r) = H(:, r)^T Pi_k Psi(:, r); also the block
-// partials of W^T W (R x R) and of the convergence value e (entries RR and
-// RR + 1: the hi and lo floats of a double-float sum).
+// W_k = G3_k Ginv with G3(k, r) = H(:, r)^T Pi_k Psi(:, r) (G3 in FP32, the
+// product with the FP64 inverse in FP64); also the block partials of W^T W
+// and of the convergence value e, both double-float sums: W^T W's hi floats
+// in entries [0, R^2), its lo floats in [R^2, 2 R^2), e's in 2 R^2 and
+// 2 R^2 + 1.  W^T W is summed from exact products of the stored FP32 W (the
+// H and V updates solve with W^T W * V^T V and W^T W * H^T H, whose
+// condition numbers reach 1e6..1e8 on nearly collinear factors: a Gram
+// matrix that disagrees with the stored W by FP32 rounding already makes
+// those systems indefinite).  e is summed as the residual itself:
+// Y_k - H S_k V^T = (Pi_k - H S_k CV^T) D^T with V = D CV, and D^T D = I to
+// FP32 rounding, so e_k = ||Pi_k - H S_k CV^T||_F^2 (an R x R residual whose
+// entries are formed before squaring; the expanded form ||Pi_k||^2 -
+// 2 tr(...) + ... subtracts terms thousands of times larger than e when the
+// model explains most of the compressed slices).
 __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* __restrict__ Psi,
-                      const float* __restrict__ H, const double* __restrict__ Ginv, const double* __restrict__ HtH,
-                      const double* __restrict__ VtV, float* __restrict__ W, float* __restrict__ part,
-                      int pstride) {
-  extern __shared__ __align__(16) float sm[];
+                      const float* __restrict__ H, const double* __restrict__ Ginv, const float* __restrict__ CV,
+                      float* __restrict__ W, float* __restrict__ part, int pstride) {
+  extern __shared__ __align__(16) double smd[];
   __shared__ float ered[32][2];
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* ps = sm;
+  double* gi = smd;  // Ginv
+  float* ps = reinterpret_cast<float*>(gi + RR);
   float* hs = ps + RR;
-  float* gi = hs + RR;
-  float* hv = gi + RR;              // HtH * VtV
-  float* slots = hv + RR;           // nw x (RR + 1)
-  float* pks = slots + nw * (RR + 1) + warp * (RR + 2 * R);
+  float* cvs = hs + RR;
+  float* slots = cvs + RR;          // nw x 2 RR (hi, lo)
+  float* pks = slots + nw * 2 * RR + warp * (RR + 2 * R);
   float* g3 = pks + RR;
   float* wn = g3 + R;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     ps[e] = (float)Psi[e];
     hs[e] = H[e];
-    gi[e] = (float)Ginv[e];
-    hv[e] = (float)(HtH[e] * VtV[e]);
+    gi[e] = Ginv[e];
+    cvs[e] = CV[e];
   }
-  for (int e = threadIdx.x; e < nw * (RR + 1); e += blockDim.x) slots[e] = 0.f;
+  for (int e = threadIdx.x; e < nw * 2 * RR; e += blockDim.x) slots[e] = 0.f;
   __syncthreads();
-  float* slot = slots + warp * (RR + 1);
-  // e_k = ||Pi_k||^2 - 2 w . g3 + w (HtH*VtV) w, accumulated per lane as a
-  // double-float sum of exact products
+  float* slot = slots + warp * 2 * RR;
+  // e_k accumulated per lane as a double-float sum of exact squares
   DF ek;
   ek.hi = 0.f;
   ek.lo = 0.f;
@@ -392,19 +422,23 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
     }
     __syncwarp();
     for (int r = lane; r < R; r += 32) {
-      float s = 0.f;
-      for (int m = 0; m < R; ++m) s = fmaf(g3[m], gi[m * R + r], s);
-      wn[r] = s;
-      W[(int64_t)k * R + r] = s;
+      double s = 0.0;
+      for (int m = 0; m < R; ++m) s = fma((double)g3[m], gi[m * R + r], s);
+      wn[r] = (float)s;
+      W[(int64_t)k * R + r] = (float)s;
     }
     __syncwarp();
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e - a * R;
-      df_mac(ek, pks[e], pks[e]);
-      df_mac(ek, wn[a] * wn[b], hv[e]);
-      slot[e] += wn[a] * wn[b];
+      float mdl = 0.f;  // (H S_k CV^T)(a, b)
+      for (int r = 0; r < R; ++r) mdl = fmaf(hs[a * R + r] * wn[r], cvs[b * R + r], mdl);
+      const float d = pks[e] - mdl;
+      df_mac(ek, d, d);
+      DF g = {slot[e], slot[RR + e]};
+      df_mac(g, wn[a], wn[b]);
+      slot[e] = g.hi;
+      slot[RR + e] = g.lo;
     }
-    for (int r = lane; r < R; r += 32) df_mac(ek, -2.f * wn[r], g3[r]);
     __syncwarp();
   }
   // lane sums -> warp -> block, as double-float sums in a fixed order (FP32 pipes)
@@ -421,22 +455,24 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += slots[w * (RR + 1) + e];
-    part[(int64_t)blockIdx.x * pstride + e] = s;
+    DF a = {0.f, 0.f};
+    for (int w = 0; w < nw; ++w) a = df_add(a, DF{slots[w * 2 * RR + e], slots[w * 2 * RR + RR + e]});
+    part[(int64_t)blockIdx.x * pstride + e] = a.hi;
+    part[(int64_t)blockIdx.x * pstride + RR + e] = a.lo;
   }
   if (threadIdx.x == 0) {
     DF s = {0.f, 0.f};
     for (int w = 0; w < nw; ++w) s = df_add(s, DF{ered[w][0], ered[w][1]});
-    part[(int64_t)blockIdx.x * pstride + RR] = s.hi;
-    part[(int64_t)blockIdx.x * pstride + RR + 1] = s.lo;
+    part[(int64_t)blockIdx.x * pstride + 2 * RR] = s.hi;
+    part[(int64_t)blockIdx.x * pstride + 2 * RR + 1] = s.lo;
   }
 }
 
 // shared memory of the H / V updates: the pseudoinverse workspace plus 5 R^2 + 2
-// doubles of intermediates when that fits in 160 KB (R <= 48), else the workspace only
+// doubles of intermediates and the refined inverse's work area when that fits
+// in 160 KB (R <= 40), else the workspace only
 inline size_t update_smem(int R, int* inshared) {
-  const size_t full = (spd_pinv_words(R) + 5 * (size_t)R * R + 2) * sizeof(double);
+  const size_t full = (spd_pinv_words(R) + 5 * (size_t)R * R + 2 + refined_work_words(R)) * sizeof(double);
   *inshared = full <= 160 * 1024;
   return *inshared ? full : spd_pinv_smem(R);
 }
@@ -475,14 +511,17 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
     __syncthreads();
   } else {
     if (it > 0) {
-      par_reduce_load(part3, nblk, pstride, RR + 2, 0, T, red, W3);
+      // W-update partials: W^T W as (hi, lo) in [0, 2 RR), e as (hi, lo) after them
+      par_reduce_load(part3, nblk, pstride, 2 * RR + 2, 0, T, red, W3);
       __syncthreads();
-      par_reduce_combine(RR + 2, 0, T, red, W3);
+      par_reduce_combine(2 * RR + 2, 0, T, red, W3);
+      __syncthreads();
+      for (int e = threadIdx.x; e < RR; e += blockDim.x) W3[e] += W3[RR + e];
       __syncthreads();
       for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
         if (e < RR) WtW[e] = W3[e];
         else {
-          const double v = W3[RR] + W3[RR + 1];
+          const double v = W3[2 * RR] + W3[2 * RR + 1];
           loss[it - 1] = v;
           if (!isfinite(v)) set_status(status, ST_NONFINITE);
         }
@@ -515,7 +554,9 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
     scl[r] = inv_norm(n2, status);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) Hn[e] *= scl[e % R];
+  // H is stored in FP32: H^T H is formed from the rounded values, so that it
+  // agrees exactly with the H the next right-hand sides are formed from
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) Hn[e] = (double)(float)(Hn[e] * scl[e % R]);
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     H[e] = (float)Hn[e];
@@ -549,11 +590,13 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
   __shared__ int ok;
   __shared__ double red[kRedMax];
   const int T = blockDim.x;
+  // the Lemma 2 partials are double-float (hi in [0, RR), lo in [RR, 2 RR)):
+  // both halves reduced (into C and DC, free until later), then added
   if (InvPre) {
     // (W^T W * H^T H)^+ comes from the Lemma 2 grid's extra block
-    par_reduce_load(part, nblk, pstride, RR, 0, T, red, g);
+    par_reduce_load(part, nblk, pstride, 2 * RR, 0, T, red, C);
     __syncthreads();
-    par_reduce_combine(RR, 0, T, red, g);
+    par_reduce_combine(2 * RR, 0, T, red, C);
     __syncthreads();
   } else {
     for (int e = threadIdx.x; e < RR; e += blockDim.x) Gm[e] = WtW[e] * HtH[e];
@@ -563,12 +606,14 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
       const bool f = warp_spd_factor<double>(Gm, R, ush);
       if (threadIdx.x == 0) ok = f;
     }
-    par_reduce_load(part, nblk, pstride, RR, 32, T - 32, red, g);
+    par_reduce_load(part, nblk, pstride, 2 * RR, 32, T - 32, red, C);
     __syncthreads();
-    par_reduce_combine(RR, 32, T - 32, red, g);
+    par_reduce_combine(2 * RR, 32, T - 32, red, C);
     __syncthreads();
     block_spd_finish<double, double>(ok != 0, Gm, Inv, L, V, R, ush, status);
   }
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) g[e] = C[e] + C[RR + e];
+  __syncthreads();
   const double* Iv = InvPre ? InvPre : Inv;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int i = e / R, r = e - i * R;
@@ -590,10 +635,16 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
     scl[r] = inv_norm(fmax(n2, 0.0), status);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    const double sc = scl[e % R];
-    C[e] *= sc;
-    DC[e] *= sc;
+  // CV is stored in FP32: Psi = D^T D CV and V^T V = CV^T D^T D CV are formed
+  // from the rounded CV, so that they agree exactly with the V = D CV the
+  // next Q-step and right-hand sides use
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) C[e] = (double)(float)(C[e] * scl[e % R]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {  // DC = DtD C
+    const int i = e / R, r = e - i * R;
+    double s = 0.0;
+    for (int m = 0; m < R; ++m) s = fma(DtD[i * R + m], C[m * R + r], s);
+    DC[e] = s;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
@@ -606,29 +657,22 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
     Gm[e] = s * HtH[e];
   }
   __syncthreads();
-  // Ginv only enters the W update in FP32 (W_k = G3_k Ginv with G3 and Ginv as
-  // floats), so it is factored in FP32 (FP64 fallback when a pivot fails)
-  {
-    float* fsh = reinterpret_cast<float*>(ush);
-    if (threadIdx.x < 32) {
-      const bool f = warp_spd_factor<float>(Gm, R, fsh);
-      if (threadIdx.x == 0) ok = f;
-    }
-    __syncthreads();
-    if (ok) block_spd_finish<float, double>(true, Gm, Ginv, L, V, R, fsh, status);
-    else block_spd_pinv<double, double>(Gm, Ginv, L, V, R, ush, status);
-  }
+  // Ginv = (V^T V * H^T H)^-1 to FP64 accuracy (the W update applies it in
+  // FP64): FP32 factorisation refined by FP64 Newton steps when the
+  // intermediates sit in shared memory, else the FP64 Cholesky
+  if (inshared) block_spd_inv_refined(Gm, Ginv, L, V, R, ush, ush + spd_pinv_words(R) + 5 * RR + 2, status);
+  else block_spd_pinv<double, double>(Gm, Ginv, L, V, R, ush, status);
 }
 
 // ----------------------------------------------------- iteration epilogue --
 __global__ void k_finish(int R, const float* __restrict__ part, int nblk, int pstride, double* __restrict__ WtW,
                          double* __restrict__ loss, int it, double* __restrict__ scratch, int* __restrict__ status) {
   const int RR = R * R;
-  block_reduce_parts(part, nblk, pstride, RR + 2, scratch);
+  block_reduce_parts(part, nblk, pstride, 2 * RR + 2, scratch);
   for (int e = threadIdx.x; e < RR + 1; e += blockDim.x) {
-    if (e < RR) WtW[e] = scratch[e];
+    if (e < RR) WtW[e] = scratch[e] + scratch[RR + e];
     else {
-      const double v = scratch[RR] + scratch[RR + 1];
+      const double v = scratch[2 * RR] + scratch[2 * RR + 1];
       loss[it] = v;
       if (!isfinite(v)) set_status(status, ST_NONFINITE);
     }
@@ -842,7 +886,7 @@ void als_set_attrs() {
 
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
   als_set_attrs();
-  k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV, b.Prot);
+  DP2_COUNTED(k_als_init<<<1 + 64, 256, 0, s>>>(b.K, b.J, b.R, b.D, V0, b.H, b.W, b.WtW, b.HtH, b.Psi, b.VtV, b.Prot));
   launch_atb(b.J, b.R, b.D, V0, b.Psi, b.atb, s);
   launch_atb(b.J, b.R, V0, V0, b.VtV, b.atb, s);
 }
@@ -850,8 +894,8 @@ void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s) {
 void launch_qstep_only(AlsBufs& b, cudaStream_t s) {
   const int R = b.R, nw = als_warps(R);
   if (launch_qstep_reg(b, b.part, 2 * R * R + 2, 0, s)) return;
-  k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part,
-                                                     2 * R * R + 2, b.status, 0, b.rank);
+  DP2_COUNTED(k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, b.part,
+                                                     2 * R * R + 2, b.status, 0, b.rank));
 }
 
 // One iteration = 5 launches: Q-step (+ Lemma 1 partials; its extra block
@@ -885,42 +929,42 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
   ph.status = pv.status = b.status;
   bool preh = pre;
   if (!launch_qstep_reg(b, p1, ps, 1, s, pre ? &ph : nullptr)) {
-    k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
-                                                       b.status, 1, b.rank);
+    DP2_COUNTED(k_qstep<<<b.nblk, nw * 32, qstep_smem(R, nw), s>>>(b.K, R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, p1, ps,
+                                                       b.status, 1, b.rank));
     preh = false;
   }
   int insh = 0;
   const size_t psm = update_smem(R, &insh);
-  k_update_h<<<1, 1024, psm, s>>>(R, p1, b.nq, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small,
-                                 b.status, insh, preh ? b.InvH : nullptr);
-  size_t g2sm = (size_t)(RR + nw * RR + nw * RR) * 4;
+  DP2_COUNTED(k_update_h<<<1, 1024, psm, s>>>(R, p1, b.nq, p3, b.nblk, ps, it, b.WtW, b.VtV, b.H, b.HtH, b.loss, b.small,
+                                 b.status, insh, preh ? b.InvH : nullptr));
+  size_t g2sm = (size_t)(RR + 2 * nw * RR + nw * RR) * 4;
   if (pre) g2sm = std::max(g2sm, pre_solve_words(R, nw * 32) * sizeof(double));
-  k_g2<<<b.nblk + (pre ? 1 : 0), nw * 32, g2sm, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps, pv, pre ? 1 : 0);
-  k_update_v<<<1, 1024, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
-                               b.status, insh, pre ? b.InvV : nullptr);
-  k_g3w<<<b.nblk, nw * 32, (size_t)(4 * RR + nw * (RR + 1) + nw * (RR + 2 * R)) * 4, s>>>(
-      b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.HtH, b.VtV, b.W, p3, ps);
+  DP2_COUNTED(k_g2<<<b.nblk + (pre ? 1 : 0), nw * 32, g2sm, s>>>(b.K, R, b.Pi, b.W, b.H, p2, ps, pv, pre ? 1 : 0));
+  DP2_COUNTED(k_update_v<<<1, 1024, psm, s>>>(R, p2, b.nblk, ps, b.WtW, b.HtH, b.DtD, b.CV, b.Psi, b.VtV, b.Ginv, b.small,
+                               b.status, insh, pre ? b.InvV : nullptr));
+  DP2_COUNTED(k_g3w<<<b.nblk, nw * 32, (size_t)RR * 8 + (size_t)(3 * RR + nw * 2 * RR + nw * (RR + 2 * R)) * 4, s>>>(
+      b.K, R, b.Pi, b.Psi, b.H, b.Ginv, b.CV, b.W, p3, ps));
 }
 
 // Closes the last iteration `it`: W^T W and loss[it] from the W-update partials.
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s) {
   const int R = b.R, RR = R * R, ps = 2 * RR + 2;
-  k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.pr * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
-                             b.status);
+  DP2_COUNTED(k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.pr * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
+                             b.status));
 }
 
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s) {
   const int64_t n = (int64_t)K * R * R;
-  k_upol_h<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, Upol, H, Tk);
+  DP2_COUNTED(k_upol_h<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, Upol, H, Tk));
 }
 
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s) {
   const int64_t n = (int64_t)K * R * R;
-  k_p_from_cv<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, CV, Ft, P);
+  DP2_COUNTED(k_p_from_cv<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, CV, Ft, P));
 }
 
 void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s) {
-  k_vtm<<<K, 128, 0, s>>>(J, R, V, Mblk, P);
+  DP2_COUNTED(k_vtm<<<K, 128, 0, s>>>(J, R, V, Mblk, P));
 }
 
 void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,
@@ -932,8 +976,8 @@ void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, d
 void launch_atb(int64_t rows, int n, const float* A, const float* B, double* out, float* part, cudaStream_t s) {
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kAtbBlocks, (rows + ATB_ROWS - 1) / ATB_ROWS));
   const int64_t chunk = (rows + nb - 1) / nb;
-  k_atb_part<<<nb, ATB_THREADS, 0, s>>>(rows, n, A, B, chunk, part);
-  k_atb_fin<<<(n * n + 255) / 256, 256, 0, s>>>(nb, n * n, part, out);
+  DP2_COUNTED(k_atb_part<<<nb, ATB_THREADS, 0, s>>>(rows, n, A, B, chunk, part));
+  DP2_COUNTED(k_atb_fin<<<(n * n + 255) / 256, 256, 0, s>>>(nb, n * n, part, out));
 }
 
 void launch_fitness(int K, int R, const float* P, const float* Upol, const float* H, const float* W,
@@ -941,13 +985,13 @@ void launch_fitness(int K, int R, const float* P, const float* Upol, const float
                     const double* AtA, int ldg) {
   als_set_attrs();
   const int nw = R > 48 ? 3 : 4;  // (2 + 3 nw) R^2 floats of shared memory <= 200 KB
-  k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 3 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2, AtA,
-                                                                           ldg, part);
-  k_reduce_f64<<<1, 32, 0, s>>>(part, nblk, out);
+  DP2_COUNTED(k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 3 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2, AtA,
+                                                                           ldg, part));
+  DP2_COUNTED(k_reduce_f64<<<1, 32, 0, s>>>(part, nblk, out));
 }
 
 void launch_p_stream(int K, int J, int Jp, int R, int LP, const float* V, const float* B, float* P, cudaStream_t s) {
-  k_p_stream<<<K, 128, 0, s>>>(J, Jp, R, LP, V, B, P);
+  DP2_COUNTED(k_p_stream<<<K, 128, 0, s>>>(J, Jp, R, LP, V, B, P));
 }
 
 }  // namespace dp2

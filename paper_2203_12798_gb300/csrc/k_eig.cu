@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) k_eig_reg(int K, const double*
 bool launch_eig_reg(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s) {
   const unsigned grid = (unsigned)((K + EIG_WARPS - 1) / EIG_WARPS);
-#define DP2_EIG(NC) k_eig_reg<NC><<<grid, 32 * EIG_WARPS, 0, s>>>(K, G, M2, ell, LP, R, T, lam, status)
+#define DP2_EIG(NC) DP2_COUNTED(k_eig_reg<NC><<<grid, 32 * EIG_WARPS, 0, s>>>(K, G, M2, ell, LP, R, T, lam, status))
   if (ell == 20) { DP2_EIG(20); return true; }
   if (ell == 30) { DP2_EIG(30); return true; }
   switch (LP) {

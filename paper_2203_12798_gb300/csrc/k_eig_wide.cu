@@ -227,7 +227,7 @@ static void eigw(const double* G, const float* M2, int K, int ell, int LP, int R
     attr = true;
   }
   const unsigned grid = (unsigned)((K + EIGW_WARPS - 1) / EIGW_WARPS);
-  k_eig_wide<N><<<grid, 32 * EIGW_WARPS, smem, s>>>(K, G, M2, ell, LP, R, T, lam, status);
+  DP2_COUNTED(k_eig_wide<N><<<grid, 32 * EIGW_WARPS, smem, s>>>(K, G, M2, ell, LP, R, T, lam, status));
 }
 
 // Register columns N: l itself for the sketch widths 50 and 60, else LP.

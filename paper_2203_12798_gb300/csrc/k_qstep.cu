@@ -375,8 +375,8 @@ static void qreg(const AlsBufs& b, float* part, int pstride, int want_g1, cudaSt
     cudaFuncSetAttribute(k_qstep_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     attr = true;
   }
-  k_qstep_reg<R><<<b.nq + on, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
-                                                  b.status, want_g1, b.Prot, b.rank, p0, on);
+  DP2_COUNTED(k_qstep_reg<R><<<b.nq + on, nw * 32, smem, s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part, pstride,
+                                                  b.status, want_g1, b.Prot, b.rank, p0, on));
 }
 
 template <int R>

@@ -397,8 +397,8 @@ static void qwide(const AlsBufs& b, float* part, int pstride, int want_g1, cudaS
     cudaFuncSetAttribute(k_qstep_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qw_smem<R>());
     attr = true;
   }
-  k_qstep_wide<R><<<b.nq + on, 64 * NP, qw_smem<R>(), s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part,
-                                                             pstride, b.status, want_g1, b.Prot, b.rank, p0, on);
+  DP2_COUNTED(k_qstep_wide<R><<<b.nq + on, 64 * NP, qw_smem<R>(), s>>>(b.K, b.R, b.Ft, b.Psi, b.W, b.H, b.Upol, b.Pi, part,
+                                                             pstride, b.status, want_g1, b.Prot, b.rank, p0, on));
 }
 
 // Blocks: one slice per pair of warps, at most `cap` blocks (the blocks loop

@@ -105,20 +105,20 @@ static int grid_for(int64_t n, int threads) {
 }
 
 void launch_gaussian(uint64_t seed, uint32_t sid, int64_t n, float* out, int r16, cudaStream_t s) {
-  k_gaussian<<<grid_for((n + 3) / 4, 256), 256, 0, s>>>(seed, sid, n, out, r16);
+  DP2_COUNTED(k_gaussian<<<grid_for((n + 3) / 4, 256), 256, 0, s>>>(seed, sid, n, out, r16));
 }
 void launch_philox_words(uint64_t seed, uint32_t sid, int64_t n, uint32_t* out, cudaStream_t s) {
-  k_philox_words<<<grid_for((n + 3) / 4, 256), 256, 0, s>>>(seed, sid, n, out);
+  DP2_COUNTED(k_philox_words<<<grid_for((n + 3) / 4, 256), 256, 0, s>>>(seed, sid, n, out));
 }
 void launch_repitch(const void* src, int64_t rows, int J, int es, void* dst, int64_t ldx, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((rows + 7) / 8, 65535);
-  k_repitch<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(static_cast<const uint8_t*>(src), rows, J, es,
-                                                                   static_cast<uint8_t*>(dst), ldx);
+  DP2_COUNTED(k_repitch<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(static_cast<const uint8_t*>(src), rows, J, es,
+                                                                   static_cast<uint8_t*>(dst), ldx));
 }
 
 void launch_pad_omega(const float* om, int J, int ell, int Jpad, int LP, dpar2_dtype dt, float* out,
                       cudaStream_t s) {
-  k_pad_omega<<<grid_for((int64_t)Jpad * LP, 256), 256, 0, s>>>(om, J, ell, Jpad, LP, (int)dt, out);
+  DP2_COUNTED(k_pad_omega<<<grid_for((int64_t)Jpad * LP, 256), 256, 0, s>>>(om, J, ell, Jpad, LP, (int)dt, out));
 }
 
 }  // namespace dp2

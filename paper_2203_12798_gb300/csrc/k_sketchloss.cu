@@ -356,13 +356,13 @@ static void sl_small_lp(const float* M1, const float* M2, const double* GB, cons
     cudaFuncSetAttribute(k_sl_small<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  k_sl_small<LP><<<K, 256, sm, s>>>(M1, M2, GB, xn, ell, ratio, P, S);
+  DP2_COUNTED(k_sl_small<LP><<<K, 256, sm, s>>>(M1, M2, GB, xn, ell, ratio, P, S));
 }
 
 void launch_sl_loss(const float* M1, const float* M2, const double* GB, const double* xn, int K, int ell, int LP,
                     double* ratio, float* P, float* S, double* out, cudaStream_t s) {
   DP2_LP_SWITCH(LP, (sl_small_lp<L>(M1, M2, GB, xn, K, ell, ratio, P, S, s)));
-  k_sl_total<<<1, 256, 0, s>>>(ratio, K, out);
+  DP2_COUNTED(k_sl_total<<<1, 256, 0, s>>>(ratio, K, out));
 }
 
 void launch_sl_rowsplit(const float* B1, int K, int Jp, int J, int Jpad, int ell, int LP, int LPN, dpar2_dtype dt,
@@ -370,11 +370,11 @@ void launch_sl_rowsplit(const float* B1, int K, int Jp, int J, int Jpad, int ell
   const int64_t warps = (int64_t)K * (out16 ? LPN : LP);
   const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
   if (out16 && dt == DPAR2_F16)
-    k_sl_rowsplit<__half><<<grid, 256, 0, s>>>(B1, K, Jp, J, Jpad, ell, LP, LPN, static_cast<__half*>(out16), out32,
-                                               rscale);
+    DP2_COUNTED(k_sl_rowsplit<__half><<<grid, 256, 0, s>>>(B1, K, Jp, J, Jpad, ell, LP, LPN, static_cast<__half*>(out16), out32,
+                                               rscale));
   else
-    k_sl_rowsplit<__nv_bfloat16><<<grid, 256, 0, s>>>(B1, K, Jp, J, Jpad, ell, LP, LPN,
-                                                      static_cast<__nv_bfloat16*>(out16), out32, rscale);
+    DP2_COUNTED(k_sl_rowsplit<__nv_bfloat16><<<grid, 256, 0, s>>>(B1, K, Jp, J, Jpad, ell, LP, LPN,
+                                                      static_cast<__nv_bfloat16*>(out16), out32, rscale));
 }
 
 template <int LP>
@@ -382,7 +382,7 @@ static void sl_wrows_lp(const float* U, const float* Q1, const int64_t* d_off, i
                         const float* S, const double* xn, double gscale, const float* rs, float* W, float* bmax,
                         cudaStream_t s) {
   dim3 grid((unsigned)std::max<int64_t>(1, (maxI + 127) / 128), (unsigned)K);
-  k_sl_wrows<LP><<<grid, 128, 0, s>>>(U, Q1, d_off, P, S, xn, gscale, K, rs, W, bmax);
+  DP2_COUNTED(k_sl_wrows<LP><<<grid, 128, 0, s>>>(U, Q1, d_off, P, S, xn, gscale, K, rs, W, bmax));
 }
 
 int64_t sl_wrows_blocks(int K, int64_t maxI) { return std::max<int64_t>(1, (maxI + 127) / 128) * K; }
@@ -392,21 +392,21 @@ void launch_sl_wrows(const float* U, const float* Q1, const int64_t* d_off, int 
                      float* bmax, unsigned* wmax, cudaStream_t s) {
   DP2_LP_SWITCH(LP, (sl_wrows_lp<L>(U, Q1, d_off, K, maxI, P, S, xn, gscale, rs, W, bmax, s)));
   cudaMemsetAsync(wmax, 0, (size_t)LP * sizeof(unsigned), s);
-  k_sl_colmax<<<64, (1024 / LP) * LP, 0, s>>>(bmax, sl_wrows_blocks(K, maxI), LP, wmax);
+  DP2_COUNTED(k_sl_colmax<<<64, (1024 / LP) * LP, 0, s>>>(bmax, sl_wrows_blocks(K, maxI), LP, wmax));
 }
 
 void launch_sl_wsplit(const float* W, int64_t N, int LP, int LPN, const unsigned* wmax, dpar2_dtype dt, void* out16,
                       cudaStream_t s) {
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 8192));
-  if (dt == DPAR2_F16) k_sl_wsplit<__half><<<grid, 256, 0, s>>>(W, N, LP, LPN, wmax, static_cast<__half*>(out16));
-  else k_sl_wsplit<__nv_bfloat16><<<grid, 256, 0, s>>>(W, N, LP, LPN, wmax, static_cast<__nv_bfloat16*>(out16));
+  if (dt == DPAR2_F16) DP2_COUNTED(k_sl_wsplit<__half><<<grid, 256, 0, s>>>(W, N, LP, LPN, wmax, static_cast<__half*>(out16)));
+  else DP2_COUNTED(k_sl_wsplit<__nv_bfloat16><<<grid, 256, 0, s>>>(W, N, LP, LPN, wmax, static_cast<__nv_bfloat16*>(out16)));
 }
 
 void launch_sl_gradsum(const float* part, int np, int LP, int Jp, int J, int ell, const unsigned* wmax, float* grad,
                        cudaStream_t s) {
   const int64_t n = (int64_t)J * ell;
-  k_sl_gradsum<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(part, np, LP, Jp, J, ell, wmax,
-                                                                                   grad);
+  DP2_COUNTED(k_sl_gradsum<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(part, np, LP, Jp, J, ell, wmax,
+                                                                                   grad));
 }
 
 }  // namespace dp2

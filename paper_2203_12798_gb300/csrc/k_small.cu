@@ -837,8 +837,8 @@ static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell
                     cudaStream_t s) {
   const dim3 grid(K, nsplit);
   const size_t smem = GR_ROWS * LP * sizeof(float);
-  if (df) k_gram_dd<NP, true><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit);
-  else k_gram_dd<NP, false><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit);
+  if (df) DP2_COUNTED(k_gram_dd<NP, true><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
+  else DP2_COUNTED(k_gram_dd<NP, false><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
 }
 
 static void gram_dispatch(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
@@ -859,7 +859,7 @@ void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell
   }
   gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, df, s);
   const int64_t n = (int64_t)LP * LP, warps = (int64_t)K * n;
-  k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G);
+  DP2_COUNTED(k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G));
 }
 
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
@@ -870,26 +870,26 @@ void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float
     attr = true;
   }
   if (fp64)
-    k_chol_drop<double><<<K, 32, 2 * ell * ell * sizeof(double), s>>>(G, ell, LP, tau, Minv, rank, status);
+    DP2_COUNTED(k_chol_drop<double><<<K, 32, 2 * ell * ell * sizeof(double), s>>>(G, ell, LP, tau, Minv, rank, status));
   else
-    k_chol_drop<float><<<K, 32, 2 * ell * ell * sizeof(float), s>>>(G, ell, LP, tau, Minv, rank, status);
+    DP2_COUNTED(k_chol_drop<float><<<K, 32, 2 * ell * ell * sizeof(float), s>>>(G, ell, LP, tau, Minv, rank, status));
 }
 
 void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s) {
   dim3 grid((maxI + 127) / 128, K);
-  DP2_LP_SWITCH(LP, (k_formq<L><<<grid, 128, 0, s>>>(Y, d_off, M1)));
+  DP2_LP_SWITCH(LP, (DP2_COUNTED(k_formq<L><<<grid, 128, 0, s>>>(Y, d_off, M1))));
 }
 
 void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s) {
-  k_reduce_rows_f64<<<(K + 127) / 128, 128, 0, s>>>(part, K, n, out);
+  DP2_COUNTED(k_reduce_rows_f64<<<(K + 127) / 128, 128, 0, s>>>(part, K, n, out));
 }
 
 void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, double* G, cudaStream_t s) {
   if (LP == 24 && ell <= 20) {  // the common l = R + p = 20
-    k_gram_b1<24, 5><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G);
+    DP2_COUNTED(k_gram_b1<24, 5><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G));
     return;
   }
-  DP2_LP_SWITCH(LP, (k_gram_b1<L, L / 4><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G)));
+  DP2_LP_SWITCH(LP, (DP2_COUNTED(k_gram_b1<L, L / 4><<<K, GB_THREADS, 0, s>>>(B1, Jp, J, ell, G))));
 }
 
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
@@ -902,7 +902,7 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
   }
   if (launch_eig_reg(G, M2, K, ell, LP, R, T, lam, status, s)) return;
   if (launch_eig_wide(G, M2, K, ell, LP, R, T, lam, status, s)) return;
-  k_eig_top<<<K, 32, smem, s>>>(G, M2, ell, LP, R, T, lam, status);
+  DP2_COUNTED(k_eig_top<<<K, 32, smem, s>>>(G, M2, ell, LP, R, T, lam, status));
 }
 
 void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
@@ -910,7 +910,7 @@ void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R
 #define DP2_MB(RB)                                                                                   \
   do {                                                                                               \
     cudaFuncSetAttribute(k_mblock<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, MB_SMEM_CAP);    \
-    k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau); \
+    DP2_COUNTED(k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau)); \
   } while (0)
   // single pass when M_k fits twice per SM in shared memory
   const size_t msm = (size_t)J * R * sizeof(float);
@@ -918,7 +918,7 @@ void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R
 #define DP2_MB1(RB, EB)                                                                                  \
   do {                                                                                                   \
     cudaFuncSetAttribute(k_mblock1<RB, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);      \
-    k_mblock1<RB, EB><<<K, MB1_THREADS, msm, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau);      \
+    DP2_COUNTED(k_mblock1<RB, EB><<<K, MB1_THREADS, msm, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau));      \
   } while (0)
   if (msm <= 100 * 1024) {
     if (R == 10 && eb == 24) { DP2_MB1(10, 24); return; }
@@ -940,22 +940,22 @@ void launch_seg_product(const float* In, int ldin, int nin, const float* T, int6
                         int ldout, const int64_t* d_off, int K, int64_t maxI, cudaStream_t s) {
   dim3 grid((unsigned)((maxI + 127) / 128), K);
   const int NBr = round_up(nout, 8);
-  DP2_LP_SWITCH(NBr, (k_seg_product<L><<<grid, 128, nin * L * sizeof(float), s>>>(In, ldin, nin, T, tstride, nout,
-                                                                                  Out, ldout, d_off)));
+  DP2_LP_SWITCH(NBr, (DP2_COUNTED(k_seg_product<L><<<grid, 128, nin * L * sizeof(float), s>>>(In, ldin, nin, T, tstride, nout,
+                                                                                  Out, ldout, d_off))));
 }
 
 void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cudaStream_t s) {
   int g = (int)min64((n + 255) / 256, 4096);
-  k_sum_parts<<<g < 1 ? 1 : g, 256, 0, s>>>(part, nparts, n, out);
+  DP2_COUNTED(k_sum_parts<<<g < 1 ? 1 : g, 256, 0, s>>>(part, nparts, n, out));
 }
 
 void launch_s2_enorm(float* Ft, int64_t rows, int R, float* D, int J, float* E, float tau, double* part,
                      float* keep, int* ndrop, cudaStream_t s) {
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kEnormBlocks, (rows + 255) / 256));
   const int64_t chunk = (rows + nb - 1) / nb;
-  k_colnorm_part<<<nb, EN_THREADS, 0, s>>>(Ft, rows, R, chunk, part);
-  k_enorm_fin<<<1, EN_THREADS, 0, s>>>(part, nb, R, E, keep, ndrop, tau);
-  k_enorm_apply<<<128, 256, 0, s>>>(Ft, rows, R, D, J, keep, ndrop);
+  DP2_COUNTED(k_colnorm_part<<<nb, EN_THREADS, 0, s>>>(Ft, rows, R, chunk, part));
+  DP2_COUNTED(k_enorm_fin<<<1, EN_THREADS, 0, s>>>(part, nb, R, E, keep, ndrop, tau));
+  DP2_COUNTED(k_enorm_apply<<<128, 256, 0, s>>>(Ft, rows, R, D, J, keep, ndrop));
 }
 
 

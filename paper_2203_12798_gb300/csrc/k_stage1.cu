@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
                                                         double* __restrict__ xpart) {
   constexpr int JPT = LP <= 32 ? 4 : 2;
   __shared__ __align__(16) float qs[PJ_QROWS * LP];
-  __shared__ float red[PJ_THREADS / 32];
+  __shared__ double red[PJ_THREADS / 32];
   const int k = blockIdx.y, tid = threadIdx.x;
   const int j0 = (blockIdx.x * PJ_THREADS + tid) * JPT;
   const bool jv = j0 < J;
@@ -187,10 +187,15 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
   for (int a = 0; a < JPT; ++a)
 #pragma unroll
     for (int c = 0; c < LP; ++c) acc[a][c] = 0.f;
-  float nrm = 0.f;
+  // ||X_k||^2 of this thread's columns: one FP32 accumulator per column over
+  // a row chunk (at most PJ_QROWS squares each), chunks added in FP64
+  float nrm[JPT];
+  double nrd = 0.0;
   const T* xcol = X + (jv ? j0 : 0);
 
   for (int64_t rs = r0; rs < r1; rs += PJ_QROWS) {
+#pragma unroll
+    for (int a = 0; a < JPT; ++a) nrm[a] = 0.f;
     const int nr = (int)min64(PJ_QROWS, r1 - rs);
     __syncthreads();
     for (int p = tid; p < nr * LP / 4; p += PJ_THREADS)
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
 #pragma unroll
         for (int a = 0; a < JPT; ++a) {
           if (j0 + a >= J) x[u][a] = 0.f;
-          nrm = fmaf(x[u][a], x[u][a], nrm);
+          nrm[a] = fmaf(x[u][a], x[u][a], nrm[a]);
         }
         const float4* qrow = reinterpret_cast<const float4*>(qs + (i + u) * LP);
 #pragma unroll
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
 #pragma unroll
       for (int a = 0; a < JPT; ++a) {
         if (j0 + a >= J) x[a] = 0.f;
-        nrm = fmaf(x[a], x[a], nrm);
+        nrm[a] = fmaf(x[a], x[a], nrm[a]);
       }
       const float4* qrow = reinterpret_cast<const float4*>(qs + i * LP);
 #pragma unroll
@@ -255,6 +260,10 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
         }
       }
     }
+    float cs = 0.f;
+#pragma unroll
+    for (int a = 0; a < JPT; ++a) cs += nrm[a];
+    nrd += (double)cs;
   }
   if (j0 < Jp) {
     float* dst = B1 + (int64_t)k * LP * Jp + j0;
@@ -265,8 +274,8 @@ __global__ void __launch_bounds__(PJ_THREADS) k_project(const T* __restrict__ X,
     }
   }
   if (xpart) {
-    nrm = warp_sum(nrm);
-    if ((tid & 31) == 0) red[tid >> 5] = nrm;
+    nrd = warp_sum(nrd);
+    if ((tid & 31) == 0) red[tid >> 5] = nrd;
     __syncthreads();
     if (tid == 0) {
       double s = 0;
@@ -290,8 +299,8 @@ static void sketch_t(const void* X, int64_t ldx, int64_t N, int J, const float* 
   if (d_off) grid = dim3((unsigned)((maxI + C::ROWS - 1) / C::ROWS), (unsigned)K);
   else grid = dim3((unsigned)((N + C::ROWS - 1) / C::ROWS));
   if (grid.x == 0) return;
-  k_sketch<T, LP><<<grid, SK_THREADS, C::SMEM, s>>>(reinterpret_cast<const T*>(X), ldx, N, J, om, Y, d_off,
-                                                    om_stride);
+  DP2_COUNTED(k_sketch<T, LP><<<grid, SK_THREADS, C::SMEM, s>>>(reinterpret_cast<const T*>(X), ldx, N, J, om, Y, d_off,
+                                                    om_stride));
 }
 
 template <int LP>
@@ -319,8 +328,8 @@ static void project_t(const void* X, int64_t ldx, const int64_t* d_off, int K, i
   constexpr int JPT = LP <= 32 ? 4 : 2;
   const int nJb = (Jp + PJ_THREADS * JPT - 1) / (PJ_THREADS * JPT);
   if (nJb_out) *nJb_out = nJb;
-  k_project<T, LP><<<dim3(nJb, K), PJ_THREADS, 0, s>>>(reinterpret_cast<const T*>(X), ldx, d_off, J, Jp, Q, B1,
-                                                       xpart);
+  DP2_COUNTED(k_project<T, LP><<<dim3(nJb, K), PJ_THREADS, 0, s>>>(reinterpret_cast<const T*>(X), ldx, d_off, J, Jp, Q, B1,
+                                                       xpart));
 }
 
 void launch_project_generic(const void* X, dpar2_dtype dt, int64_t ldx, const int64_t* d_off, int K, int J,

@@ -204,15 +204,15 @@ void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, 
   dim3 grid((J + S2_JT - 1) / S2_JT, nch);
   const size_t smem = (size_t)2 * (R * S2_JT + R * LP) * sizeof(float);
   DP2_LP_SWITCH(LP, (set_smem_attr(k_s2_sketch<L>, smem),
-                     k_s2_sketch<L><<<grid, S2_THREADS, smem, s>>>(Mblk, K, J, R, om2, kchunk, Y2p)));
+                     DP2_COUNTED(k_s2_sketch<L><<<grid, S2_THREADS, smem, s>>>(Mblk, K, J, R, om2, kchunk, Y2p))));
 }
 
 void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s) {
   const int spb = std::max(1, 128 / R);
   const size_t smem = (size_t)2 * (S2_PJ * 128 + S2_PJ * LP) * sizeof(float);
   DP2_LP_SWITCH(LP, (set_smem_attr(k_s2_project<L>, smem),
-                     k_s2_project<L><<<(unsigned)((K + spb - 1) / spb), S2_THREADS, smem, s>>>(Mblk, K, J, R, Q2,
-                                                                                              spb, B2p)));
+                     DP2_COUNTED(k_s2_project<L><<<(unsigned)((K + spb - 1) / spb), S2_THREADS, smem, s>>>(Mblk, K, J, R, Q2,
+                                                                                              spb, B2p))));
 }
 
 }  // namespace dp2

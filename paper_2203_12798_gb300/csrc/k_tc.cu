@@ -813,7 +813,10 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       PJ_ITEM(it);
       const int64_t nrows = off[k + 1] - off[k];
       const int nch = (int)((nrows + PJ_BK - 1) / PJ_BK);
-      float acc = 0.f;
+      // per lane: eight independent FP32 accumulators (one per element of a
+      // 16-byte load, 64 squares each per staged chunk, so no accumulator grows
+      // far beyond its terms), combined pairwise and added in FP64 per chunk
+      double acc = 0.0;
       bool ok = true;
       for (int c = 0; c < nch; ++c) {
         if (!wait_bounded(&full[s], ph, abort_flag)) {
@@ -824,6 +827,9 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         // last chunk is aligned to the slice's end)
         const int valid = (int)min64(PJ_BK, nrows - (int64_t)c * PJ_BK);
         const uint8_t* a = sA + s * S::A + nw * BYTES_PER;
+        float a8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a8[e] = 0.f;
 #pragma unroll
         for (int it = 0; it < BYTES_PER / 512; ++it) {
           const int byte = nw * BYTES_PER + it * 512 + lane * 16;
@@ -834,9 +840,10 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
             if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
             else Vec16<__half>::unpack(u, f);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc = fmaf(f[e], f[e], acc);
+            for (int e = 0; e < 8; ++e) a8[e] = fmaf(f[e], f[e], a8[e]);
           }
         }
+        acc += (double)(((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7])));
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (++s == ST) {
@@ -846,7 +853,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
       }
       if (!ok) break;
       acc = warp_sum(acc);
-      if (lane == 0) xpart[((int64_t)k * nJb + jb) * PJ_NORM_WARPS + nw] = (double)acc;
+      if (lane == 0) xpart[((int64_t)k * nJb + jb) * PJ_NORM_WARPS + nw] = acc;
     }
   }
   tc_fence_before();
@@ -1011,14 +1018,14 @@ bool launch_sketch_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, int
       cudaFuncSetAttribute(tc::k_sketch_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SketchSmem<32>::BYTES);
       attr = true;
     }
-    tc::k_sketch_tc<32><<<grid, 192, tc::SketchSmem<32>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status);
+    DP2_COUNTED(tc::k_sketch_tc<32><<<grid, 192, tc::SketchSmem<32>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status));
   } else {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(tc::k_sketch_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SketchSmem<64>::BYTES);
       attr = true;
     }
-    tc::k_sketch_tc<64><<<grid, 192, tc::SketchSmem<64>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status);
+    DP2_COUNTED(tc::k_sketch_tc<64><<<grid, 192, tc::SketchSmem<64>::BYTES, s>>>(mx, mo, N, J, LP, Y, bf ? 1 : 0, status));
   }
   return true;
 }
@@ -1039,8 +1046,8 @@ bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N,
                            tc::SegSmem<32>::BYTES);
       attr = true;
     }
-    tc::k_sketch_seg_tc<32><<<grid, 192, tc::SegSmem<32>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
-                                                                      bf ? 1 : 0, status);
+    DP2_COUNTED(tc::k_sketch_seg_tc<32><<<grid, 192, tc::SegSmem<32>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
+                                                                      bf ? 1 : 0, status));
   } else {
     static bool attr = false;
     if (!attr) {
@@ -1048,8 +1055,8 @@ bool launch_sketch_seg_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N,
                            tc::SegSmem<64>::BYTES);
       attr = true;
     }
-    tc::k_sketch_seg_tc<64><<<grid, 192, tc::SegSmem<64>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
-                                                                      bf ? 1 : 0, status);
+    DP2_COUNTED(tc::k_sketch_seg_tc<64><<<grid, 192, tc::SegSmem<64>::BYTES, s>>>(mx, mm, d_off, d_toff, K, J, LP, U,
+                                                                      bf ? 1 : 0, status));
   }
   return true;
 }
@@ -1114,8 +1121,8 @@ static void project_launch(const CUtensorMap& mx, const CUtensorMap& mq, int gri
     cudaFuncSetAttribute(tc::k_project_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<NS>::BYTES);
     attr = true;
   }
-  tc::k_project_tc<NS><<<grid, tc::PJ_THREADS, tc::ProjSmem<NS>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, OFF,
-                                                                           B1, xpart, nJb, bf, qs, lptr, items, status);
+  DP2_COUNTED(tc::k_project_tc<NS><<<grid, tc::PJ_THREADS, tc::ProjSmem<NS>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, OFF,
+                                                                           B1, xpart, nJb, bf, qs, lptr, items, status));
 }
 
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
@@ -1145,14 +1152,14 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
 
 void launch_omega_t16(const float* om_pad, int Jpad, int LP, int LPN, dpar2_dtype dt, void* out, cudaStream_t s) {
   const int64_t n = (int64_t)LPN * Jpad;
-  tc::k_omega_t16<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(om_pad, Jpad, LP, LPN,
-                                                                                     dt == DPAR2_BF16 ? 1 : 0, out);
+  DP2_COUNTED(tc::k_omega_t16<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(om_pad, Jpad, LP, LPN,
+                                                                                     dt == DPAR2_BF16 ? 1 : 0, out));
 }
 
 void launch_qsplit(const float* Q, int LP, int NS, int OFF, const int64_t* d_off, const int64_t* d_poff, int K,
                    int64_t Npad, int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s) {
   dim3 grid((unsigned)std::max<int64_t>(1, (maxPad + 127) / 128), K);
-  tc::k_qsplit<<<grid, 128, 0, s>>>(Q, LP, NS, OFF, d_off, d_poff, K, Npad, dt == DPAR2_BF16 ? 1 : 0, out);
+  DP2_COUNTED(tc::k_qsplit<<<grid, 128, 0, s>>>(Q, LP, NS, OFF, d_off, d_poff, K, Npad, dt == DPAR2_BF16 ? 1 : 0, out));
 }
 
 }  // namespace dp2

@@ -206,6 +206,101 @@ __device__ void block_spd_pinv(const double* A, OutT* Inv, double* L, double* V,
   block_spd_finish<T, OutT>(ok != 0, A, Inv, L, V, n, sh, status);
 }
 
+// Inv <- A^-1 for symmetric positive definite A (n x n, FP64), to FP64
+// accuracy, by the whole block.  Warp 0 factors A in FP32 (Cholesky and
+// triangular inverse, fast on the FP32 pipes); X0 = R^-1 R^-T then takes
+// Newton steps X <- X + X (I - A X), the residual E = I - A X formed in FP64
+// and the correction X E in FP32 (E is small, so X E needs only a few
+// digits).  Each step squares the residual: from max|E0| <= 0.1 (condition
+// numbers up to ~1e5 for n ~ 10) at most five steps reach max|E| <= 1e-12 or
+// the FP64 rounding floor (~n kappa 1e-16), and the result is accepted when
+// max|E| <= 1e-9.  Otherwise -- an FP32 pivot failed, the start was too far
+// off, or the steps stalled -- the FP64 Cholesky path (block_spd_finish) runs
+// instead.  Worth it for small n: the Newton products cost 2 n^3 FP64
+// operations per step against the factorisation's n^3 / 3, but their FP64
+// chains are n long where the Cholesky's are n rsqrt-and-update steps long.
+// sh: spd_pinv_words(n) doubles (the factorisations), work:
+// refined_work_words(n) doubles, both shared memory; L, V: n x n global work
+// arrays of the pseudoinverse fallback.
+__host__ __device__ inline size_t refined_work_words(int n) { return 2 * (size_t)n * n + 40; }
+
+__device__ inline void block_spd_inv_refined(const double* A, double* Inv, double* L, double* V, int n, double* sh,
+                                             double* work, int* status) {
+  float* fsh = reinterpret_cast<float*>(sh);
+  double* E = work;
+  double* X = E + n * n;
+  double* red = X + n * n;  // one maximum per warp
+  __shared__ int ok;
+  const int T = blockDim.x, nn = n * n, nwarp = (T + 31) / 32;
+  if (threadIdx.x < 32) {
+    const bool f = warp_spd_factor<float>(A, n, fsh);
+    if (threadIdx.x == 0) ok = f;
+  }
+  __syncthreads();
+  bool good = ok != 0 && nn <= 4 * T;
+  if (good) {
+    const float* Mi = fsh + nn;
+    for (int e = threadIdx.x; e < nn; e += T) {  // X0 = Mi Mi^T
+      const int a = e / n, b = e - a * n;
+      float s = 0.f;
+      for (int i = max(a, b); i < n; ++i) s = fmaf(Mi[a * n + i], Mi[b * n + i], s);
+      X[e] = (double)s;
+    }
+    __syncthreads();
+    for (int step = 0;; ++step) {
+      double m = 0.0;
+      for (int e = threadIdx.x; e < nn; e += T) {  // E = I - A X (FP64)
+        const int a = e / n, b = e - a * n;
+        double s = (a == b) ? 1.0 : 0.0;
+        for (int i = 0; i < n; ++i) s = fma(-A[a * n + i], X[i * n + b], s);
+        E[e] = s;
+        m = fmax(m, fabs(s));
+      }
+      m = warp_max(m);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+      __syncthreads();
+      double mm = 0.0;
+      for (int w = 0; w < nwarp; ++w) mm = fmax(mm, red[w]);
+      if (step == 0 && !(mm <= 0.1)) {
+        good = false;
+        break;
+      }
+      if (mm <= 1e-12 || step == 5) {
+        good = mm <= 1e-9;
+        break;
+      }
+      double xn[4];  // X + X E for this thread's entries (n^2 <= 4 T)
+      int q = 0;
+      for (int e = threadIdx.x; e < nn; e += T, ++q) {
+        const int a = e / n, b = e - a * n;
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s = fmaf((float)X[a * n + i], (float)E[i * n + b], s);
+        xn[q] = X[e] + (double)s;
+      }
+      __syncthreads();  // every thread has read X, E and red
+      q = 0;
+      for (int e = threadIdx.x; e < nn; e += T, ++q) X[e] = xn[q];
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (good) {
+    for (int e = threadIdx.x; e < nn; e += T) {  // symmetric part
+      const int a = e / n, b = e - a * n;
+      Inv[e] = 0.5 * (X[a * n + b] + X[b * n + a]);
+    }
+    __syncthreads();
+    return;
+  }
+  // FP64 Cholesky (or the eigen pseudoinverse) on the same shared workspace
+  if (threadIdx.x < 32) {
+    const bool f = warp_spd_factor<double>(A, n, sh);
+    if (threadIdx.x == 0) ok = f;
+  }
+  __syncthreads();
+  block_spd_finish<double, double>(ok != 0, A, Inv, L, V, n, sh, status);
+}
+
 // Scale factors 1 / ||column r|| for the R columns whose squared norms are
 // n2[r] (1 for a zero column); flags a non-finite norm.
 __device__ inline double inv_norm(double n2, int* status) {
@@ -221,25 +316,27 @@ __device__ inline double inv_norm(double n2, int* status) {
 // what it writes, so the factorisation leaves the iteration's critical path.
 // sh: pre_solve_words(R, blockDim.x) doubles of shared memory.
 __host__ __device__ inline size_t pre_solve_words(int R, int T) {
-  return spd_pinv_words(R) + 2 * (size_t)R * R + 2 + T;
+  return spd_pinv_words(R) + 3 * (size_t)R * R + 2 + T;
 }
 __device__ inline void pre_solve(const PreSolve& p, double* sh) {
   const int R = p.R, RR = R * R, T = blockDim.x;
   double* fac = sh;
   double* Gm = sh + spd_pinv_words(R);
   double* W3 = Gm + RR;
-  double* red = W3 + RR + 2;
+  double* red = W3 + 2 * RR + 2;  // W3: W^T W (hi, lo) and e (hi, lo)
   __shared__ int ok;
   const double* A = p.WtW;
   if (p.part3 && p.it > 0) {
-    par_reduce_load(p.part3, p.nparts, p.pstride, RR + 2, 0, T, red, W3);
+    par_reduce_load(p.part3, p.nparts, p.pstride, 2 * RR + 2, 0, T, red, W3);
     __syncthreads();
-    par_reduce_combine(RR + 2, 0, T, red, W3);
+    par_reduce_combine(2 * RR + 2, 0, T, red, W3);
+    __syncthreads();
+    for (int e = threadIdx.x; e < RR; e += T) W3[e] += W3[RR + e];
     __syncthreads();
     for (int e = threadIdx.x; e < RR + 1; e += T) {
       if (e < RR) p.WtW[e] = W3[e];
       else {
-        const double v = W3[RR] + W3[RR + 1];
+        const double v = W3[2 * RR] + W3[2 * RR + 1];
         p.loss[p.it - 1] = v;
         if (!isfinite(v)) set_status(p.status, ST_NONFINITE);
       }

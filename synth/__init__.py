@@ -14,5 +14,6 @@ from .generators import (  # noqa: F401
     plain_parafac2,
     spectrogram_like,
     skewed_series,
+    tenrand,
     workload,
 )

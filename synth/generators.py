@@ -45,6 +45,9 @@ WORKLOADS = {
     "ranksweep": Workload("ranksweep", 8455, 32, 174, 2049, 10, 10, "uniform", "spectrogram"),
     # learned-sketch training set: 2000 FMA-shaped slices, R=20.
     "learned": Workload("learned", 2000, 100, 704, 2049, 20, 10, "uniform", "spectrogram"),
+    # the paper's synthetic scalability tensors (Sec. IV-A/IV-C): regular I x J x K,
+    # uniform on [0, 1); sizes from 1000^3 to 2000 x 2000 x 4000.
+    "tenrand": Workload("tenrand", 4000, 2000, 2000, 2000, 10, 10, "uniform", "tenrand"),
 }
 
 
@@ -235,4 +238,23 @@ def skewed_series(K=4742, Imin=100, Imax=7883, J=88, R=20, seed=1003, phi=0.95, 
         sd = s.std(0, keepdim=True)
         s = (s - mu) / torch.where(sd > 0, sd, torch.ones_like(sd))
         X[off[k]:off[k + 1], :J] = s.to(out_dtype)
+    return dict(X=X, offsets=offsets, ld=ld)
+
+
+def tenrand(I=2000, J=2000, K=4000, seed=1006, device="cpu", out_dtype=torch.float32, ld=None,
+            chunk_rows=1 << 20):
+    """The synthetic tensors of the paper's scalability experiments (Sec. IV-A,
+    "Synthetic Data"; Tensor Toolbox's tenrand(I, J, K)): entries drawn
+    independently and uniformly from [0, 1), slice k = X(:, :, k), every slice
+    I x J.  Written chunk by chunk into a (K I) x ld buffer of ``out_dtype``
+    (ld >= J, columns >= J zero) straight from the device generator, so a
+    32 GB BF16 tensor needs no FP32 copy.  Returns dict(X, offsets, ld)."""
+    offsets = torch.arange(K + 1, dtype=torch.int64) * I
+    N = K * I
+    ld = J if ld is None else ld
+    X = torch.zeros(N, ld, device=device, dtype=out_dtype)
+    g = _gen(device, seed)
+    for r0 in range(0, N, chunk_rows):
+        r1 = min(N, r0 + chunk_rows)
+        X[r0:r1, :J] = torch.rand(r1 - r0, J, generator=g, device=device).to(out_dtype)
     return dict(X=X, offsets=offsets, ld=ld)

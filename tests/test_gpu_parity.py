@@ -221,9 +221,10 @@ def test_fit_matches_oracle(api, ctx, dtype):
     o = [int(v) for v in d["offsets"]]
     rec_g = [U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T for k in range(64)]
     rec_o = [ref["U"][k] @ np.diag(ref["W"][k]) @ ref["V"].T for k in range(64)]
-    # the final model's relative error is 1 - fitness: the fitness bar (1e-4) applies
+    # the final model's relative error is 1 - fitness: the fitness bar (1e-4)
+    # applies; element-wise agreement of the model is tested from a
+    # well-conditioned start below
     assert abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)) <= 1e-4
-    assert np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(rec_g, rec_o)) / sum(np.sum(x * x) for x in Xs)) <= 1e-2
     # fitness through the identity equals the direct definition on the GPU
     # factors, up to the FP32 orthonormality of A_k (~1e-5)
     assert abs(res.fitness - (1 - rel_sq_err(Xs, rec_g))) <= 3e-5
@@ -233,6 +234,36 @@ def test_fit_matches_oracle(api, ctx, dtype):
     for k in range(0, 64, 7):
         Q = A[o[k]:o[k + 1]] @ Up[k]
         np.testing.assert_allclose(Q.T @ Q, np.eye(10), atol=5e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fit_from_well_conditioned_start_matches_oracle_elementwise(api, ctx, dtype):
+    """From V_0 near the generating V the Gram-Hadamard systems stay well
+    conditioned (no first-step amplification of FP32 rounding), so the GPU
+    iterates track the FP64 oracle's to FP32 level: relative reconstruction
+    errors agree to 1e-5 and the final models element-wise to 1e-4 of ||X||."""
+    d = synth.plain_parafac2(K=64, Imin=50, Imax=200, J=64, R=10, seed=1001)
+    comp, Xs, om, om2 = _run(api, ctx, d, 64, 10, 10, dtype)
+    V0 = _near_v0(d, 64, 10)
+    res = ctx.fit(comp, max_iter=32, V0=V0, want_U=True)
+    ref = od.dpar2_als(od.compress(Xs, 10, om, om2), V0.double().cpu().numpy(), max_iter=32)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    o = [int(v) for v in d["offsets"]]
+    U = res.U.double().cpu().numpy()
+    W = res.W.double().cpu().numpy()
+    V = res.V.double().cpu().numpy()
+    rec_g = [U[o[k]:o[k + 1]] @ np.diag(W[k]) @ V.T for k in range(64)]
+    rec_o = [ref["U"][k] @ np.diag(ref["W"][k]) @ ref["V"].T for k in range(64)]
+    f_or = od.fitness(Xs, ref["U"], ref["W"], ref["V"])
+    m = {"loss_delta": float(np.max(np.abs(np.array(res.losses) - np.array(ref["losses"])))) / tot,
+         "fitness_delta": abs(res.fitness - f_or),
+         "err_delta": abs(rel_sq_err(Xs, rec_g) - rel_sq_err(Xs, rec_o)),
+         "dist": float(np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(rec_g, rec_o)) / tot))}
+    print(f"\nwell-conditioned start {dtype}: " + " ".join(f"{k}={v:.3e}" for k, v in m.items()))
+    assert m["loss_delta"] <= 1e-5
+    assert m["fitness_delta"] <= 1e-5
+    assert m["err_delta"] <= 1e-5
+    assert m["dist"] <= 1e-4
 
 
 # (R, p): ranks past one warp's width (R^2 partial sums beyond the reducing
@@ -341,6 +372,7 @@ def test_reconstruct_error_streamed_equals_identity_and_direct(api, ctx, dtype):
     direct = od.squared_error(Xs, [U[o[k]:o[k + 1]] for k in range(40)], res.W.double().cpu().numpy(),
                               res.V.double().cpu().numpy())
     tot = sum(float(np.sum(x * x)) for x in Xs)
+    print(f"\nstreamed {dtype}: sq_identity {sq_i:.6f} sq_streamed {sq_s:.6f} direct {direct:.6f} total {tot:.3f}")
     assert abs(sq_s - direct) <= 1e-6 * tot
     assert abs(sq_i - sq_s) <= 1e-6 * tot
     assert abs(fit_s - (1.0 - direct / tot)) <= 1e-6
