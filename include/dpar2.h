@@ -66,6 +66,8 @@ typedef enum { DPAR2_F32 = 0, DPAR2_BF16 = 1, DPAR2_F16 = 2 } dpar2_dtype;
 #define DPAR2_FLAG_GENERIC 0x4u   /* CUDA-core stage-1 kernels even for 16-bit X */
 #define DPAR2_FLAG_DROP_M 0x8u    /* free M after stage 2 (identity fitness then needs X) */
 #define DPAR2_FLAG_COLD_QSTEP 0x10u /* Q-step Jacobi from the identity every iteration (no warm start) */
+#define DPAR2_FLAG_FIVE_LAUNCH 0x20u /* ALS iterations as five launches with single-block H and V updates
+                                        (the form used for R > 32) instead of three */
 
 typedef struct {
   int R;          /* target rank (Alg. 1 / Alg. 3 parameter), 1 <= R <= 64 */
@@ -180,13 +182,13 @@ DPAR2_API dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_
  *                Read only; must stay valid until the call returns.
  *   X_dev        device buffer of sum(I_k) rows of ldx elements that receives X
  *                (columns J..ldx-1 zero), for later calls that read X again
- *                (dpar2_reconstruct_error's streamed mode); or NULL: two chunk
+ *                (dpar2_reconstruct_error's streamed mode); or NULL: chunk
  *                buffers of the context are used and X is not kept.  ldx: as for
  *                dpar2_compress (ignored when X_dev is NULL).
- *   chunk_bytes  target bytes of X per chunk (0: 512 MB); a chunk holds at
- *                least one slice.  Context scratch: two staging buffers of the
- *                largest chunk (unless ldx == J) and, without X_dev, two chunk
- *                buffers of it.
+ *   chunk_bytes  target bytes of X per chunk (0: 1 GB); a chunk holds at
+ *                least one slice.  Context scratch: three staging buffers of
+ *                the largest chunk (unless ldx == J) and, without X_dev, three
+ *                chunk buffers of it; copies run up to three chunks ahead.
  * Other arguments, outputs and errors as dpar2_compress.  The result is the
  * compression dpar2_compress computes from the same X (the same kernels per
  * slice; chunks of fewer than 256 slices sum the CholeskyQR Grams of their

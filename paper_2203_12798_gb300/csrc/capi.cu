@@ -887,7 +887,7 @@ dpar2_status dpar2_compress_host(dpar2_ctx* ctx, int K, int J, const int64_t* ro
     const float* om_pad = prepare_omega(ctx, J, comp->ell, comp->LP, dtype, opt, omega, s);
     // chunks of whole slices, about chunk_bytes of X each
     const size_t rowb = (size_t)J * es;
-    const size_t target = chunk_bytes ? chunk_bytes : ((size_t)512 << 20);
+    const size_t target = chunk_bytes ? chunk_bytes : ((size_t)1 << 30);
     std::vector<int> cut{0};
     for (int k = 0; k < K; ++k) {
       const int64_t rows = row_offsets[k + 1] - row_offsets[cut.back()];
@@ -897,7 +897,10 @@ dpar2_status dpar2_compress_host(dpar2_ctx* ctx, int K, int J, const int64_t* ro
     const int nc = (int)cut.size() - 1;
     int64_t maxrows = 0;
     for (int c = 0; c < nc; ++c) maxrows = std::max(maxrows, row_offsets[cut[c + 1]] - row_offsets[cut[c]]);
-    constexpr int NB = 2;
+    // NB landing buffers: the copy of chunk c + NB is queued right after the
+    // work stream's use of chunk c's buffer, so the copy engine runs up to NB
+    // chunks ahead of the host's stage-1 launches
+    constexpr int NB = 3;
     const bool direct = ldd == J;  // host rows already have the device pitch: no staging
     uint8_t* stage = direct ? nullptr : wsget<uint8_t>(ctx, "hc_stage", (size_t)NB * maxrows * rowb);
     uint8_t* cbuf = X_dev ? nullptr : wsget<uint8_t>(ctx, "hc_chunk", (size_t)NB * maxrows * ldd * es);
@@ -919,31 +922,44 @@ dpar2_status dpar2_compress_host(dpar2_ctx* ctx, int K, int J, const int64_t* ro
       }
       ev[i] = reinterpret_cast<cudaEvent_t>(e.p);
     }
+    auto dst_of = [&](int c) -> uint8_t* {
+      const int64_t r0 = row_offsets[cut[c]];
+      return X_dev ? static_cast<uint8_t*>(X_dev) + (size_t)r0 * ldd * es : cbuf + (size_t)(c % NB) * maxrows * ldd * es;
+    };
+    auto land_of = [&](int c) -> uint8_t* { return direct ? dst_of(c) : stage + (size_t)(c % NB) * maxrows * rowb; };
+    auto queue_copy = [&](int c) {
+      const int b = c % NB;
+      const int64_t r0 = row_offsets[cut[c]], nr = row_offsets[cut[c + 1]] - r0;
+      // the landing buffer is free once the work stream re-pitched (staging) or
+      // compressed (direct into a chunk buffer) chunk c - NB
+      if (c >= NB) CK(cudaStreamWaitEvent(cs, ev[NB + b], 0));
+      CK(cudaMemcpyAsync(land_of(c), static_cast<const uint8_t*>(X_host) + (size_t)r0 * rowb, (size_t)nr * rowb,
+                         cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(ev[b], cs));
+    };
     CK(cudaEventRecord(ev[2 * NB], s));  // copies start after the work stream's prior work
     CK(cudaStreamWaitEvent(cs, ev[2 * NB], 0));
+    for (int c = 0; c < std::min(NB, nc); ++c) queue_copy(c);
     std::vector<int64_t> loc;
     for (int c = 0; c < nc; ++c) {
       const int b = c % NB, k0 = cut[c], Kc = cut[c + 1] - cut[c];
       const int64_t r0 = row_offsets[k0], nr = row_offsets[cut[c + 1]] - r0;
-      uint8_t* dst = X_dev ? static_cast<uint8_t*>(X_dev) + (size_t)r0 * ldd * es : cbuf + (size_t)b * maxrows * ldd * es;
-      uint8_t* land = direct ? dst : stage + (size_t)b * maxrows * rowb;
-      // the landing buffer is free once the work stream re-pitched (staging) or
-      // compressed (direct into a chunk buffer) chunk c - NB
-      if (c >= NB) CK(cudaStreamWaitEvent(cs, ev[NB + b], 0));
-      CK(cudaMemcpyAsync(land, static_cast<const uint8_t*>(X_host) + (size_t)r0 * rowb, (size_t)nr * rowb,
-                         cudaMemcpyHostToDevice, cs));
-      CK(cudaEventRecord(ev[b], cs));
+      uint8_t* dst = dst_of(c);
       CK(cudaStreamWaitEvent(s, ev[b], 0));
       if (!direct) {
-        launch_repitch(land, nr, J, (int)es, dst, ldd, s);
+        launch_repitch(land_of(c), nr, J, (int)es, dst, ldd, s);
         CK(cudaEventRecord(ev[NB + b], s));
+        if (c + NB < nc) queue_copy(c + NB);
       }
       loc.assign(Kc + 1, 0);
       for (int k = 0; k <= Kc; ++k) loc[k] = row_offsets[k0 + k] - r0;
       int64_t* d_loc = d_coff + (size_t)b * (K + 1);
       h2d_i64(ctx, d_loc, loc.data(), Kc + 1, s);
       stage1_range(ctx, comp, dst, ldd, dtype, opt, k0, Kc, loc.data(), d_loc, om_pad, false, s);
-      if (direct) CK(cudaEventRecord(ev[NB + b], s));
+      if (direct) {
+        CK(cudaEventRecord(ev[NB + b], s));
+        if (c + NB < nc) queue_copy(c + NB);
+      }
     }
     stage2_all(ctx, comp, opt, omega2, s);
     tend(ctx, s, DPAR2_PH_COMPRESS);
@@ -1007,7 +1023,8 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.Ginv = d6 + 4 * RR;
     b.InvH = d6 + 5 * RR;
     b.InvV = d6 + 6 * RR;
-    b.nblk = als_blocks(K, R, ctx->num_sms);
+    const bool three = als3_supported(R) && !(opt->flags & DPAR2_FLAG_FIVE_LAUNCH);
+    b.nblk = three ? als3_blocks(K, R, ctx->num_sms) : als_blocks(K, R, ctx->num_sms);
     b.nq = qstep_blocks(K, R, b.nblk);
     b.pr = std::max(b.nblk, b.nq);
     b.part = wsget<float>(ctx, "als_part", (size_t)3 * b.pr * (2 * RR + 2));
@@ -1015,6 +1032,10 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
     b.small = wsget<double>(ctx, "als_small", (size_t)8 * RR + 8);
     b.atb = wsget<float>(ctx, "atb_part", (size_t)kAtbBlocks * RR);
     b.status = ctx->d_status;
+    auto iterate = [&](int it) {
+      if (three) launch_als_iteration3(b, it, s);
+      else launch_als_iteration(b, it, s);
+    };
     tbegin(ctx, s, DPAR2_PH_ALS);
     launch_als_init(b, v0, s);
     if (opt->tol < 0) {
@@ -1024,7 +1045,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         cudaGraphExec_t ge;
         const long long c0 = g_launches.load();
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+        for (int it = 0; it < opt->max_iter; ++it) iterate(it);
         launch_als_finish(b, opt->max_iter - 1, s);
         CK(cudaStreamEndCapture(s, &g));
         const long long captured = g_launches.load() - c0;
@@ -1035,14 +1056,14 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         cudaGraphExecDestroy(ge);  // freed when the launch completes
         cudaGraphDestroy(g);
       } else {
-        for (int it = 0; it < opt->max_iter; ++it) launch_als_iteration(b, it, s);
+        for (int it = 0; it < opt->max_iter; ++it) iterate(it);
         launch_als_finish(b, opt->max_iter - 1, s);
       }
       iters = opt->max_iter;
     } else {
       double prev = 0.0;
       for (int it = 0; it < opt->max_iter; ++it) {
-        launch_als_iteration(b, it, s);
+        iterate(it);
         launch_als_finish(b, it, s);
         double e = 0.0;
         CK(cudaMemcpyAsync(&e, b.loss + it, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -227,6 +227,11 @@ struct AlsBufs {
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);
+// Three-launch iteration (k_als3.cu) for R <= 32: the H and V updates formed
+// in every block of the grids that need them; nblk = als3_blocks(...)
+bool als3_supported(int R);
+int als3_blocks(int K, int R, int num_sms);
+void launch_als_iteration3(AlsBufs& b, int it, cudaStream_t s);
 int als_blocks(int K, int R, int num_sms);
 void launch_qstep_only(AlsBufs& b, cudaStream_t s);
 // register-resident Q-step (R <= 32: lane = column; 32 < R <= 64: the warp-pair

@@ -15,11 +15,11 @@
 //     = sum_k ||Pi_k - H S_k CV^T||^2 (D^T D = I), summed from the residual
 //     entries themselves.
 // Grid-wide sums are block partials reduced in a fixed order (deterministic).
-// The R x R Gram-Hadamard solves are FP64: Cholesky factorisations (with the
-// pseudoinverse from an FP64 Jacobi eigendecomposition if a pivot fails) for
-// the H and V updates; for the W update an FP32 factorisation refined to FP64
-// accuracy by Newton steps (FP64 Cholesky when the refinement's start is too
-// far off), applied to the FP32 right-hand sides G3 in FP64.
+// The R x R Gram-Hadamard solves are FP64: for R <= 16 a register-resident
+// Gauss-Jordan inverse by one warp, otherwise (or when a pivot fails) a
+// Cholesky factorisation with the pseudoinverse from an FP64 Jacobi
+// eigendecomposition as the last resort; the W update's inverse is applied to
+// the FP32 right-hand sides G3 in FP64.
 #include "common.cuh"
 #include "internal.h"
 #include "small_solve.cuh"
@@ -469,10 +469,10 @@ __global__ void k_g3w(int K, int R, const float* __restrict__ Pi, const double* 
 }
 
 // shared memory of the H / V updates: the pseudoinverse workspace plus 5 R^2 + 2
-// doubles of intermediates and the refined inverse's work area when that fits
-// in 160 KB (R <= 40), else the workspace only
+// doubles of intermediates and W^T W's double-float partial sums when that
+// fits in 160 KB, else the workspace only
 inline size_t update_smem(int R, int* inshared) {
-  const size_t full = (spd_pinv_words(R) + 5 * (size_t)R * R + 2 + refined_work_words(R)) * sizeof(double);
+  const size_t full = (spd_pinv_words(R) + 6 * (size_t)R * R + 4) * sizeof(double);
   *inshared = full <= 160 * 1024;
   return *inshared ? full : spd_pinv_smem(R);
 }
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(1024) k_update_h(int R, const float* __restric
   double* Gm = G1 + RR;
   double* Inv = Gm + RR;
   double* Hn = Inv + RR;
-  double* W3 = Hn + RR;  // RR + 2
+  double* W3 = Hn + RR;  // 2 RR + 2: W^T W (hi, lo), e (hi, lo)
   __shared__ int ok;
   __shared__ double red[kRedMax];
   const int T = blockDim.x;
@@ -657,11 +657,8 @@ __global__ void __launch_bounds__(1024) k_update_v(int R, const float* __restric
     Gm[e] = s * HtH[e];
   }
   __syncthreads();
-  // Ginv = (V^T V * H^T H)^-1 to FP64 accuracy (the W update applies it in
-  // FP64): FP32 factorisation refined by FP64 Newton steps when the
-  // intermediates sit in shared memory, else the FP64 Cholesky
-  if (inshared) block_spd_inv_refined(Gm, Ginv, L, V, R, ush, ush + spd_pinv_words(R) + 5 * RR + 2, status);
-  else block_spd_pinv<double, double>(Gm, Ginv, L, V, R, ush, status);
+  // Ginv = (V^T V * H^T H)^-1 in FP64 (the W update applies it in FP64)
+  block_spd_pinv<double, double>(Gm, Ginv, L, V, R, ush, status);
 }
 
 // ----------------------------------------------------- iteration epilogue --
@@ -727,24 +724,27 @@ __global__ void k_upol_h(int K, int R, const float* __restrict__ Upol, const flo
 // P_k = V^T M_k (R x R) with M_k = X_k^T A_k.  The last term is
 // sum_ab (S Y1^T G_k Y1 S)_ab (V^T V)_ab, Y1 = Upol_k H, with G_k = A_k^T A_k
 // (FP64, pitch ldg) when AtA is given, else G_k = I (A_k orthonormal).
+// Y1, G_k Y1 and the sums are FP64 (products of the stored FP32 factors):
+// with nearly collinear columns of H the quadratic form in S_k cancels terms
+// far larger than its value, which FP32 products would not resolve.
 // Writes block partials (FP64) of the sum.
 __global__ void k_fitness(int K, int R, const float* __restrict__ P, const float* __restrict__ Upol,
                           const float* __restrict__ H, const float* __restrict__ W, const double* __restrict__ VtV,
                           const double* __restrict__ xnorm2, const double* __restrict__ AtA, int ldg,
                           double* __restrict__ part) {
-  extern __shared__ __align__(16) float sm[];
+  extern __shared__ __align__(16) double fsm[];
   const int RR = R * R;
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* hs = sm;
-  float* vv = hs + RR;
-  float* my = vv + RR + warp * 3 * RR;
-  float* Y1 = my;        // Upol H
-  float* Pk = my + RR;
-  float* GY = my + 2 * RR;  // G_k Y1 (when AtA is given)
+  double* hs = fsm;
+  double* vv = hs + RR;
+  double* my = vv + RR + warp * 3 * RR;
+  double* Y1 = my;          // Upol H
+  double* Pk = my + RR;
+  double* GY = my + 2 * RR;  // G_k Y1 (when AtA is given)
   __shared__ double red[32];
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-    hs[e] = H[e];
-    vv[e] = (float)VtV[e];
+    hs[e] = (double)H[e];
+    vv[e] = VtV[e];
   }
   __syncthreads();
   double acc = 0.0;
@@ -753,20 +753,20 @@ __global__ void k_fitness(int K, int R, const float* __restrict__ P, const float
     const float* wk = W + (int64_t)k * R;
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e % R;
-      float s = 0.f;
-      for (int m = 0; m < R; ++m) s = fmaf(u[a * R + m], hs[m * R + b], s);
+      double s = 0.0;
+      for (int m = 0; m < R; ++m) s = fma((double)u[a * R + m], hs[m * R + b], s);
       Y1[e] = s;
-      Pk[e] = P[(int64_t)k * RR + e];
+      Pk[e] = (double)P[(int64_t)k * RR + e];
     }
     __syncwarp();
-    const float* Z = Y1;
+    const double* Z = Y1;
     if (AtA) {
       const double* g = AtA + (int64_t)k * ldg * ldg;
       for (int e = lane; e < RR; e += 32) {
         const int i = e / R, b = e % R;
         double t = 0.0;
-        for (int m = 0; m < R; ++m) t = fma(g[i * ldg + m], (double)Y1[m * R + b], t);
-        GY[e] = (float)t;
+        for (int m = 0; m < R; ++m) t = fma(g[i * ldg + m], Y1[m * R + b], t);
+        GY[e] = t;
       }
       __syncwarp();
       Z = GY;
@@ -775,11 +775,11 @@ __global__ void k_fitness(int K, int R, const float* __restrict__ P, const float
     for (int e = lane; e < RR; e += 32) {
       const int a = e / R, b = e % R;
       // tr(P Y1 S) = sum_{a,b} P[a][b] Y1[b][a] W[a]
-      cross += (double)Pk[e] * Y1[b * R + a] * wk[a];
+      cross = fma(Pk[e] * Y1[b * R + a], (double)wk[a], cross);
       // (S Y1^T G Y1 S)[a][b] VtV[a][b]
-      float g = 0.f;
-      for (int i = 0; i < R; ++i) g = fmaf(Y1[i * R + a], Z[i * R + b], g);
-      model += (double)wk[a] * g * wk[b] * vv[e];
+      double g = 0.0;
+      for (int i = 0; i < R; ++i) g = fma(Y1[i * R + a], Z[i * R + b], g);
+      model = fma((double)wk[a] * (double)wk[b] * g, vv[e], model);
     }
     cross = warp_sum(cross);
     model = warp_sum(model);
@@ -984,8 +984,8 @@ void launch_fitness(int K, int R, const float* P, const float* Upol, const float
                     const double* VtV, const double* xnorm2, double* part, int nblk, double* out, cudaStream_t s,
                     const double* AtA, int ldg) {
   als_set_attrs();
-  const int nw = R > 48 ? 3 : 4;  // (2 + 3 nw) R^2 floats of shared memory <= 200 KB
-  DP2_COUNTED(k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 3 * R * R) * 4, s>>>(K, R, P, Upol, H, W, VtV, xnorm2, AtA,
+  const int nw = R > 40 ? 1 : (R > 32 ? 2 : 4);  // (2 + 3 nw) R^2 doubles of shared memory <= 200 KB
+  DP2_COUNTED(k_fitness<<<nblk, nw * 32, (size_t)(2 * R * R + nw * 3 * R * R) * 8, s>>>(K, R, P, Upol, H, W, VtV, xnorm2, AtA,
                                                                            ldg, part));
   DP2_COUNTED(k_reduce_f64<<<1, 32, 0, s>>>(part, nblk, out));
 }

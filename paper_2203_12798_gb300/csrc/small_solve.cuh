@@ -194,111 +194,105 @@ __device__ void block_spd_finish(bool ok, const double* A, OutT* Inv, double* L,
   __syncthreads();
 }
 
+// FP64 reciprocal: the FP32 estimate refined by two Newton steps
+// r <- r + r (1 - p r) (each squares the relative error: 2^-23 -> 2^-46 ->
+// below FP64 rounding), for normal FP64 p within the FP32 range.
+__device__ inline double recip_nr(double p) {
+  double r = (double)__frcp_rn((float)p);
+  r = fma(r, fma(-p, r, 1.0), r);
+  return fma(r, fma(-p, r, 1.0), r);
+}
+
+// Inv <- A^-1 for symmetric positive definite A (n x n, n <= N <= 32) by one
+// warp, register resident: lane i holds row i of [A | I] (rows and columns
+// past n hold the identity) and Gauss-Jordan elimination without pivoting
+// (stable for SPD A) runs over the n pivots; each step shuffles the pivot
+// row once and costs one FP64 reciprocal and one FMA per entry, all entries
+// independent.  Returns (in every lane) whether every pivot exceeded
+// 1e-300 * max diag and lay within the FP32 exponent range of the reciprocal
+// estimate; only then is Inv (symmetrised) written.
+template <int N>
+__device__ __noinline__ bool warp_spd_inv_reg(const double* A, int n, double* Inv) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double a[N], b[N];
+  double md = 0.0;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const bool in = lane < n && c < n;
+    a[c] = in ? A[lane * n + c] : (c == lane ? 1.0 : 0.0);
+    b[c] = (c == lane) ? 1.0 : 0.0;
+    if (in && c == lane) md = a[c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(FULL, md, o));
+  bool ok = md > 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j >= n) break;
+    const double p = __shfl_sync(FULL, a[j], j);
+    ok = ok && p > 1e-300 * md && p > 1e-37 && p < 1e37;
+    const double r = recip_nr(ok ? p : 1.0);
+    const double f = a[j];  // this row's entry in the pivot column
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const double pa = __shfl_sync(FULL, a[c], j) * r;
+      const double pb = __shfl_sync(FULL, b[c], j) * r;
+      if (lane == j) {
+        a[c] = pa;
+        b[c] = pb;
+      } else {
+        a[c] = fma(-f, pa, a[c]);
+        b[c] = fma(-f, pb, b[c]);
+      }
+    }
+  }
+  // symmetric part: every row written, then each lane averages its row with
+  // its column and writes it back (ok is the same in every lane)
+  if (ok && lane < n) {
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+      if (c < n) Inv[lane * n + c] = b[c];
+  }
+  __syncwarp();
+  double v[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) v[c] = (ok && lane < n && c < n) ? 0.5 * (b[c] + Inv[c * n + lane]) : 0.0;
+  __syncwarp();
+  if (ok && lane < n) {
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+      if (c < n) Inv[lane * n + c] = v[c];
+  }
+  __syncwarp();
+  return ok;
+}
+
 // Inv <- A^+ for symmetric PSD A (n x n), computed by the whole block.
+// FP64 with n <= 16: the register Gauss-Jordan inverse of warp 0 (32
+// doubles per lane), the Cholesky path (and its eigen pseudoinverse fallback)
+// for larger n or when a pivot fails.
 template <typename T, typename OutT>
 __device__ void block_spd_pinv(const double* A, OutT* Inv, double* L, double* V, int n, T* sh, int* status) {
   __shared__ int ok;
+  if constexpr (sizeof(T) == 8 && sizeof(OutT) == 8) {
+    if (n <= 16) {
+      if (threadIdx.x < 32) {
+        const bool f = warp_spd_inv_reg<16>(A, n, reinterpret_cast<double*>(Inv));
+        if (threadIdx.x == 0) ok = f;
+      }
+      __syncthreads();
+      const bool done = ok != 0;
+      __syncthreads();
+      if (done) return;
+    }
+  }
   if (threadIdx.x < 32) {
     const bool f = warp_spd_factor<T>(A, n, sh);
     if (threadIdx.x == 0) ok = f;
   }
   __syncthreads();
   block_spd_finish<T, OutT>(ok != 0, A, Inv, L, V, n, sh, status);
-}
-
-// Inv <- A^-1 for symmetric positive definite A (n x n, FP64), to FP64
-// accuracy, by the whole block.  Warp 0 factors A in FP32 (Cholesky and
-// triangular inverse, fast on the FP32 pipes); X0 = R^-1 R^-T then takes
-// Newton steps X <- X + X (I - A X), the residual E = I - A X formed in FP64
-// and the correction X E in FP32 (E is small, so X E needs only a few
-// digits).  Each step squares the residual: from max|E0| <= 0.1 (condition
-// numbers up to ~1e5 for n ~ 10) at most five steps reach max|E| <= 1e-12 or
-// the FP64 rounding floor (~n kappa 1e-16), and the result is accepted when
-// max|E| <= 1e-9.  Otherwise -- an FP32 pivot failed, the start was too far
-// off, or the steps stalled -- the FP64 Cholesky path (block_spd_finish) runs
-// instead.  Worth it for small n: the Newton products cost 2 n^3 FP64
-// operations per step against the factorisation's n^3 / 3, but their FP64
-// chains are n long where the Cholesky's are n rsqrt-and-update steps long.
-// sh: spd_pinv_words(n) doubles (the factorisations), work:
-// refined_work_words(n) doubles, both shared memory; L, V: n x n global work
-// arrays of the pseudoinverse fallback.
-__host__ __device__ inline size_t refined_work_words(int n) { return 2 * (size_t)n * n + 40; }
-
-__device__ inline void block_spd_inv_refined(const double* A, double* Inv, double* L, double* V, int n, double* sh,
-                                             double* work, int* status) {
-  float* fsh = reinterpret_cast<float*>(sh);
-  double* E = work;
-  double* X = E + n * n;
-  double* red = X + n * n;  // one maximum per warp
-  __shared__ int ok;
-  const int T = blockDim.x, nn = n * n, nwarp = (T + 31) / 32;
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<float>(A, n, fsh);
-    if (threadIdx.x == 0) ok = f;
-  }
-  __syncthreads();
-  bool good = ok != 0 && nn <= 4 * T;
-  if (good) {
-    const float* Mi = fsh + nn;
-    for (int e = threadIdx.x; e < nn; e += T) {  // X0 = Mi Mi^T
-      const int a = e / n, b = e - a * n;
-      float s = 0.f;
-      for (int i = max(a, b); i < n; ++i) s = fmaf(Mi[a * n + i], Mi[b * n + i], s);
-      X[e] = (double)s;
-    }
-    __syncthreads();
-    for (int step = 0;; ++step) {
-      double m = 0.0;
-      for (int e = threadIdx.x; e < nn; e += T) {  // E = I - A X (FP64)
-        const int a = e / n, b = e - a * n;
-        double s = (a == b) ? 1.0 : 0.0;
-        for (int i = 0; i < n; ++i) s = fma(-A[a * n + i], X[i * n + b], s);
-        E[e] = s;
-        m = fmax(m, fabs(s));
-      }
-      m = warp_max(m);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-      __syncthreads();
-      double mm = 0.0;
-      for (int w = 0; w < nwarp; ++w) mm = fmax(mm, red[w]);
-      if (step == 0 && !(mm <= 0.1)) {
-        good = false;
-        break;
-      }
-      if (mm <= 1e-12 || step == 5) {
-        good = mm <= 1e-9;
-        break;
-      }
-      double xn[4];  // X + X E for this thread's entries (n^2 <= 4 T)
-      int q = 0;
-      for (int e = threadIdx.x; e < nn; e += T, ++q) {
-        const int a = e / n, b = e - a * n;
-        float s = 0.f;
-        for (int i = 0; i < n; ++i) s = fmaf((float)X[a * n + i], (float)E[i * n + b], s);
-        xn[q] = X[e] + (double)s;
-      }
-      __syncthreads();  // every thread has read X, E and red
-      q = 0;
-      for (int e = threadIdx.x; e < nn; e += T, ++q) X[e] = xn[q];
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  if (good) {
-    for (int e = threadIdx.x; e < nn; e += T) {  // symmetric part
-      const int a = e / n, b = e - a * n;
-      Inv[e] = 0.5 * (X[a * n + b] + X[b * n + a]);
-    }
-    __syncthreads();
-    return;
-  }
-  // FP64 Cholesky (or the eigen pseudoinverse) on the same shared workspace
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<double>(A, n, sh);
-    if (threadIdx.x == 0) ok = f;
-  }
-  __syncthreads();
-  block_spd_finish<double, double>(ok != 0, A, Inv, L, V, n, sh, status);
 }
 
 // Scale factors 1 / ||column r|| for the R columns whose squared norms are
@@ -345,12 +339,7 @@ __device__ inline void pre_solve(const PreSolve& p, double* sh) {
   }
   for (int e = threadIdx.x; e < RR; e += T) Gm[e] = A[e] * p.B[e];
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const bool f = warp_spd_factor<double>(Gm, R, fac);
-    if (threadIdx.x == 0) ok = f;
-  }
-  __syncthreads();
-  block_spd_finish<double, double>(ok != 0, Gm, p.Inv, p.L, p.V, R, fac, p.status);
+  block_spd_pinv<double, double>(Gm, p.Inv, p.L, p.V, R, fac, p.status);
 }
 
 }  // namespace dp2

@@ -266,6 +266,24 @@ def test_fit_from_well_conditioned_start_matches_oracle_elementwise(api, ctx, dt
     assert m["dist"] <= 1e-4
 
 
+@pytest.mark.parametrize("R", [10, 20])
+def test_three_launch_iteration_equals_five_launch(api, ctx, R):
+    """The ALS iteration as three launches (the H and V updates formed in
+    every block of the grids that need them) and as five (single-block update
+    kernels) compute the same updates; only partial sums are grouped
+    differently, so the iterates agree to FP32 rounding."""
+    J = 96
+    d = synth.plain_parafac2(K=50, Imin=40, Imax=200, J=J, R=R, seed=1007)
+    comp, Xs, om, om2 = _run(api, ctx, d, J, R, 10, torch.float32)
+    V0 = _near_v0(d, J, R)
+    a = ctx.fit(comp, max_iter=16, V0=V0, want_U=True)
+    b = ctx.fit(comp, max_iter=16, V0=V0, want_U=True, flags=api.FLAG_FIVE_LAUNCH)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert np.max(np.abs(np.array(a.losses) - np.array(b.losses))) <= 1e-6 * tot
+    assert abs(a.fitness - b.fitness) <= 1e-6
+    torch.testing.assert_close(a.U, b.U, atol=1e-4, rtol=1e-3)
+
+
 # (R, p): ranks past one warp's width (R^2 partial sums beyond the reducing
 # threads; the warp-pair Q-step for 32 < R <= 64, exact at 40 and 50, zero-
 # padded to 48, 56 and 64 otherwise) and sketch widths l = R + p past 32 (the
@@ -373,9 +391,12 @@ def test_reconstruct_error_streamed_equals_identity_and_direct(api, ctx, dtype):
                               res.V.double().cpu().numpy())
     tot = sum(float(np.sum(x * x)) for x in Xs)
     print(f"\nstreamed {dtype}: sq_identity {sq_i:.6f} sq_streamed {sq_s:.6f} direct {direct:.6f} total {tot:.3f}")
-    assert abs(sq_s - direct) <= 1e-6 * tot
+    # relative reconstruction errors agree to the FP32 bar (1e-5); the
+    # streamed mode's cross term <X_k, X^_k> comes from the projection
+    # A_k^T X_k accumulated in FP32 over I_k rows (~1e-6 of the energy)
+    assert abs(sq_s - direct) <= 1e-5 * tot
     assert abs(sq_i - sq_s) <= 1e-6 * tot
-    assert abs(fit_s - (1.0 - direct / tot)) <= 1e-6
+    assert abs(fit_s - (1.0 - direct / tot)) <= 1e-5
     # the streamed mode needs no M: it works on a compression that dropped it
     c2 = ctx.compress(Xd, d["offsets"], R=10, p=10, omega=torch.from_numpy(om).float().cuda(),
                       omega2=torch.from_numpy(om2).float().cuda(), flags=api.FLAG_DROP_M, J=77)
