@@ -34,10 +34,12 @@ static int a3_warps(int R) {
   return w < 1 ? 1 : (w > 16 ? 16 : w);
 }
 
+// The Lemma 2 grid launches one extra block (the V update's factor): at most
+// num_sms - 1 regular blocks keep both grids within one wave of one block per SM.
 int als3_blocks(int K, int R, int num_sms) {
   const int nw = a3_warps(R);
   const int want = (K + nw - 1) / nw;
-  return std::max(1, std::min(want, num_sms));
+  return std::max(1, std::min(want, num_sms - 1));
 }
 
 // ---------------------------------------------------------------- H update --

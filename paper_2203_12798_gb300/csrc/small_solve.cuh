@@ -1,6 +1,7 @@
 // Small FP64 solves shared by the ALS kernels: partial-sum reductions, the
-// Cholesky-based pseudoinverse of the R x R Gram-Hadamard matrices of the H,
-// V and W updates (Alg. 3, the normal equations of each CP-ALS step), and
+// pseudoinverse of the R x R Gram-Hadamard matrices of the H, V and W updates
+// (Alg. 3, the normal equations of each CP-ALS step; block Gauss-Jordan, with
+// Cholesky and eigen fallbacks), and
 // pre_solve, which factors the matrix of the next H or V update in an extra
 // block of a grid whose work it does not depend on.
 #pragma once
@@ -203,88 +204,69 @@ __device__ inline double recip_nr(double p) {
   return fma(r, fma(-p, r, 1.0), r);
 }
 
-// Inv <- A^-1 for symmetric positive definite A (n x n, n <= N <= 32) by one
-// warp, register resident: lane i holds row i of [A | I] (rows and columns
-// past n hold the identity) and Gauss-Jordan elimination without pivoting
-// (stable for SPD A) runs over the n pivots; each step shuffles the pivot
-// row once and costs one FP64 reciprocal and one FMA per entry, all entries
-// independent.  Returns (in every lane) whether every pivot exceeded
-// 1e-300 * max diag and lay within the FP32 exponent range of the reciprocal
-// estimate; only then is Inv (symmetrised) written.
-template <int N>
-__device__ __noinline__ bool warp_spd_inv_reg(const double* A, int n, double* Inv) {
-  constexpr unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  double a[N], b[N];
+// Inv <- A^-1 for symmetric positive definite A (n x n, n <= 32, FP64) by the
+// whole block: in-place Gauss-Jordan elimination without pivoting (stable
+// for SPD A) on a shared copy S (n^2 doubles).  Pivot step p maps every
+// entry independently,
+//   S(p, p) <- 1 / d,  S(p, j) <- S(p, j) / d,  S(i, p) <- -S(i, p) / d,
+//   S(i, j) <- S(i, j) - S(i, p) S(p, j) / d      (d = S(p, p), i, j != p),
+// and the entries are spread over all threads.  On this part one warp's
+// FP64 instructions issue at a quarter of the SM's FP64 rate (one SM
+// sub-partition), so the n^3 FP64 operations of the inverse go to at least
+// four warps rather than to one.  Returns (in every thread) whether every
+// pivot exceeded 1e-300 max diag and lay within the FP32 range of the
+// reciprocal estimate; only then is Inv (symmetrised) written.
+__device__ inline bool block_spd_inv_gj(const double* A, double* Inv, int n, double* S) {
+  constexpr int EMAX = 8;  // entries per thread for n^2 <= 1024 and >= 128 threads
+  const int nn = n * n, T = blockDim.x;
+  for (int e = threadIdx.x; e < nn; e += T) S[e] = A[e];
+  __syncthreads();
   double md = 0.0;
+  for (int i = 0; i < n; ++i) md = fmax(md, S[i * n + i]);
+  bool ok = md > 0.0 && T * EMAX >= nn;
+  for (int p = 0; p < n && ok; ++p) {
+    const double d = S[p * n + p];
+    ok = d > 1e-300 * md && d > 1e-37 && d < 1e37;
+    if (!ok) break;  // the same decision in every thread (all read the same d)
+    const double r = recip_nr(d);
+    double nv[EMAX];
 #pragma unroll
-  for (int c = 0; c < N; ++c) {
-    const bool in = lane < n && c < n;
-    a[c] = in ? A[lane * n + c] : (c == lane ? 1.0 : 0.0);
-    b[c] = (c == lane) ? 1.0 : 0.0;
-    if (in && c == lane) md = a[c];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(FULL, md, o));
-  bool ok = md > 0.0;
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    if (j >= n) break;
-    const double p = __shfl_sync(FULL, a[j], j);
-    ok = ok && p > 1e-300 * md && p > 1e-37 && p < 1e37;
-    const double r = recip_nr(ok ? p : 1.0);
-    const double f = a[j];  // this row's entry in the pivot column
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      const double pa = __shfl_sync(FULL, a[c], j) * r;
-      const double pb = __shfl_sync(FULL, b[c], j) * r;
-      if (lane == j) {
-        a[c] = pa;
-        b[c] = pb;
-      } else {
-        a[c] = fma(-f, pa, a[c]);
-        b[c] = fma(-f, pb, b[c]);
+    for (int u = 0; u < EMAX; ++u) {
+      const int e = threadIdx.x + u * T;
+      if (e < nn) {
+        const int i = e / n, j = e - i * n;
+        const double sij = S[e];
+        if (i == p) nv[u] = (j == p) ? r : sij * r;
+        else if (j == p) nv[u] = -sij * r;
+        else nv[u] = fma(-S[i * n + p], S[p * n + j] * r, sij);
       }
     }
-  }
-  // symmetric part: every row written, then each lane averages its row with
-  // its column and writes it back (ok is the same in every lane)
-  if (ok && lane < n) {
+    __syncthreads();
 #pragma unroll
-    for (int c = 0; c < N; ++c)
-      if (c < n) Inv[lane * n + c] = b[c];
+    for (int u = 0; u < EMAX; ++u) {
+      const int e = threadIdx.x + u * T;
+      if (e < nn) S[e] = nv[u];
+    }
+    __syncthreads();
   }
-  __syncwarp();
-  double v[N];
-#pragma unroll
-  for (int c = 0; c < N; ++c) v[c] = (ok && lane < n && c < n) ? 0.5 * (b[c] + Inv[c * n + lane]) : 0.0;
-  __syncwarp();
-  if (ok && lane < n) {
-#pragma unroll
-    for (int c = 0; c < N; ++c)
-      if (c < n) Inv[lane * n + c] = v[c];
-  }
-  __syncwarp();
+  if (ok)
+    for (int e = threadIdx.x; e < nn; e += T) {
+      const int i = e / n, j = e - i * n;
+      Inv[e] = 0.5 * (S[e] + S[j * n + i]);
+    }
+  __syncthreads();
   return ok;
 }
 
 // Inv <- A^+ for symmetric PSD A (n x n), computed by the whole block.
-// FP64 with n <= 16: the register Gauss-Jordan inverse of warp 0 (32
-// doubles per lane), the Cholesky path (and its eigen pseudoinverse fallback)
-// for larger n or when a pivot fails.
+// FP64 with n <= 32: the block Gauss-Jordan inverse above; the Cholesky path
+// (and its eigen pseudoinverse fallback) for larger n or when a pivot fails.
 template <typename T, typename OutT>
 __device__ void block_spd_pinv(const double* A, OutT* Inv, double* L, double* V, int n, T* sh, int* status) {
   __shared__ int ok;
   if constexpr (sizeof(T) == 8 && sizeof(OutT) == 8) {
-    if (n <= 16) {
-      if (threadIdx.x < 32) {
-        const bool f = warp_spd_inv_reg<16>(A, n, reinterpret_cast<double*>(Inv));
-        if (threadIdx.x == 0) ok = f;
-      }
-      __syncthreads();
-      const bool done = ok != 0;
-      __syncthreads();
-      if (done) return;
+    if (n <= 32 && blockDim.x * 8 >= n * n) {
+      if (block_spd_inv_gj(A, reinterpret_cast<double*>(Inv), n, reinterpret_cast<double*>(sh))) return;
     }
   }
   if (threadIdx.x < 32) {
