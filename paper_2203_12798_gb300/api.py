@@ -19,6 +19,7 @@ F32, BF16, F16 = 0, 1, 2
 _DT = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 FLAG_PER_SLICE, FLAG_NO_GRAPH, FLAG_GENERIC, FLAG_DROP_M, FLAG_COLD_QSTEP = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_FIVE_LAUNCH = 0x20
+FLAG_NO_PERSIST = 0x40
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "CUDA", 4: "NUMERICAL", 5: "TIMEOUT", 6: "OOM",
           7: "UNSUPPORTED"}

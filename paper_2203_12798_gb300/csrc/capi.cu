@@ -1037,8 +1037,54 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
       else launch_als_iteration(b, it, s);
     };
     tbegin(ctx, s, DPAR2_PH_ALS);
-    launch_als_init(b, v0, s);
-    if (opt->tol < 0) {
+    // one persistent launch for the whole loop (fixed iteration count, R <= 20)
+    bool persisted = false;
+    if (opt->tol < 0 && persist_supported(R) && ctx->num_sms >= 2 &&
+        !(opt->flags & (DPAR2_FLAG_FIVE_LAUNCH | DPAR2_FLAG_NO_PERSIST))) {
+      const int nsb = ctx->num_sms - 1;
+      AlsBufs bp = b;
+      bp.nblk = bp.nq = bp.pr = nsb;
+      bp.pstride = round_up(2 * RR + 2, 4);
+      bp.part = wsget<float>(ctx, "als_part_p", (size_t)3 * nsb * bp.pstride);
+      PersistArgs pa;
+      pa.K = K;
+      pa.R = R;
+      pa.max_iter = opt->max_iter;
+      pa.pstride = bp.pstride;
+      pa.wstride = 0;
+      pa.Ft = b.Ft;
+      pa.DtD = b.DtD;
+      pa.rank = b.rank;
+      pa.H = b.H;
+      pa.W = b.W;
+      pa.CV = b.CV;
+      pa.Upol = b.Upol;
+      pa.Pi = b.Pi;
+      pa.Prot = b.Prot;
+      pa.Psi = b.Psi;
+      pa.VtV = b.VtV;
+      pa.HtH = b.HtH;
+      pa.WtW = b.WtW;
+      pa.Ginv = b.Ginv;
+      pa.InvH = b.InvH;
+      pa.InvV = b.InvV;
+      pa.part1 = bp.part;
+      pa.part2 = bp.part + (size_t)nsb * pa.pstride;
+      pa.part3 = bp.part + (size_t)2 * nsb * pa.pstride;
+      pa.loss = b.loss;
+      pa.status = b.status;
+      pa.bar = wsget<unsigned>(ctx, "als_bar", 4);
+      pa.abort = nullptr;
+      launch_als_init(bp, v0, s);
+      if (launch_als_persist(pa, ctx->num_sms, s)) {
+        launch_als_finish(bp, opt->max_iter - 1, s);
+        b = bp;
+        persisted = true;
+        iters = opt->max_iter;
+      }
+    }
+    if (!persisted) launch_als_init(b, v0, s);
+    if (!persisted && opt->tol < 0) {
       bool graph = !(opt->flags & DPAR2_FLAG_NO_GRAPH);
       if (graph) {
         cudaGraph_t g;
@@ -1060,7 +1106,7 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
         launch_als_finish(b, opt->max_iter - 1, s);
       }
       iters = opt->max_iter;
-    } else {
+    } else if (!persisted) {
       double prev = 0.0;
       for (int it = 0; it < opt->max_iter; ++it) {
         iterate(it);

@@ -223,7 +223,27 @@ struct AlsBufs {
   int nblk;      // blocks of the Lemma 2 / 3 kernels (partials in regions 2, 3)
   int nq = 0;    // blocks of the Q-step (Lemma 1 partials in region 1)
   int pr = 0;    // partials per region of `part` (max(nblk, nq))
+  int pstride = 0;  // floats per partial when not 2 R^2 + 2
 };
+// Persistent ALS kernel (k_als_persist.cu): every iteration of a fit in one
+// cooperative launch of one block per SM, for R <= 20.
+struct PersistArgs {
+  int K, R, max_iter;
+  int pstride;  // floats per partial (2 R^2 + 2 rounded up to a multiple of 4)
+  int wstride;  // per-warp shared scratch (set by the launcher)
+  const float* Ft;
+  const double* DtD;
+  const int* rank;
+  float *H, *W, *CV, *Upol, *Pi, *Prot;
+  double *Psi, *VtV, *HtH, *WtW, *Ginv, *InvH, *InvV;
+  float *part1, *part2, *part3;  // num_sms - 1 partials each
+  double* loss;
+  int* status;
+  unsigned* bar;  // 3 words of device scratch (zeroed by the launcher)
+  int* abort;     // set by the launcher (bar + 2)
+};
+bool persist_supported(int R);
+bool launch_als_persist(PersistArgs& a, int num_sms, cudaStream_t s);
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s);

@@ -948,7 +948,7 @@ void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s) {
 
 // Closes the last iteration `it`: W^T W and loss[it] from the W-update partials.
 void launch_als_finish(AlsBufs& b, int it, cudaStream_t s) {
-  const int R = b.R, RR = R * R, ps = 2 * RR + 2;
+  const int R = b.R, RR = R * R, ps = b.pstride ? b.pstride : 2 * RR + 2;
   DP2_COUNTED(k_finish<<<1, 512, 0, s>>>(R, b.part + (size_t)2 * b.pr * ps, b.nblk, ps, b.WtW, b.loss, it, b.small,
                              b.status));
 }

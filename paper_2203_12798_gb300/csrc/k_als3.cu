@@ -22,6 +22,7 @@
 // grid that needs their result.
 #include "common.cuh"
 #include "internal.h"
+#include "als_phases.cuh"
 #include "small_solve.cuh"
 
 namespace dp2 {
@@ -42,47 +43,6 @@ int als3_blocks(int K, int R, int num_sms) {
   return std::max(1, std::min(want, num_sms - 1));
 }
 
-// ---------------------------------------------------------------- H update --
-// Hs (float, shared) and HtH (double, shared) <- the H update of Lemma 1 from
-// the Q-step's partials: G1 = sum of the partials (FP64 combine), H = G1 InvH
-// (FP64), columns scaled to unit norm, rounded to FP32; H^T H from the
-// rounded H.  Whole block; work areas G1, Hn: R^2 doubles each; red: T doubles.
-__device__ void block_h_update(const float* __restrict__ part1, int nq, int pstride, const double* __restrict__ InvH,
-                               int R, double* red, double* G1, double* Hn, float* Hs, double* HtH, int* status) {
-  __shared__ double scl[kMaxR];
-  const int RR = R * R, T = blockDim.x;
-  par_reduce_load(part1, nq, pstride, RR, 0, T, red, G1);
-  __syncthreads();
-  par_reduce_combine(RR, 0, T, red, G1);
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    const int i = e / R, r = e - i * R;
-    double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(G1[i * R + m], InvH[m * R + r], s);
-    Hn[e] = s;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < R; r += T) {
-    double n2 = 0.0;
-    for (int i = 0; i < R; ++i) n2 = fma(Hn[i * R + r], Hn[i * R + r], n2);
-    scl[r] = inv_norm(n2, status);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    const float h = (float)(Hn[e] * scl[e % R]);
-    Hs[e] = h;
-    Hn[e] = (double)h;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    const int a = e / R, b = e - a * R;
-    double s = 0.0;
-    for (int i = 0; i < R; ++i) s = fma(Hn[i * R + a], Hn[i * R + b], s);
-    HtH[e] = s;
-  }
-  __syncthreads();
-}
-
 // ------------------------------------------------------ H update + Lemma 2 --
 // part2[blk] (R x R): g(m, r) = sum over the block's slices of W(k, r)
 // sum_i Pi_k(i, m) H(i, r) as double-float sums (hi in [0, RR), lo in
@@ -97,7 +57,7 @@ __global__ void k_als_hg2(int K, int R, const float* __restrict__ part1, int nq,
                           double* __restrict__ Vw, int* __restrict__ status) {
   extern __shared__ __align__(16) double sd[];
   const int RR = R * R, T = blockDim.x;
-  const int nw = T >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = T >> 5, warp = threadIdx.x >> 5;
   double* red = sd;          // T
   double* G1 = red + T;      // RR
   double* Hn = G1 + RR;      // RR
@@ -123,33 +83,9 @@ __global__ void k_als_hg2(int K, int R, const float* __restrict__ part1, int nq,
   const int nb = gridDim.x - 1;
   for (int e = threadIdx.x; e < 2 * nw * RR; e += T) slots[e] = 0.f;
   __syncthreads();
-  float* slot = slots + warp * 2 * RR;
-  for (int k = blockIdx.x * nw + warp; k < K; k += nb * nw) {
-    for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
-    __syncwarp();
-    const float* wk = W + (int64_t)k * R;
-    for (int e = lane; e < RR; e += 32) {
-      const int m = e / R, r = e % R;
-      DF d = {0.f, 0.f};
-      for (int i = 0; i < R; ++i) df_mac(d, pks[i * R + m], hs[i * R + r]);
-      const float w = wk[r];
-      const float p = d.hi * w;
-      DF t;
-      t.hi = p;
-      t.lo = fmaf(d.hi, w, -p) + d.lo * w;
-      const DF acc = df_add(DF{slot[e], slot[RR + e]}, t);
-      slot[e] = acc.hi;
-      slot[RR + e] = acc.lo;
-    }
-    __syncwarp();
-  }
+  lemma2_warp(K, R, Pi, W, hs, slots + warp * 2 * RR, pks, (int64_t)blockIdx.x * nw + warp, (int64_t)nb * nw, 1);
   __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    DF a = {0.f, 0.f};
-    for (int w = 0; w < nw; ++w) a = df_add(a, DF{slots[w * 2 * RR + e], slots[w * 2 * RR + RR + e]});
-    part2[(int64_t)blockIdx.x * pstride + e] = a.hi;
-    part2[(int64_t)blockIdx.x * pstride + RR + e] = a.lo;
-  }
+  block_slots_df(slots, nw, 2 * RR, RR, part2 + (int64_t)blockIdx.x * pstride);
 }
 
 // ------------------------------------------------- V update + W update --
@@ -168,10 +104,9 @@ __global__ void k_als_vg3(int K, int R, const float* __restrict__ part2, int nb2
                           double* __restrict__ Ginvg, float* __restrict__ W, float* __restrict__ part3,
                           int* __restrict__ status) {
   extern __shared__ __align__(16) double sd[];
-  __shared__ double scl[kMaxR];
   __shared__ float ered[32][2];
   const int RR = R * R, T = blockDim.x;
-  const int nw = T >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = T >> 5, warp = threadIdx.x >> 5;
   double* red = sd;          // T
   double* Cb = red + T;      // 2 RR: reduced hi / lo halves
   double* C = Cb + 2 * RR;   // RR
@@ -190,57 +125,9 @@ __global__ void k_als_vg3(int K, int R, const float* __restrict__ part2, int nb2
   float* wn = g3 + R;
 
   // ---- V update (Lemma 2), the same in every block
-  par_reduce_load(part2, nb2, pstride, 2 * RR, 0, T, red, Cb);
-  __syncthreads();
-  par_reduce_combine(2 * RR, 0, T, red, Cb);
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    const int i = e / R, r = e - i * R;
-    double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(Cb[i * R + m] + Cb[RR + i * R + m], InvV[m * R + r], s);
-    C[e] = s;
-    hs[e] = Hg[e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {  // DC = DtD C
-    const int i = e / R, r = e - i * R;
-    double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(DtD[i * R + m], C[m * R + r], s);
-    DC[e] = s;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < R; r += T) {  // ||V(:, r)||^2 = C(:, r)^T DtD C(:, r)
-    double n2 = 0.0;
-    for (int i = 0; i < R; ++i) n2 = fma(C[i * R + r], DC[i * R + r], n2);
-    scl[r] = inv_norm(fmax(n2, 0.0), status);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    const float c = (float)(C[e] * scl[e % R]);
-    cvs[e] = c;
-    C[e] = (double)c;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {  // Psi = DtD CV (rounded CV)
-    const int i = e / R, r = e - i * R;
-    double s = 0.0;
-    for (int m = 0; m < R; ++m) s = fma(DtD[i * R + m], C[m * R + r], s);
-    DC[e] = s;
-    ps[e] = (float)s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {  // V^T V = CV^T DtD CV; Gm = V^T V * H^T H
-    const int a = e / R, b = e - a * R;
-    double s = 0.0;
-    for (int i = 0; i < R; ++i) s = fma(C[i * R + a], DC[i * R + b], s);
-    Gm[e] = s * HtHg[e];
-    if (blockIdx.x == 0) {
-      VtVg[e] = s;
-      Psig[e] = DC[e];
-      CVg[e] = cvs[e];
-    }
-  }
-  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += T) hs[e] = Hg[e];
+  block_v_update(part2, nb2, pstride, InvV, DtD, HtHg, R, red, Cb, C, DC, Gm, cvs, ps,
+                 blockIdx.x == 0 ? VtVg : nullptr, CVg, Psig, status);
   block_spd_pinv<double, double>(Gm, gi, Lw, Vw, R, fac, status);
   if (blockIdx.x == 0)
     for (int e = threadIdx.x; e < RR; e += T) Ginvg[e] = gi[e];
@@ -248,65 +135,11 @@ __global__ void k_als_vg3(int K, int R, const float* __restrict__ part2, int nb2
   // ---- Lemma 3 and the W update for this block's slices
   for (int e = threadIdx.x; e < nw * 2 * RR; e += T) slots[e] = 0.f;
   __syncthreads();
-  float* slot = slots + warp * 2 * RR;
   DF ek = {0.f, 0.f};
-  for (int k = blockIdx.x * nw + warp; k < K; k += gridDim.x * nw) {
-    for (int e = lane; e < RR; e += 32) pks[e] = Pi[(int64_t)k * RR + e];
-    __syncwarp();
-    for (int r = lane; r < R; r += 32) {
-      float s = 0.f;
-      for (int i = 0; i < R; ++i) {
-        float t = 0.f;
-        for (int m = 0; m < R; ++m) t = fmaf(pks[i * R + m], ps[m * R + r], t);
-        s = fmaf(hs[i * R + r], t, s);
-      }
-      g3[r] = s;
-    }
-    __syncwarp();
-    for (int r = lane; r < R; r += 32) {
-      double s = 0.0;
-      for (int m = 0; m < R; ++m) s = fma((double)g3[m], gi[m * R + r], s);
-      wn[r] = (float)s;
-      W[(int64_t)k * R + r] = (float)s;
-    }
-    __syncwarp();
-    for (int e = lane; e < RR; e += 32) {
-      const int a = e / R, b = e - a * R;
-      float mdl = 0.f;  // (H S_k CV^T)(a, b)
-      for (int r = 0; r < R; ++r) mdl = fmaf(hs[a * R + r] * wn[r], cvs[b * R + r], mdl);
-      const float d = pks[e] - mdl;
-      df_mac(ek, d, d);
-      DF g = {slot[e], slot[RR + e]};
-      df_mac(g, wn[a], wn[b]);
-      slot[e] = g.hi;
-      slot[RR + e] = g.lo;
-    }
-    __syncwarp();
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    DF other;
-    other.hi = __shfl_xor_sync(0xffffffffu, ek.hi, o);
-    other.lo = __shfl_xor_sync(0xffffffffu, ek.lo, o);
-    ek = df_add(ek, other);
-  }
-  if (lane == 0) {
-    ered[warp][0] = ek.hi;
-    ered[warp][1] = ek.lo;
-  }
+  lemma3_warp(K, R, Pi, ps, hs, cvs, gi, W, slots + warp * 2 * RR, pks, g3, wn, ek, (int64_t)blockIdx.x * nw + warp,
+              (int64_t)gridDim.x * nw, 1);
   __syncthreads();
-  for (int e = threadIdx.x; e < RR; e += T) {
-    DF a = {0.f, 0.f};
-    for (int w = 0; w < nw; ++w) a = df_add(a, DF{slots[w * 2 * RR + e], slots[w * 2 * RR + RR + e]});
-    part3[(int64_t)blockIdx.x * pstride + e] = a.hi;
-    part3[(int64_t)blockIdx.x * pstride + RR + e] = a.lo;
-  }
-  if (threadIdx.x == 0) {
-    DF s = {0.f, 0.f};
-    for (int w = 0; w < nw; ++w) s = df_add(s, DF{ered[w][0], ered[w][1]});
-    part3[(int64_t)blockIdx.x * pstride + 2 * RR] = s.hi;
-    part3[(int64_t)blockIdx.x * pstride + 2 * RR + 1] = s.lo;
-  }
+  block_lemma3_out(slots, nw, 2 * RR, R, ek, ered, part3 + (int64_t)blockIdx.x * pstride);
 }
 
 // ---------------------------------------------------------------- launchers --

@@ -84,6 +84,68 @@ __device__ inline void par_reduce_combine(int n, int t0, int T, const double* re
   out[t] = a + b;
 }
 
+// The same two-phase reduction reading the partials as float4 quads (pstride
+// a multiple of 4, part 16-byte aligned, entries n .. round_up(n, 4) - 1 of a
+// partial readable): item t = (quad q = t mod nq, sub-sum s = t / nq) adds
+// partials s, s + S, ... with compensation in FP32 (S = min(T / nq, nparts)
+// sub-sums per quad, 16 loads in flight), so that a thread meets one or two
+// rounds of L2 latency where a scalar walk over the partials meets several;
+// phase 2 adds each entry's S sub-sums in order in FP64.  red4: 4 T doubles.
+__device__ inline int red4_subs(int n, int nparts, int T) {
+  const int nq = (n + 3) / 4;
+  return max(1, min(T / nq, nparts));
+}
+__device__ inline void neumaier4(float4& s, float4& c, float4 v) {
+  neumaier(s.x, c.x, v.x);
+  neumaier(s.y, c.y, v.y);
+  neumaier(s.z, c.z, v.z);
+  neumaier(s.w, c.w, v.w);
+}
+__device__ inline void par_reduce4_load(const float* __restrict__ part, int nparts, int pstride, int n, double* red4) {
+  const int T = blockDim.x, nq = (n + 3) / 4, S = red4_subs(n, nparts, T);
+  for (int t = threadIdx.x; t < nq * S; t += T) {
+    const int q = t % nq, s0 = t / nq;
+    const float4* p4 = reinterpret_cast<const float4*>(part) + q;
+    const int ps4 = pstride >> 2;
+    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), cm = sm;
+    int b = s0;
+    for (; b + 15 * S < nparts; b += 16 * S) {
+      float4 x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = p4[(int64_t)(b + u * S) * ps4];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) neumaier4(sm, cm, x[u]);
+    }
+    for (; b + 3 * S < nparts; b += 4 * S) {
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = p4[(int64_t)(b + u * S) * ps4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) neumaier4(sm, cm, x[u]);
+    }
+    for (; b < nparts; b += S) neumaier4(sm, cm, p4[(int64_t)b * ps4]);
+    double* r = red4 + 4 * (size_t)t;
+    r[0] = (double)sm.x + (double)cm.x;
+    r[1] = (double)sm.y + (double)cm.y;
+    r[2] = (double)sm.z + (double)cm.z;
+    r[3] = (double)sm.w + (double)cm.w;
+  }
+}
+__device__ inline void par_reduce4_combine(int n, int nparts, const double* red4, double* out) {
+  const int T = blockDim.x, nq = (n + 3) / 4, S = red4_subs(n, nparts, T);
+  for (int e = threadIdx.x; e < n; e += T) {
+    const int q = e >> 2, c = e & 3;
+    double a = 0.0, b = 0.0;
+    int s = 0;
+    for (; s + 1 < S; s += 2) {
+      a += red4[4 * (size_t)(s * nq + q) + c];
+      b += red4[4 * (size_t)((s + 1) * nq + q) + c];
+    }
+    if (s < S) a += red4[4 * (size_t)(s * nq + q) + c];
+    out[e] = a + b;
+  }
+}
+
 // -------------------------------------------------------- FP64 small solves --
 // Symmetric FP64 Jacobi eigendecomposition (cyclic, one thread) for the
 // pseudoinverse fallback: A <- diag, V eigenvectors.
@@ -195,60 +257,77 @@ __device__ void block_spd_finish(bool ok, const double* A, OutT* Inv, double* L,
   __syncthreads();
 }
 
-// FP64 reciprocal: the FP32 estimate refined by two Newton steps
-// r <- r + r (1 - p r) (each squares the relative error: 2^-23 -> 2^-46 ->
-// below FP64 rounding), for normal FP64 p within the FP32 range.
-__device__ inline double recip_nr(double p) {
-  double r = (double)__frcp_rn((float)p);
-  r = fma(r, fma(-p, r, 1.0), r);
-  return fma(r, fma(-p, r, 1.0), r);
-}
-
 // Inv <- A^-1 for symmetric positive definite A (n x n, n <= 32, FP64) by the
 // whole block: in-place Gauss-Jordan elimination without pivoting (stable
 // for SPD A) on a shared copy S (n^2 doubles).  Pivot step p maps every
 // entry independently,
 //   S(p, p) <- 1 / d,  S(p, j) <- S(p, j) / d,  S(i, p) <- -S(i, p) / d,
-//   S(i, j) <- S(i, j) - S(i, p) S(p, j) / d      (d = S(p, p), i, j != p),
-// and the entries are spread over all threads.  On this part one warp's
-// FP64 instructions issue at a quarter of the SM's FP64 rate (one SM
-// sub-partition), so the n^3 FP64 operations of the inverse go to at least
-// four warps rather than to one.  Returns (in every thread) whether every
-// pivot exceeded 1e-300 max diag and lay within the FP32 range of the
-// reciprocal estimate; only then is Inv (symmetrised) written.
+//   S(i, j) <- S(i, j) - S(i, p) S(p, j) / d      (d = S(p, p), i, j != p).
+// FP64 instructions issue at a small fraction of the FP32 rate on this part
+// (one warp instruction per 16 SM cycles), so the FP64 work is kept to the
+// threads that own entries (entry e by thread e mod T, spread over the SM's
+// sub-partitions), and the reciprocal of the next pivot (the __drcp_rn
+// intrinsic) is computed once, by the thread that produces that pivot, one
+// step ahead.  Returns (in every thread) whether every pivot exceeded
+// 1e-300 max diag; only then is Inv (symmetrised) written.
 __device__ inline bool block_spd_inv_gj(const double* A, double* Inv, int n, double* S) {
   constexpr int EMAX = 8;  // entries per thread for n^2 <= 1024 and >= 128 threads
+  __shared__ double g_r, g_md;
+  __shared__ int g_ok;
   const int nn = n * n, T = blockDim.x;
-  for (int e = threadIdx.x; e < nn; e += T) S[e] = A[e];
+  if (T * EMAX < nn) return false;
+  int ei[EMAX], ej[EMAX];  // this thread's entries (e = threadIdx.x + u T)
+#pragma unroll
+  for (int u = 0; u < EMAX; ++u) {
+    const int e = threadIdx.x + u * T;
+    ei[u] = e < nn ? e / n : -1;
+    ej[u] = e < nn ? e - ei[u] * n : -1;
+    if (e < nn) S[e] = A[e];
+  }
   __syncthreads();
-  double md = 0.0;
-  for (int i = 0; i < n; ++i) md = fmax(md, S[i * n + i]);
-  bool ok = md > 0.0 && T * EMAX >= nn;
-  for (int p = 0; p < n && ok; ++p) {
-    const double d = S[p * n + p];
-    ok = d > 1e-300 * md && d > 1e-37 && d < 1e37;
-    if (!ok) break;  // the same decision in every thread (all read the same d)
-    const double r = recip_nr(d);
+  if (threadIdx.x == 0) {
+    double md = 0.0;
+    for (int i = 0; i < n; ++i) md = fmax(md, S[i * n + i]);
+    g_md = md;
+    g_ok = md > 0.0 && S[0] > 1e-300 * md;
+    g_r = __drcp_rn(S[0]);
+  }
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    if (!g_ok) break;  // the same decision in every thread (all read the same flag)
     double nv[EMAX];
+    double rn = 0.0;
+    int okn = 1;
+    const double r = g_r;
 #pragma unroll
     for (int u = 0; u < EMAX; ++u) {
-      const int e = threadIdx.x + u * T;
-      if (e < nn) {
-        const int i = e / n, j = e - i * n;
-        const double sij = S[e];
+      const int i = ei[u], j = ej[u];
+      if (i >= 0) {
+        const double sij = S[i * n + j];
         if (i == p) nv[u] = (j == p) ? r : sij * r;
         else if (j == p) nv[u] = -sij * r;
         else nv[u] = fma(-S[i * n + p], S[p * n + j] * r, sij);
+        if (i == p + 1 && j == p + 1) {  // the next pivot: its reciprocal one step ahead
+          rn = __drcp_rn(nv[u]);
+          okn = nv[u] > 1e-300 * g_md;
+        }
       }
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < EMAX; ++u) {
-      const int e = threadIdx.x + u * T;
-      if (e < nn) S[e] = nv[u];
+      const int i = ei[u], j = ej[u];
+      if (i >= 0) {
+        S[i * n + j] = nv[u];
+        if (i == p + 1 && j == p + 1) {
+          g_r = rn;
+          g_ok = okn;
+        }
+      }
     }
     __syncthreads();
   }
+  const bool ok = g_ok != 0;
   if (ok)
     for (int e = threadIdx.x; e < nn; e += T) {
       const int i = e / n, j = e - i * n;

@@ -269,19 +269,49 @@ def test_fit_from_well_conditioned_start_matches_oracle_elementwise(api, ctx, dt
 @pytest.mark.parametrize("R", [10, 20])
 def test_three_launch_iteration_equals_five_launch(api, ctx, R):
     """The ALS iteration as three launches (the H and V updates formed in
-    every block of the grids that need them) and as five (single-block update
-    kernels) compute the same updates; only partial sums are grouped
-    differently, so the iterates agree to FP32 rounding."""
+    every block of the grids that need them), as five (single-block update
+    kernels) and, for R <= 20, as one persistent launch of the whole loop
+    compute the same updates; only partial sums are grouped differently, so
+    the iterates agree to FP32 rounding."""
     J = 96
     d = synth.plain_parafac2(K=50, Imin=40, Imax=200, J=J, R=R, seed=1007)
     comp, Xs, om, om2 = _run(api, ctx, d, J, R, 10, torch.float32)
     V0 = _near_v0(d, J, R)
-    a = ctx.fit(comp, max_iter=16, V0=V0, want_U=True)
+    a = ctx.fit(comp, max_iter=16, V0=V0, want_U=True, flags=api.FLAG_NO_PERSIST)
     b = ctx.fit(comp, max_iter=16, V0=V0, want_U=True, flags=api.FLAG_FIVE_LAUNCH)
+    c = ctx.fit(comp, max_iter=16, V0=V0, want_U=True)  # persistent for R <= 20
     tot = sum(float(np.sum(x * x)) for x in Xs)
-    assert np.max(np.abs(np.array(a.losses) - np.array(b.losses))) <= 1e-6 * tot
-    assert abs(a.fitness - b.fitness) <= 1e-6
-    torch.testing.assert_close(a.U, b.U, atol=1e-4, rtol=1e-3)
+    for o in (b, c):
+        assert np.max(np.abs(np.array(a.losses) - np.array(o.losses))) <= 1e-6 * tot
+        assert abs(a.fitness - o.fitness) <= 1e-6
+        torch.testing.assert_close(a.U, o.U, atol=1e-4, rtol=1e-3)
+
+
+# (R, K): the persistent ALS launch at padded ranks (R = 7 runs as 10, 15 as
+# 20), with fewer slices than blocks (K = 40), and with more slices than one
+# pass of the warps holds (10 * 3 * 18 * (SMs - 1) slices at R <= 10, 8 * (SMs
+# - 1) at R = 20), so that warps own several groups.
+PERSIST_CASES = [(7, 40), (15, 300), (20, 2600), (10, 9000)]
+
+
+@pytest.mark.parametrize("R,K", PERSIST_CASES)
+def test_persistent_loop_equals_per_iteration_launches(api, ctx, R, K):
+    """The whole loop in one persistent launch against one launch sequence per
+    iteration, from the same start: the same updates with partial sums
+    grouped differently, so the loss histories, fitness and U agree to FP32
+    rounding."""
+    J = 48
+    d = synth.plain_parafac2(K=K, Imin=30, Imax=90, J=J, R=R, seed=1011 + R)
+    comp, Xs, _, _ = _run(api, ctx, d, J, R, 8, torch.float32)
+    V0 = _near_v0(d, J, R)
+    a = ctx.fit(comp, max_iter=12, V0=V0, want_U=True, flags=api.FLAG_NO_PERSIST)
+    c = ctx.fit(comp, max_iter=12, V0=V0, want_U=True)
+    tot = sum(float(np.sum(x * x)) for x in Xs)
+    assert len(c.losses) == 12
+    assert np.max(np.abs(np.array(a.losses) - np.array(c.losses))) <= 1e-6 * tot
+    assert abs(a.fitness - c.fitness) <= 1e-6
+    torch.testing.assert_close(a.U, c.U, atol=1e-4, rtol=1e-3)
+    torch.testing.assert_close(a.W, c.W, atol=1e-4 * float(a.W.abs().max()), rtol=1e-3)
 
 
 # (R, p): ranks past one warp's width (R^2 partial sums beyond the reducing

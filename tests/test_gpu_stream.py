@@ -92,16 +92,20 @@ def test_compress_host_rejects_bad_arguments(api, ctx):
 
 
 def test_kernel_launch_counter_counts_graph_launches(api, ctx):
-    # the ALS loop runs as one CUDA graph by default and as separate launches
-    # with FLAG_NO_GRAPH: the same kernels, so the same count (at least three
-    # launches per iteration)
+    # the per-iteration ALS loop runs as one CUDA graph by default and as
+    # separate launches with FLAG_NO_GRAPH: the same kernels, so the same
+    # count (at least three launches per iteration); the persistent form runs
+    # the whole loop in one launch
     d = synth.plain_parafac2(K=30, Imin=50, Imax=150, J=64, R=10, seed=23)
     X = padded(d["X"].cuda().float(), 64, torch.float32)
     comp = ctx.compress(X, d["offsets"], R=10, p=10, J=64)
     torch.cuda.synchronize()
     n0 = api.kernel_launches()
-    ctx.fit(comp, max_iter=6)
+    ctx.fit(comp, max_iter=6, flags=api.FLAG_NO_PERSIST)
     n1 = api.kernel_launches()
-    ctx.fit(comp, max_iter=6, flags=api.FLAG_NO_GRAPH)
+    ctx.fit(comp, max_iter=6, flags=api.FLAG_NO_PERSIST | api.FLAG_NO_GRAPH)
     n2 = api.kernel_launches()
+    ctx.fit(comp, max_iter=6)
+    n3 = api.kernel_launches()
     assert n1 - n0 == n2 - n1 >= 6 * 3
+    assert n3 - n2 < 6 * 3
