@@ -330,6 +330,43 @@ DPAR2_API dpar2_status dpar2_sketch_loss_bwd(dpar2_ctx* ctx, double grad_scale, 
  * only.  Errors: INVALID_ARG (null A), SHAPE. */
 DPAR2_API dpar2_status dpar2_orthonormalize(dpar2_ctx* ctx, int64_t rows, int cols, float* A, void* stream);
 
+/* Post-fit analyses of the discovery section (Sec. IV-E).  The paper applies
+ * them to the fitted factors of stock data: U_k of the stocks with a common
+ * time range (equal I) and V's rows (latent feature vectors).
+ *
+ * dpar2_similarity: S(i, j) = exp(-gamma ||U_i - U_j||_F^2) (Eq. similarity)
+ *   for K slices of one shape, each flattened to L = I R values: U device
+ *   K x L row-major FP32 (row pitch ldu >= L floats; the U of dpar2_fit for
+ *   K slices of equal length I is this layout with L = ldu = I R); S device
+ *   K x K FP32 (row pitch lds >= K), written in full (symmetric, unit
+ *   diagonal).  Squared distances come from the Gram matrix of the rows,
+ *   n_i + n_j - 2 <U_i, U_j> (FP64 norms, Gram on the tensor cores with FP32
+ *   accuracy: U split into three bf16 parts), clamped at zero.  Errors:
+ *   INVALID_ARG / SHAPE before any launch, UNSUPPORTED without tensor maps.
+ * dpar2_topk: for each of nrows rows of scores (device, row pitch ld >= n),
+ *   the k largest values (1 <= k <= 16), largest first, equal values by
+ *   lower column index, leaving out column exclude[row] (exclude: host,
+ *   nrows ints, or NULL; -1 leaves nothing out): idx device nrows x k int32
+ *   (-1 past the available columns), val device nrows x k FP32.  k-nearest
+ *   neighbours: scores = rows of S, exclude = the targets.
+ * dpar2_rwr: random walks with restarts on the similarity graph for nq
+ *   queries at once (1 <= nq <= 16): adjacency A = S with a zero diagonal
+ *   (no self loops), A~ = D^-1 A its row-normalised form (D the row sums;
+ *   a zero row stays zero), r <- (1 - c) A~^T r + c q for `iters` steps from
+ *   r = q, q one-hot at targets[query] (host, nq ints in [0, K)).  S device
+ *   K x K symmetric (pitch lds), r device nq x K FP32 output.  The paper's
+ *   settings are c = 0.15 and 100 steps.
+ * dpar2_feature_pcc: C (device J x J FP32) <- the Pearson correlation
+ *   coefficients between the rows of V (device J x R FP32, R >= 2); rows of
+ *   zero variance give NaN. */
+DPAR2_API dpar2_status dpar2_similarity(dpar2_ctx* ctx, int K, int64_t L, const float* U, int64_t ldu, double gamma,
+                                        float* S, int64_t lds, void* stream);
+DPAR2_API dpar2_status dpar2_topk(dpar2_ctx* ctx, int nrows, int n, const float* scores, int64_t ld,
+                                  const int* exclude, int k, int* idx, float* val, void* stream);
+DPAR2_API dpar2_status dpar2_rwr(dpar2_ctx* ctx, int K, const float* S, int64_t lds, int nq, const int* targets,
+                                 double c, int iters, float* r, void* stream);
+DPAR2_API dpar2_status dpar2_feature_pcc(dpar2_ctx* ctx, int J, int R, const float* V, float* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

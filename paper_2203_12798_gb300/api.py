@@ -78,6 +78,12 @@ SIGNATURES = {
     "dpar2_scratch": (ctypes.c_int, [VP, ctypes.c_char_p, ctypes.POINTER(VP), ctypes.POINTER(ctypes.c_size_t)]),
     "dpar2_set_timing": (ctypes.c_int, [VP, ctypes.c_int]),
     "dpar2_last_timings": (ctypes.c_int, [VP, DP, ctypes.c_int]),
+    "dpar2_similarity": (ctypes.c_int, [VP, ctypes.c_int, I64, VP, I64, ctypes.c_double, VP, I64, VP]),
+    "dpar2_topk": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, VP, I64, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                  VP, VP, VP]),
+    "dpar2_rwr": (ctypes.c_int, [VP, ctypes.c_int, VP, I64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.c_double, ctypes.c_int, VP, VP]),
+    "dpar2_feature_pcc": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, VP, VP, VP]),
 }
 
 PHASES = ["sketch", "qr", "project", "small", "stage2", "compress", "als", "output"]
@@ -281,6 +287,49 @@ class Context:
         assert A.is_cuda and A.dtype == torch.float32 and A.is_contiguous() and A.dim() == 2
         self._check(lib().dpar2_orthonormalize(self._h, A.shape[0], A.shape[1], _ptr(A), _stream()))
         return A
+
+    # ------------------------------------------------------------- post-fit analyses
+    def similarity(self, U: torch.Tensor, gamma: float, out=None) -> torch.Tensor:
+        """S (K x K) = exp(-gamma ||U_i - U_j||_F^2) for the rows of U (K x L,
+        float32, CUDA: each row one slice's U_k flattened)."""
+        assert U.is_cuda and U.dtype == torch.float32 and U.dim() == 2 and U.stride(1) == 1
+        K, L = U.shape
+        S = torch.empty(K, K, dtype=torch.float32, device=U.device) if out is None else out
+        self._check(lib().dpar2_similarity(self._h, K, L, _ptr(U), U.stride(0), float(gamma), _ptr(S), S.stride(0),
+                                           _stream()))
+        return S
+
+    def topk(self, scores: torch.Tensor, k: int, exclude=None):
+        """(idx, val): the k largest entries of each row of scores (float32,
+        CUDA), largest first, ties by lower index, column exclude[row] left out."""
+        assert scores.is_cuda and scores.dtype == torch.float32 and scores.dim() == 2 and scores.stride(1) == 1
+        n_rows, n = scores.shape
+        idx = torch.empty(n_rows, k, dtype=torch.int32, device=scores.device)
+        val = torch.empty(n_rows, k, dtype=torch.float32, device=scores.device)
+        ex = None
+        if exclude is not None:
+            ex = (ctypes.c_int * n_rows)(*[int(v) for v in exclude])
+        self._check(lib().dpar2_topk(self._h, n_rows, n, _ptr(scores), scores.stride(0), ex, k, _ptr(idx), _ptr(val),
+                                     _stream()))
+        return idx, val
+
+    def rwr(self, S: torch.Tensor, targets, c: float = 0.15, iters: int = 100) -> torch.Tensor:
+        """RWR scores (len(targets) x K) on the similarity graph of S."""
+        assert S.is_cuda and S.dtype == torch.float32 and S.dim() == 2 and S.stride(1) == 1
+        K = S.shape[0]
+        t = [int(v) for v in targets]
+        r = torch.empty(len(t), K, dtype=torch.float32, device=S.device)
+        self._check(lib().dpar2_rwr(self._h, K, _ptr(S), S.stride(0), len(t), (ctypes.c_int * len(t))(*t), float(c),
+                                    int(iters), _ptr(r), _stream()))
+        return r
+
+    def feature_pcc(self, V: torch.Tensor) -> torch.Tensor:
+        """Pearson correlation coefficients (J x J) between the rows of V (J x R)."""
+        assert V.is_cuda and V.dtype == torch.float32 and V.is_contiguous() and V.dim() == 2
+        J, R = V.shape
+        C = torch.empty(J, J, dtype=torch.float32, device=V.device)
+        self._check(lib().dpar2_feature_pcc(self._h, J, R, _ptr(V), _ptr(C), _stream()))
+        return C
 
     def reconstruct_error_noalloc(self, comp: "Compressed", H, V, W, Upol):
         """Identity-mode error with the library's fixed device scratch (no device

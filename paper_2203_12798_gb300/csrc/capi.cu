@@ -1599,4 +1599,94 @@ dpar2_status dpar2_orthonormalize(dpar2_ctx* ctx, int64_t rows, int cols, float*
   });
 }
 
+// ------------------------------------------------------- post-fit analyses --
+dpar2_status dpar2_similarity(dpar2_ctx* ctx, int K, int64_t L, const float* U, int64_t ldu, double gamma, float* S,
+                              int64_t lds, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!U || !S) {
+    ctx->err = "U and S must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (K < 1 || L < 1 || ldu < L || lds < K || L > (int64_t)1 << 30 || !(gamma >= 0.0)) {
+    ctx->err = "need K >= 1, L >= 1, ldu >= L, lds >= K and gamma >= 0";
+    return DPAR2_ERR_SHAPE;
+  }
+  if (!tc_available()) {
+    ctx->err = "tensor-map encoding unavailable (driver entry point cuTensorMapEncodeTiled)";
+    return DPAR2_ERR_UNSUPPORTED;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    const int ldp = round_up((int)L, 8);
+    void* parts = wsget<uint16_t>(ctx, "sim_parts", (size_t)3 * K * ldp);
+    double* nrm = wsget<double>(ctx, "sim_nrm", (size_t)K);
+    if (!launch_similarity(K, (int)L, U, ldu, gamma, S, lds, parts, ldp, nrm, ctx->num_sms, ctx->d_status, s))
+      throw Fail{DPAR2_ERR_UNSUPPORTED, "tensor map creation failed"};
+  });
+}
+
+dpar2_status dpar2_topk(dpar2_ctx* ctx, int nrows, int n, const float* scores, int64_t ld, const int* exclude, int k,
+                        int* idx, float* val, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!scores || !idx || !val) {
+    ctx->err = "scores, idx and val must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (nrows < 1 || n < 1 || ld < n || k < 1 || k > 16) {
+    ctx->err = "need nrows >= 1, n >= 1, ld >= n and 1 <= k <= 16";
+    return DPAR2_ERR_SHAPE;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    int* dex = nullptr;
+    if (exclude) {
+      std::vector<int32_t> hx(exclude, exclude + nrows);
+      dex = wsget<int>(ctx, "topk_ex", (size_t)nrows);
+      h2d_bytes(ctx, dex, hx.data(), (size_t)nrows * sizeof(int32_t), s);
+    }
+    launch_topk(nrows, n, scores, ld, dex, k, idx, val, s);
+  });
+}
+
+dpar2_status dpar2_rwr(dpar2_ctx* ctx, int K, const float* S, int64_t lds, int nq, const int* targets, double c,
+                       int iters, float* r, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!S || !targets || !r) {
+    ctx->err = "S, targets and r must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (K < 2 || lds < K || nq < 1 || nq > rwr_max_queries() || iters < 0 || !(c >= 0.0 && c <= 1.0)) {
+    ctx->err = "need K >= 2, lds >= K, 1 <= nq <= 16, iters >= 0 and 0 <= c <= 1";
+    return DPAR2_ERR_SHAPE;
+  }
+  for (int q = 0; q < nq; ++q)
+    if (targets[q] < 0 || targets[q] >= K) {
+      ctx->err = "targets must lie in [0, K)";
+      return DPAR2_ERR_SHAPE;
+    }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    std::vector<int32_t> ht(targets, targets + nq);
+    int* dt = wsget<int>(ctx, "rwr_tgt", (size_t)nq);
+    h2d_bytes(ctx, dt, ht.data(), (size_t)nq * sizeof(int32_t), s);
+    double* deg = wsget<double>(ctx, "rwr_deg", (size_t)K);
+    float* y0 = wsget<float>(ctx, "rwr_y0", (size_t)nq * K);
+    float* y1 = wsget<float>(ctx, "rwr_y1", (size_t)nq * K);
+    launch_rwr(K, S, lds, nq, dt, c, iters, deg, r, y0, y1, s);
+  });
+}
+
+dpar2_status dpar2_feature_pcc(dpar2_ctx* ctx, int J, int R, const float* V, float* C, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!V || !C) {
+    ctx->err = "V and C must be non-null";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  if (J < 1 || R < 2) {
+    ctx->err = "need J >= 1 and R >= 2";
+    return DPAR2_ERR_SHAPE;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    float* Vn = wsget<float>(ctx, "pcc_vn", (size_t)J * R);
+    launch_feature_pcc(J, R, V, Vn, C, s);
+  });
+}
+
 }  // extern "C"

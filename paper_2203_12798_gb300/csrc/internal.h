@@ -243,6 +243,16 @@ struct PersistArgs {
   int* abort;     // set by the launcher (bar + 2)
 };
 bool persist_supported(int R);
+// Post-fit analyses (k_analytics.cu).
+// parts: 3 K ldp bf16 values of scratch; nrm: K doubles.
+bool launch_similarity(int K, int L, const float* U, int64_t ldu, double gamma, float* S, int64_t lds, void* parts,
+                       int ldp, double* nrm, int num_sms, int* status, cudaStream_t s);
+void launch_topk(int nrows, int n, const float* sc, int64_t ld, const int* exclude, int k, int* idx, float* val,
+                 cudaStream_t s);
+int rwr_max_queries();
+void launch_rwr(int K, const float* S, int64_t lds, int nq, const int* tgt, double c, int iters, double* deg,
+                float* r, float* y0, float* y1, cudaStream_t s);
+void launch_feature_pcc(int J, int R, const float* V, float* Vn, float* C, cudaStream_t s);
 bool launch_als_persist(PersistArgs& a, int num_sms, cudaStream_t s);
 void launch_als_init(AlsBufs& b, const float* V0, cudaStream_t s);
 void launch_als_iteration(AlsBufs& b, int it, cudaStream_t s);

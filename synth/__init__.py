@@ -13,6 +13,7 @@ from .generators import (  # noqa: F401
     make_row_offsets,
     plain_parafac2,
     spectrogram_like,
+    stock_factors,
     skewed_series,
     tenrand,
     workload,

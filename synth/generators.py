@@ -258,3 +258,21 @@ def tenrand(I=2000, J=2000, K=4000, seed=1006, device="cpu", out_dtype=torch.flo
         r1 = min(N, r0 + chunk_rows)
         X[r0:r1, :J] = torch.rand(r1 - r0, J, generator=g, device=device).to(out_dtype)
     return dict(X=X, offsets=offsets, ld=ld)
+
+
+def stock_factors(K=4742, I=324, R=10, clusters=40, spread=0.6, seed=1007, device="cpu"):
+    """Fitted-factor-like inputs for the post-fit analyses (Sec. IV-E): K
+    slices of one length I (stocks over a common date range), U_k = Q_k H
+    with Q_k = the orthonormal factor of (C_c + spread * N(0, 1)) for the
+    slice's cluster c (clusters of similar stocks), C_c standard Gaussian
+    I x R, and H with unit-norm columns, so that ||U_k||_F^2 = R as for the
+    U_k = Q_k H of a fit.  Returns dict(U (K, I, R) float32, labels (K,))."""
+    g = _gen(device, seed)
+    H = torch.randn(R, R, generator=g, device=device)
+    H = H / H.norm(dim=0, keepdim=True)
+    C = torch.randn(clusters, I, R, generator=g, device=device)
+    labels = torch.randint(0, clusters, (K,), generator=g, device=device)
+    A = C[labels] + spread * torch.randn(K, I, R, generator=g, device=device)
+    Q, _ = torch.linalg.qr(A.cpu())
+    U = (Q.to(device) @ H).float().contiguous()
+    return dict(U=U, labels=labels)
