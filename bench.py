@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="learned-sketch leg: train Omega on 2000 slices, compare held-out fits with Gaussian q=0,1,2")
     ap.add_argument("--lr", type=float, default=0.05)
+    ap.add_argument("--analytics", action="store_true",
+                    help="post-fit analyses leg (Sec. IV-E): fit equal-length stock-like series, then similarity, "
+                         "k-NN, RWR and feature correlation")
     return ap.parse_args()
 
 
@@ -616,6 +619,135 @@ def main_learned(args):
     print(json.dumps(out))
 
 
+# --------------------------------------------------------- post-fit analyses ----
+ANALYTICS = dict(K=4742, I=323, J=88, R=10, p=10, seed=1008, iters=32, gamma=0.01, c=0.15, rwr_iters=100, k=10,
+                 cpu_slices=400)
+
+
+def main_analytics(args):
+    """US-Stock-shaped analyses (Sec. IV-E): K = 4742 stocks over a common
+    range of I = 323 trading days, J = 88 features, fitted at R = 10; then
+    S = exp(-gamma ||U_i - U_j||^2) (gamma = 0.01), the top-10 neighbours of
+    one target, RWR (c = 0.15, 100 steps) for 16 targets and its top-10, and
+    the PCC of V's rows.  One step = the four analyses; the fit is timed
+    separately.  The FP64 oracle runs the same analyses on a prefix of the
+    slices (similarity from the definition, RWR, rankings)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_12798_gb300 as pkg
+    import synth
+
+    torch.cuda.set_device(0)
+    pkg.build()
+    api = pkg.load()
+    w = ANALYTICS
+    K, I, J, R = w["K"], w["I"], w["J"], w["R"]
+    d = synth.skewed_series(K=K, Imin=I, Imax=I, J=J, R=R, seed=w["seed"], device="cuda", ld=J)
+    X = d["X"]
+    ctx = api.Context(0)
+    comp = ctx.compress(X, d["offsets"], R=R, p=w["p"], seed=w["seed"], J=J)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    res = ctx.fit(comp, max_iter=w["iters"], seed=w["seed"], want_U=True)
+    f1.record()
+    torch.cuda.synchronize()
+    fit_ms = f0.elapsed_time(f1)
+    U = res.U.reshape(K, I * R)  # slice k's U_k flattened (equal lengths: contiguous rows)
+    targets = list(range(0, K, K // 16))[:16]
+    ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for n in ("similarity", "knn", "rwr", "rwr_1q", "pcc")}
+
+    def step():
+        a, b = ev["similarity"]
+        a.record()
+        S = ctx.similarity(U, w["gamma"])
+        b.record()
+        a, b = ev["knn"]
+        a.record()
+        kn = ctx.topk(S[targets].contiguous(), w["k"], exclude=targets)
+        b.record()
+        a, b = ev["rwr"]
+        a.record()
+        r = ctx.rwr(S, targets, c=w["c"], iters=w["rwr_iters"])
+        rk = ctx.topk(r, w["k"], exclude=targets)
+        b.record()
+        a, b = ev["rwr_1q"]
+        a.record()
+        ctx.rwr(S, targets[:1], c=w["c"], iters=w["rwr_iters"])
+        b.record()
+        a, b = ev["pcc"]
+        a.record()
+        C = ctx.feature_pcc(res.V.contiguous())
+        b.record()
+        return S, kn, r, rk, C
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    times = {n: [] for n in ev}
+    with ClockSampler(0) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            S, kn, r, rk, C = step()
+            torch.cuda.synchronize()
+            for n, (a, b) in ev.items():
+                times[n].append(a.elapsed_time(b))
+        t1.record()
+        torch.cuda.synchronize()
+    ms = {n: statistics.median(v) for n, v in times.items()}
+    step_ms = sum(ms.values())
+    # the Gram on the tensor cores: 6 bf16 products over the upper-triangle
+    # tiles (128 x 128, K steps of 64); algorithmic: K (K + 1) / 2 inner
+    # products of length L = I R
+    L = I * R
+    nb = (K + 127) // 128
+    ksteps = ((L + 7) // 8 * 8 + 63) // 64
+    tc_flops = 6 * 2.0 * (nb * (nb + 1) // 2) * 128 * 128 * ksteps * 64
+    alg_flops = 2.0 * K * (K + 1) / 2 * L
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak_tf = float(peaks.get("bf16_tflops", 1900.0))
+    # oracle on a prefix of the slices
+    from oracle import analytics as oa
+
+    n = min(w["cpu_slices"], K)
+    Un = U[:n].double().cpu().numpy().reshape(n, I, R)
+    c0 = time.perf_counter()
+    S_ref = oa.similarity(list(Un), w["gamma"])
+    t_sim = time.perf_counter() - c0
+    Sg = ctx.similarity(U[:n].contiguous(), w["gamma"]).double().cpu().numpy()
+    c0 = time.perf_counter()
+    r_ref = oa.rwr(Sg, 0, c=w["c"], iters=w["rwr_iters"])
+    t_rwr = time.perf_counter() - c0
+    r_g = ctx.rwr(torch.from_numpy(Sg).float().cuda(), [0], c=w["c"], iters=w["rwr_iters"]).double().cpu().numpy()[0]
+    knn_g = ctx.topk(torch.from_numpy(Sg[:1]).float().cuda(), w["k"], exclude=[0])[0].cpu().numpy()[0]
+    knn_ref, _ = oa.knn(Sg, 0, w["k"])
+    parity = {"sample": f"first {n} slices", "similarity_max_abs_err": float(np.max(np.abs(Sg - S_ref))),
+              "rwr_max_abs_err": float(np.max(np.abs(r_g - r_ref))),
+              "knn_equal": bool(list(knn_g) == list(knn_ref))}
+    cpu = {"value": t_sim * (K / n) ** 2 + t_rwr * (K / n) ** 2, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"similarity and one RWR query on {n} of {K} slices, extrapolated by (K / n)^2"}
+    out = {"metric": "post-fit analyses (Sec. IV-E): similarity + k-NN + RWR (16 queries, and 1 query) + feature PCC",
+           "value": step_ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": step_ms, "higher_is_better": False, "dtype": "f32 (bf16x3 Gram)", "data": "synthetic",
+           "config": {"workload": f"US-Stock-shaped equal-length series K={K} I={I} J={J} R={R}, gamma={w['gamma']}, "
+                                  f"c={w['c']}, {w['rwr_iters']} RWR steps, top-{w['k']}"},
+           "phases_ms": ms, "fit_ms": fit_ms, "fitness": res.fitness,
+           "roofline": {"bound": "tensor", "kernel": "similarity Gram (k_sim_tc)",
+                        "achieved": tc_flops / (ms["similarity"] * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                        "frac": tc_flops / (ms["similarity"] * 1e-3) / 1e12 / peak_tf,
+                        "algorithmic_tflops": alg_flops / (ms["similarity"] * 1e-3) / 1e12,
+                        "note": "achieved counts the six bf16 products the kernel issues; algorithmic_tflops the "
+                                "FP32 Gram's K(K+1)L flops"},
+           "parity": parity, "cpu_baseline": cpu, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def generate(w, K, device="cuda", out_dtype=None, ld=None):
     """The workload's synthetic slices (same generator, seed and shapes)."""
     import synth
@@ -646,5 +778,7 @@ if __name__ == "__main__":
         reference_arm(a)
     elif a.learned:
         main_learned(a)
+    elif a.analytics:
+        main_analytics(a)
     else:
         main_ours(a)

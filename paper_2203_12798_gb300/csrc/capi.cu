@@ -1667,8 +1667,8 @@ dpar2_status dpar2_rwr(dpar2_ctx* ctx, int K, const float* S, int64_t lds, int n
     int* dt = wsget<int>(ctx, "rwr_tgt", (size_t)nq);
     h2d_bytes(ctx, dt, ht.data(), (size_t)nq * sizeof(int32_t), s);
     double* deg = wsget<double>(ctx, "rwr_deg", (size_t)K);
-    float* y0 = wsget<float>(ctx, "rwr_y0", (size_t)nq * K);
-    float* y1 = wsget<float>(ctx, "rwr_y1", (size_t)nq * K);
+    float* y0 = wsget<float>(ctx, "rwr_y0", (size_t)K * rwr_max_queries());
+    float* y1 = wsget<float>(ctx, "rwr_y1", (size_t)K * rwr_max_queries());
     launch_rwr(K, S, lds, nq, dt, c, iters, deg, r, y0, y1, s);
   });
 }

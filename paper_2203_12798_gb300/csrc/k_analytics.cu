@@ -345,46 +345,89 @@ __global__ void k_rwr_degree(int K, const float* __restrict__ S, int64_t lds, do
   if (lane == 0) deg[w] = s;
 }
 
-// y[q][j] = r[q][j] / d_j for the starting vector r = q (one-hot at the target).
-__global__ void k_rwr_init(int K, int nq, const int* __restrict__ tgt, const double* __restrict__ deg,
+// The iterates are kept query-fastest, y[j][q] with NQ = 4 NQ4 floats per
+// column j (nq <= NQ queries, the rest zero), so that one column of all
+// queries is NQ4 float4 loads.
+constexpr int RWR_MAXQ = 16;
+constexpr int RWR_ROWS = 4;   // rows of S per block (the y loads serve all of them)
+constexpr int RWR_WARPS = 8;  // warps per block, splitting the columns
+
+// y[j][q] = r[q][j] / d_j for the starting vector r = q (one-hot at the target);
+// r is written query-major (nq x K) as the output.
+__global__ void k_rwr_init(int K, int nq, int NQ, const int* __restrict__ tgt, const double* __restrict__ deg,
                            float* __restrict__ r, float* __restrict__ y) {
-  const int64_t n = (int64_t)nq * K;
+  const int64_t n = (int64_t)K * NQ;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(e / K), j = (int)(e - (int64_t)q * K);
-    const float v = j == tgt[q] ? 1.f : 0.f;
-    r[e] = v;
+    const int j = (int)(e / NQ), q = (int)(e - (int64_t)j * NQ);
+    const float v = (q < nq && j == tgt[q]) ? 1.f : 0.f;
+    if (q < nq) r[(int64_t)q * K + j] = v;
     y[e] = deg[j] > 0.0 ? (float)(v / deg[j]) : 0.f;
   }
 }
 
 // One step for every query: r'(q, i) = (1 - c) sum_{j != i} S(i, j) y(q, j) +
 // c [i == t_q], since A~^T r = A D^-1 r for the symmetric A; then
-// y'(q, i) = r'(q, i) / d_i.  Warp per row i, nq <= RWR_MAXQ queries at once
-// (S read once per step for all of them).
-constexpr int RWR_MAXQ = 16;
-__global__ void k_rwr_step(int K, int nq, const float* __restrict__ S, int64_t lds, const int* __restrict__ tgt,
-                           const double* __restrict__ deg, float c, const float* __restrict__ y,
-                           float* __restrict__ rn, float* __restrict__ yn) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= K) return;
-  const float* srow = S + (int64_t)i * lds;
-  float acc[RWR_MAXQ];
+// y'(q, i) = r'(q, i) / d_i.  A block takes RWR_ROWS rows; its threads walk
+// the columns j (two at a time), load y(:, j) once and apply it to every row;
+// the partial sums meet through warp shuffles and shared memory.
+template <int NQ4>
+__global__ void __launch_bounds__(32 * RWR_WARPS) k_rwr_step(int K, int nq, const float* __restrict__ S, int64_t lds,
+                                                            const int* __restrict__ tgt,
+                                                            const double* __restrict__ deg, float c,
+                                                            const float* __restrict__ y, float* __restrict__ rn,
+                                                            float* __restrict__ yn) {
+  constexpr int NQ = 4 * NQ4;
+  __shared__ float part[RWR_WARPS][RWR_ROWS * NQ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, T = blockDim.x;
+  const int i0 = blockIdx.x * RWR_ROWS;
+  float acc[RWR_ROWS][NQ];
 #pragma unroll
-  for (int q = 0; q < RWR_MAXQ; ++q) acc[q] = 0.f;
-  for (int j = lane; j < K; j += 32) {
-    const float sv = j == i ? 0.f : srow[j];
+  for (int a = 0; a < RWR_ROWS; ++a)
 #pragma unroll
-    for (int q = 0; q < RWR_MAXQ; ++q)
-      if (q < nq) acc[q] = fmaf(sv, y[(int64_t)q * K + j], acc[q]);
+    for (int q = 0; q < NQ; ++q) acc[a][q] = 0.f;
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  auto column = [&](int j) {
+    float sv[RWR_ROWS];
+#pragma unroll
+    for (int a = 0; a < RWR_ROWS; ++a) {
+      const int i = i0 + a;
+      sv[a] = (i < K && j != i) ? S[(int64_t)i * lds + j] : 0.f;
+    }
+    float4 t[NQ4];
+#pragma unroll
+    for (int u = 0; u < NQ4; ++u) t[u] = y4[(int64_t)j * NQ4 + u];
+#pragma unroll
+    for (int a = 0; a < RWR_ROWS; ++a)
+#pragma unroll
+      for (int u = 0; u < NQ4; ++u) {
+        acc[a][4 * u] = fmaf(sv[a], t[u].x, acc[a][4 * u]);
+        acc[a][4 * u + 1] = fmaf(sv[a], t[u].y, acc[a][4 * u + 1]);
+        acc[a][4 * u + 2] = fmaf(sv[a], t[u].z, acc[a][4 * u + 2]);
+        acc[a][4 * u + 3] = fmaf(sv[a], t[u].w, acc[a][4 * u + 3]);
+      }
+  };
+  int j = threadIdx.x;
+  for (; j + T < K; j += 2 * T) {
+    column(j);
+    column(j + T);
   }
+  if (j < K) column(j);
 #pragma unroll
-  for (int q = 0; q < RWR_MAXQ; ++q) {
-    if (q >= nq) break;
-    const float s = warp_sum(acc[q]);
-    if (lane == 0) {
-      const float v = (1.f - c) * s + (i == tgt[q] ? c : 0.f);
-      rn[(int64_t)q * K + i] = v;
-      yn[(int64_t)q * K + i] = deg[i] > 0.0 ? (float)(v / deg[i]) : 0.f;
+  for (int a = 0; a < RWR_ROWS; ++a)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float v = warp_sum(acc[a][q]);
+      if (lane == 0) part[warp][a * NQ + q] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < RWR_ROWS * NQ) {
+    const int a = threadIdx.x / NQ, q = threadIdx.x - a * NQ, i = i0 + a;
+    float s = 0.f;
+    for (int w = 0; w < RWR_WARPS; ++w) s += part[w][threadIdx.x];
+    if (i < K) {
+      const float v = q < nq ? (1.f - c) * s + (i == tgt[q] ? c : 0.f) : 0.f;
+      if (q < nq) rn[(int64_t)q * K + i] = v;
+      yn[(int64_t)i * NQ + q] = deg[i] > 0.0 ? (float)(v / deg[i]) : 0.f;
     }
   }
 }
@@ -444,18 +487,24 @@ void launch_topk(int nrows, int n, const float* sc, int64_t ld, const int* exclu
 
 int rwr_max_queries() { return RWR_MAXQ; }
 
-// r (nq x K) <- the scores after `iters` steps from r = q; y0, y1: nq x K
-// scratch for the degree-scaled iterates, deg: K doubles.
+// r (nq x K) <- the scores after `iters` steps from r = q; y0, y1: K x 16
+// floats of scratch for the degree-scaled iterates, deg: K doubles.
 void launch_rwr(int K, const float* S, int64_t lds, int nq, const int* tgt, double c, int iters, double* deg,
                 float* r, float* y0, float* y1, cudaStream_t s) {
-  const int wpb = 8;  // warps per block
-  const unsigned gk = (unsigned)((K + wpb - 1) / wpb);
-  DP2_COUNTED(k_rwr_degree<<<gk, 32 * wpb, 0, s>>>(K, S, lds, deg));
-  DP2_COUNTED(k_rwr_init<<<256, 256, 0, s>>>(K, nq, tgt, deg, r, y0));
+  const int wpb = 8;
+  DP2_COUNTED(k_rwr_degree<<<(unsigned)((K + wpb - 1) / wpb), 32 * wpb, 0, s>>>(K, S, lds, deg));
+  const int nq4 = (nq + 3) / 4;
+  DP2_COUNTED(k_rwr_init<<<256, 256, 0, s>>>(K, nq, 4 * nq4, tgt, deg, r, y0));
+  const unsigned gs = (unsigned)((K + RWR_ROWS - 1) / RWR_ROWS);
   float* ya = y0;
   float* yb = y1;
   for (int it = 0; it < iters; ++it) {
-    DP2_COUNTED(k_rwr_step<<<gk, 32 * wpb, 0, s>>>(K, nq, S, lds, tgt, deg, (float)c, ya, r, yb));
+    switch (nq4) {
+      case 1: DP2_COUNTED(k_rwr_step<1><<<gs, 32 * RWR_WARPS, 0, s>>>(K, nq, S, lds, tgt, deg, (float)c, ya, r, yb)); break;
+      case 2: DP2_COUNTED(k_rwr_step<2><<<gs, 32 * RWR_WARPS, 0, s>>>(K, nq, S, lds, tgt, deg, (float)c, ya, r, yb)); break;
+      case 3: DP2_COUNTED(k_rwr_step<3><<<gs, 32 * RWR_WARPS, 0, s>>>(K, nq, S, lds, tgt, deg, (float)c, ya, r, yb)); break;
+      default: DP2_COUNTED(k_rwr_step<4><<<gs, 32 * RWR_WARPS, 0, s>>>(K, nq, S, lds, tgt, deg, (float)c, ya, r, yb)); break;
+    }
     std::swap(ya, yb);
   }
 }
