@@ -42,6 +42,8 @@ MEASURED_TRAFFIC = {
     "sketch": {"ratio": 13.75e9 / 13.451e9, "k_tc_sha1": "c04bab0b0ecd9ae6748f84cf9e7f6d106ce8d1b5"},
 }
 WORKLOADS = {
+    # the plain PARAFAC2 workload the oracle finishes in seconds (20 dB SNR)
+    "plain": dict(name="plain", K=64, Imin=50, Imax=200, J=64, R=10, p=10, q=0, seed=1001, iters=32, cpu_slices=64),
     # FMA-shaped spectrogram magnitudes (the default, headline workload)
     "spectrogram": dict(name="spectrogram", K=8000, Imin=100, Imax=704, J=2049, R=10, p=10, q=0, seed=1002, iters=32),
     # US-Stock-shaped skewed-length series: I_k log-uniform, z-scored columns, AR(1) rows
@@ -220,7 +222,8 @@ def measured_traffic(kernel: str, algorithmic_bytes: float, args):
 
 def workload_config(args):
     w = WORKLOAD
-    kind = {"spectrogram": "spectrogram-like |PARAFAC2+noise|", "ranksweep": "spectrogram-like |PARAFAC2+noise|",
+    kind = {"plain": "PARAFAC2 + 20 dB noise", "spectrogram": "spectrogram-like |PARAFAC2+noise|",
+            "ranksweep": "spectrogram-like |PARAFAC2+noise|",
             "skewed": "skewed-length z-scored AR(1) + PARAFAC2 series",
             "tenrand": "tenrand uniform[0,1)"}[w["name"]]
     if w["name"] == "skewed":
@@ -750,6 +753,8 @@ def main_analytics(args):
 
 def generate(w, K, device="cuda", out_dtype=None, ld=None):
     """The workload's synthetic slices (same generator, seed and shapes)."""
+    import torch
+
     import synth
 
     if w["name"] == "skewed":
@@ -757,6 +762,12 @@ def generate(w, K, device="cuda", out_dtype=None, ld=None):
                                    device=device, out_dtype=out_dtype, ld=ld)
     if w["name"] == "tenrand":
         return synth.tenrand(I=w["Imin"], J=w["J"], K=K, seed=w["seed"], device=device, out_dtype=out_dtype, ld=ld)
+    if w["name"] == "plain":
+        d = synth.plain_parafac2(K=K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"])
+        ld = w["J"] if ld is None else ld
+        X = torch.zeros(d["X"].shape[0], ld, dtype=out_dtype or torch.float32, device=device)
+        X[:, :w["J"]] = d["X"].to(device=device, dtype=X.dtype)
+        return dict(X=X, offsets=d["offsets"], ld=ld)
     return synth.spectrogram_like(K=K, Imin=w["Imin"], Imax=w["Imax"], J=w["J"], R=w["R"], seed=w["seed"],
                                   device=device, out_dtype=out_dtype, ld=ld)
 

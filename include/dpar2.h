@@ -27,9 +27,13 @@
  *   - The library owns dpar2_ctx and dpar2_comp objects (free them with
  *     dpar2_destroy / dpar2_comp_free); everything else is caller-owned.
  *   - Precision: X may be FP32, BF16 or FP16 (storage and multiplication
- *     type, FP32 accumulation).  Gram matrices of the CholeskyQR2 steps, the
- *     R x R Gram-Hadamard normal equations of the H, V, W updates and the
- *     norm / fitness reductions are FP64.  All factor outputs are FP32.
+ *     type, FP32 accumulation).  The Gram matrices of both CholeskyQR2 steps
+ *     are double-float sums of exact FP32 products (about 48 significant
+ *     bits), stored in FP64; the first step's Cholesky is FP64, the second's
+ *     (a matrix within ~1e-6 of the identity) FP32.  The R x R Gram-Hadamard
+ *     normal equations of the H, V and W updates are inverted and applied in
+ *     FP64.  Norm and fitness reductions are FP64.  All factor outputs are
+ *     FP32.
  */
 #ifndef DPAR2_H_
 #define DPAR2_H_

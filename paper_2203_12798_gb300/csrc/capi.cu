@@ -232,9 +232,13 @@ int gram_splits(int K, int64_t maxI) {
 
 // CholeskyQR2 of the per-slice sketches Y (rows x LP, in place): after the
 // call Y holds Q1 = Y R1^+ and M2 = R2^+ with Q = Q1 M2 column-orthonormal on
-// its numerical rank (first step: double-float Gram and FP64 Cholesky; second
-// step, whose Gram is near the identity: FP32 Gram and Cholesky; dependent
-// columns dropped).
+// its numerical rank.  Both Grams are double-float sums of exact products
+// (about 48 significant bits) stored in FP64: an FP32 sum of the second Gram
+// over I_k rows is off by ~sqrt(I_k) eps32 (4e-6 at 4000 rows), more than the
+// departure of Q1 from orthonormality it is there to measure.  First step:
+// FP64 Cholesky; second step, whose matrix is within ~1e-6 of the identity:
+// FP32 Cholesky (relative accuracy eps32 for a matrix of condition ~1);
+// dependent columns dropped.
 void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI, int ell, int LP, float* M2,
              int* rank, cudaStream_t s, const char* tag) {
   std::string t(tag);
@@ -242,10 +246,10 @@ void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI
   float* M1 = wsget<float>(ctx, (t + "_M1").c_str(), (size_t)K * LP * LP);
   const int nsplit = gram_splits(K, maxI);
   double* Gp = nsplit > 1 ? wsget<double>(ctx, (t + "_Gp").c_str(), (size_t)K * nsplit * LP * LP) : nullptr;
-  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, true, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, true, s);
   launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
-  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, false, s);
+  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, false, s);
 }
 
@@ -517,7 +521,7 @@ void stage2_all(dpar2_ctx* ctx, dpar2_comp* comp, const dpar2_options* opt, cons
   {
     const int ns = gram_splits(1, KR);
     double* Gp = wsget<double>(ctx, "G2p", (size_t)ns * LP * LP);
-    launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, true, s);
+    launch_gram_dd(B2p, LP, off2 + 2, 1, ell, G2, Gp, ns, s);
   }
   float* T2 = wsget<float>(ctx, "T2", (size_t)LP * R);
   launch_eig_top(G2, M2s, 1, ell, LP, R, T2, nullptr, ctx->d_status, s);
@@ -1233,7 +1237,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
       double* G = wsget<double>(ctx, "re_AtA", (size_t)K * LP * LP);
       const int nsplit = gram_splits(K, comp->maxI);
       double* Gp = nsplit > 1 ? wsget<double>(ctx, "re_AtAp", (size_t)K * nsplit * LP * LP) : nullptr;
-      launch_gram_dd(Ap, LP, d_off, K, R, G, Gp, nsplit, true, s);
+      launch_gram_dd(Ap, LP, d_off, K, R, G, Gp, nsplit, s);
       float* Bs = wsget<float>(ctx, "re_B", (size_t)K * LP * Jp);
       double* xn = wsget<double>(ctx, "re_xn", (size_t)K);
       bool projected = false;

@@ -142,9 +142,9 @@ void launch_sl_gradsum(const float* part, int np, int LP, int Jp, int J, int ell
 // ---- per-slice small linear algebra ----
 // G[k] = Y_k^T Y_k (FP64, pitch LP).  nsplit > 1 splits every slice's rows over
 // nsplit blocks (partials in Gpart, K * nsplit * LP * LP) for few long slices.
-// df: double-float accumulation (first CholeskyQR step) or plain FP32 (second).
+// Double-float accumulation of exact products (both CholeskyQR steps).
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
-                    int nsplit, bool df, cudaStream_t s);
+                    int nsplit, cudaStream_t s);
 // fp64: factorise in FP64 (first CholeskyQR step) or FP32 (second step).
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
                       bool fp64, cudaStream_t s);

@@ -15,11 +15,13 @@
 //     = sum_k ||Pi_k - H S_k CV^T||^2 (D^T D = I), summed from the residual
 //     entries themselves.
 // Grid-wide sums are block partials reduced in a fixed order (deterministic).
-// The R x R Gram-Hadamard solves are FP64: for R <= 16 a register-resident
-// Gauss-Jordan inverse by one warp, otherwise (or when a pivot fails) a
-// Cholesky factorisation with the pseudoinverse from an FP64 Jacobi
-// eigendecomposition as the last resort; the W update's inverse is applied to
-// the FP32 right-hand sides G3 in FP64.
+// The R x R Gram-Hadamard solves are FP64: a Gauss-Jordan inverse by the
+// whole block for R <= 32, otherwise (or when a pivot fails) a Cholesky
+// factorisation with the pseudoinverse from an FP64 Jacobi eigendecomposition
+// as the last resort, applied in FP64 to the right-hand sides: Lemma 1 and 3
+// partials in FP32 (compensated block sums), Lemma 2 partials and W^T W as
+// double-float sums of exact products.  For R <= 20 and a fixed iteration
+// count the whole loop runs as one persistent launch (k_als_persist.cu).
 #include "common.cuh"
 #include "internal.h"
 #include "small_solve.cuh"

@@ -24,11 +24,9 @@ constexpr int GR_THREADS = 256;
 constexpr int GR_ROWS = 64;
 
 // GR_MAXP = pair slots per thread, ceil(ell (ell + 1) / 2 / 256) (1 for ell <= 22).
-// DFACC: double-float accumulation of exact products (the Gram of a raw
-// sketch, whose condition number is squared); otherwise plain FP32 FMA with
-// two interleaved accumulators (the Gram of Q1, which is close to the
-// identity, so that rounding stays at the FP32 level of Q1 itself).
-template <int GR_MAXP, bool DFACC>
+// Double-float accumulation of exact products (TwoProduct + TwoSum), two
+// independent accumulators per pair (even and odd rows).
+template <int GR_MAXP>
 __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict__ Y, int LP,
                                                         const int64_t* __restrict__ off, int ell,
                                                         double* __restrict__ G, int nsplit) {
@@ -36,7 +34,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
   const int k = blockIdx.x, tid = threadIdx.x, split = blockIdx.y;
   const int P = ell * (ell + 1) / 2;
   int pa[GR_MAXP], pb[GR_MAXP];
-  DF acc[GR_MAXP];   // (hi, lo) double-float, or two plain FP32 partial sums
+  DF acc[GR_MAXP];   // (hi, lo) double-float
   DF acc2[GR_MAXP];  // second double-float accumulator (odd rows): two independent chains
 #pragma unroll
   for (int i = 0; i < GR_MAXP; ++i) {
@@ -63,38 +61,20 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict_
     for (int p = tid; p < nr * LP / 4; p += GR_THREADS)
       reinterpret_cast<float4*>(ys)[p] = reinterpret_cast<const float4*>(Y + rs * LP)[p];
     __syncthreads();
-    if constexpr (DFACC) {
-      int i = 0;
-      for (; i + 1 < nr; i += 2) {
-        const float* y0 = ys + i * LP;
-        const float* y1 = y0 + LP;
+    int i = 0;
+    for (; i + 1 < nr; i += 2) {
+      const float* y0 = ys + i * LP;
+      const float* y1 = y0 + LP;
 #pragma unroll
-        for (int q = 0; q < GR_MAXP; ++q) {
-          df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
-          df_mac(acc2[q], y1[pa[q]], y1[pb[q]]);
-        }
+      for (int q = 0; q < GR_MAXP; ++q) {
+        df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
+        df_mac(acc2[q], y1[pa[q]], y1[pb[q]]);
       }
-      if (i < nr) {
-        const float* y0 = ys + i * LP;
+    }
+    if (i < nr) {
+      const float* y0 = ys + i * LP;
 #pragma unroll
-        for (int q = 0; q < GR_MAXP; ++q) df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
-      }
-    } else {
-      int i = 0;
-      for (; i + 1 < nr; i += 2) {
-        const float* y0 = ys + i * LP;
-        const float* y1 = y0 + LP;
-#pragma unroll
-        for (int q = 0; q < GR_MAXP; ++q) {
-          acc[q].hi = fmaf(y0[pa[q]], y0[pb[q]], acc[q].hi);
-          acc[q].lo = fmaf(y1[pa[q]], y1[pb[q]], acc[q].lo);
-        }
-      }
-      if (i < nr) {
-        const float* y0 = ys + i * LP;
-#pragma unroll
-        for (int q = 0; q < GR_MAXP; ++q) acc[q].hi = fmaf(y0[pa[q]], y0[pb[q]], acc[q].hi);
-      }
+      for (int q = 0; q < GR_MAXP; ++q) df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
     }
   }
   double* g = G + ((int64_t)k * nsplit + split) * LP * LP;
@@ -833,31 +813,30 @@ __global__ void k_sum_splits(const double* __restrict__ Gpart, int nsplit, int K
 }
 
 template <int NP>
-static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit, bool df,
+static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
                     cudaStream_t s) {
   const dim3 grid(K, nsplit);
   const size_t smem = GR_ROWS * LP * sizeof(float);
-  if (df) DP2_COUNTED(k_gram_dd<NP, true><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
-  else DP2_COUNTED(k_gram_dd<NP, false><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
+  DP2_COUNTED(k_gram_dd<NP><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
 }
 
 static void gram_dispatch(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
-                          bool df, cudaStream_t s) {
+                          cudaStream_t s) {
   const int np = (ell * (ell + 1) / 2 + GR_THREADS - 1) / GR_THREADS;
-  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, df, s);
-  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, df, s);
-  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, df, s);
-  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, df, s);
-  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, df, s);
+  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, s);
+  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, s);
 }
 
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
-                    int nsplit, bool df, cudaStream_t s) {
+                    int nsplit, cudaStream_t s) {
   if (nsplit <= 1 || !Gpart) {
-    gram_dispatch(Y, LP, d_off, K, ell, G, 1, df, s);
+    gram_dispatch(Y, LP, d_off, K, ell, G, 1, s);
     return;
   }
-  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, df, s);
+  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, s);
   const int64_t n = (int64_t)LP * LP, warps = (int64_t)K * n;
   DP2_COUNTED(k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G));
 }
