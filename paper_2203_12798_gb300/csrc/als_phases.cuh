@@ -317,7 +317,9 @@ __device__ __forceinline__ void lemma2_group(int K, int Ra, const float* __restr
 
 // Lemma 3 and the W update: W_k(c) = sum_m G3(k, m) Ginv(m, c) (FP64) with
 // G3(k, c) = H(:, c)^T Pi_k Psi(:, c); wtw[a] (lane c) += W(k, a) W(k, c) and
-// ek += ||Pi_k(:, c) - (H S_k CV^T)(:, c)||^2, both double-float.
+// ek += ||Pi_k(:, c) - (H S_k CV^T)(:, c)||^2, both double-float.  H, Psi, CV
+// and Ginv are read from shared memory where they are used (no register
+// copies: the kernels running this hold many registers already).
 template <int RP>
 __device__ __forceinline__ void lemma3_group(int K, int Ra, const float* __restrict__ Pi, const float* ps,
                                              const float* hs, const float* cvs, const double* gi,
@@ -327,16 +329,9 @@ __device__ __forceinline__ void lemma3_group(int K, int Ra, const float* __restr
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, g = lane / RP, c = lane - g * RP;
   const bool lane_act = g < G && c < Ra;
+  const int cc = lane_act ? c : 0;
   const int RaRa = Ra * Ra;
   float* Ps = gscr + (size_t)(g < G ? g : 0) * RP * RP;
-  float psc[RP], hc[RP], cvc[RP];  // Psi(:, c), H(:, c), CV(c, :)
-#pragma unroll
-  for (int i = 0; i < RP; ++i) {
-    const bool in = lane_act && i < Ra;
-    psc[i] = in ? ps[i * Ra + c] : 0.f;
-    hc[i] = in ? hs[i * Ra + c] : 0.f;
-    cvc[i] = in ? cvs[c * Ra + i] : 0.f;
-  }
 #pragma unroll
   for (int m = 0; m < RP; ++m) wtw[m] = DF{0.f, 0.f};
   ek = DF{0.f, 0.f};
@@ -344,47 +339,50 @@ __device__ __forceinline__ void lemma3_group(int K, int Ra, const float* __restr
     const int64_t k = kb + g;
     const bool act = lane_act && k < K;
     __syncwarp();
-    float pc[RP];  // Pi_k(:, c)
-#pragma unroll
-    for (int i = 0; i < RP; ++i) pc[i] = (act && i < Ra) ? Pi[k * RaRa + i * Ra + c] : 0.f;
     if (g < G) {
 #pragma unroll
-      for (int i = 0; i < RP; ++i) Ps[i * RP + c] = pc[i];
+      for (int i = 0; i < RP; ++i) Ps[i * RP + c] = (act && i < Ra) ? Pi[k * RaRa + i * Ra + c] : 0.f;
     }
     __syncwarp();
     // G3(k, c) = sum_i H(i, c) sum_m Pi(i, m) Psi(m, c)
     float g3 = 0.f;
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
-      float t = 0.f;
+      if (i < Ra) {
+        float t = 0.f;
 #pragma unroll
-      for (int m = 0; m < RP; ++m)
-        if (m < Ra) t = fmaf(Ps[i * RP + m], psc[m], t);
-      if (i < Ra) g3 = fmaf(hc[i], t, g3);
+        for (int m = 0; m < RP; ++m)
+          if (m < Ra) t = fmaf(Ps[i * RP + m], ps[m * Ra + cc], t);
+        g3 = fmaf(hs[i * Ra + cc], t, g3);
+      }
     }
     // W(k, c) = sum_m G3(k, m) Ginv(m, c) in FP64
     double s = 0.0;
 #pragma unroll
     for (int m = 0; m < RP; ++m) {
       const float gm = __shfl_sync(FULL, g3, (g * RP + m) & 31);
-      if (m < Ra) s = fma((double)gm, lane_act ? gi[m * Ra + c] : 0.0, s);
+      if (m < Ra) s = fma((double)gm, gi[m * Ra + cc], s);
     }
-    const float wc = (float)s;
+    const float wc = lane_act ? (float)s : 0.f;
     if (act) W[k * Ra + c] = wc;
-    float wr[RP];  // W(k, r) of the slice
+    // t_r = W(k, r) CV(c, r); the model column (H S_k CV^T)(:, c) = H t
+    float tr[RP];
 #pragma unroll
-    for (int r = 0; r < RP; ++r) wr[r] = __shfl_sync(FULL, wc, (g * RP + r) & 31);
+    for (int r = 0; r < RP; ++r) {
+      const float wr = __shfl_sync(FULL, wc, (g * RP + r) & 31);
+      tr[r] = (r < Ra) ? wr * cvs[cc * Ra + r] : 0.f;
+      if (act && r < Ra) df_mac(wtw[r], wr, wc);
+    }
     if (act) {
 #pragma unroll
       for (int a = 0; a < RP; ++a) {
         if (a < Ra) {
-          float mdl = 0.f;  // (H S_k CV^T)(a, c)
+          float mdl = 0.f;  // (H S_k CV^T)(a, c) = sum_r H(a, r) t_r
 #pragma unroll
           for (int r = 0; r < RP; ++r)
-            if (r < Ra) mdl = fmaf(hs[a * Ra + r] * wr[r], cvc[r], mdl);
-          const float d = pc[a] - mdl;
+            if (r < Ra) mdl = fmaf(hs[a * Ra + r], tr[r], mdl);
+          const float d = Ps[a * RP + c] - mdl;
           df_mac(ek, d, d);
-          df_mac(wtw[a], wr[a], wc);
         }
       }
     }

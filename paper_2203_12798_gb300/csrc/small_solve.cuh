@@ -88,7 +88,7 @@ __device__ inline void par_reduce_combine(int n, int t0, int T, const double* re
 // a multiple of 4, part 16-byte aligned, entries n .. round_up(n, 4) - 1 of a
 // partial readable): item t = (quad q = t mod nq, sub-sum s = t / nq) adds
 // partials s, s + S, ... with compensation in FP32 (S = min(T / nq, nparts)
-// sub-sums per quad, 16 loads in flight), so that a thread meets one or two
+// sub-sums per quad, 8 loads in flight), so that a thread meets one or two
 // rounds of L2 latency where a scalar walk over the partials meets several;
 // phase 2 adds each entry's S sub-sums in order in FP64.  red4: 4 T doubles.
 __device__ inline int red4_subs(int n, int nparts, int T) {
@@ -108,22 +108,19 @@ __device__ inline void par_reduce4_load(const float* __restrict__ part, int npar
     const float4* p4 = reinterpret_cast<const float4*>(part) + q;
     const int ps4 = pstride >> 2;
     float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), cm = sm;
-    int b = s0;
-    for (; b + 15 * S < nparts; b += 16 * S) {
-      float4 x[16];
+    // chunks of 8 partials, loads predicated, so that a thread's loads are in
+    // flight together whatever nparts / S is
+    for (int b = s0; b < nparts; b += 8 * S) {
+      float4 x[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = p4[(int64_t)(b + u * S) * ps4];
+      for (int u = 0; u < 8; ++u) {
+        const int bb = b + u * S;
+        x[u] = bb < nparts ? p4[(int64_t)bb * ps4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
-      for (int u = 0; u < 16; ++u) neumaier4(sm, cm, x[u]);
+      for (int u = 0; u < 8; ++u)
+        if (b + u * S < nparts) neumaier4(sm, cm, x[u]);
     }
-    for (; b + 3 * S < nparts; b += 4 * S) {
-      float4 x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = p4[(int64_t)(b + u * S) * ps4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) neumaier4(sm, cm, x[u]);
-    }
-    for (; b < nparts; b += S) neumaier4(sm, cm, p4[(int64_t)b * ps4]);
     double* r = red4 + 4 * (size_t)t;
     r[0] = (double)sm.x + (double)cm.x;
     r[1] = (double)sm.y + (double)cm.y;
@@ -270,8 +267,8 @@ __device__ void block_spd_finish(bool ok, const double* A, OutT* Inv, double* L,
 // intrinsic) is computed once, by the thread that produces that pivot, one
 // step ahead.  Returns (in every thread) whether every pivot exceeded
 // 1e-300 max diag; only then is Inv (symmetrised) written.
-__device__ inline bool block_spd_inv_gj(const double* A, double* Inv, int n, double* S) {
-  constexpr int EMAX = 8;  // entries per thread for n^2 <= 1024 and >= 128 threads
+template <int EMAX>  // entries per thread: n^2 <= EMAX blockDim.x
+__device__ inline bool block_spd_inv_gj_t(const double* A, double* Inv, int n, double* S) {
   __shared__ double g_r, g_md;
   __shared__ int g_ok;
   const int nn = n * n, T = blockDim.x;
@@ -335,6 +332,12 @@ __device__ inline bool block_spd_inv_gj(const double* A, double* Inv, int n, dou
     }
   __syncthreads();
   return ok;
+}
+
+__device__ inline bool block_spd_inv_gj(const double* A, double* Inv, int n, double* S) {
+  if (n * n <= (int)blockDim.x) return block_spd_inv_gj_t<1>(A, Inv, n, S);
+  if (n * n <= 2 * (int)blockDim.x) return block_spd_inv_gj_t<2>(A, Inv, n, S);
+  return block_spd_inv_gj_t<8>(A, Inv, n, S);
 }
 
 // Inv <- A^+ for symmetric PSD A (n x n), computed by the whole block.
