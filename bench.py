@@ -34,12 +34,13 @@ METRIC = "DPar2 time-to-fit (s) & stage-1 HBM GB/s vs peak; chosen vs plain at Î
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # stage-1 kernels on the spectrogram workload, as a ratio to the launch's
-# algorithmic bytes, from one ncu capture (profiles/); scaled to the timed
-# launch by its algorithmic bytes, and valid only for the kernel source it was
-# taken on (sha1 of k_tc.cu).
+# algorithmic bytes, from one ncu capture of a K = 1500 case (profiles/);
+# scaled to the timed launch by its algorithmic bytes, and valid only for the
+# kernel source it was taken on (sha1 of k_tc.cu).
 MEASURED_TRAFFIC = {
-    "project": {"ratio": 15.96e9 / 14.763e9, "k_tc_sha1": "c04bab0b0ecd9ae6748f84cf9e7f6d106ce8d1b5"},
-    "sketch": {"ratio": 13.75e9 / 13.451e9, "k_tc_sha1": "c04bab0b0ecd9ae6748f84cf9e7f6d106ce8d1b5"},
+    # K = 1500 capture (2.5 GB of X; profiles/dram_stage_kernels_spectrogram_K1500_bf16.md)
+    "project": {"ratio": (2.682089984e9 + 0.250196992e9) / 2.770202532e9, "k_tc_sha1": "ba505bb387fe49eaef1c5e3ba36ae8c20b14cce0"},
+    "sketch": {"ratio": (2.511421440e9 + 0.057870592e9) / 2.524322532e9, "k_tc_sha1": "ba505bb387fe49eaef1c5e3ba36ae8c20b14cce0"},
 }
 WORKLOADS = {
     # the plain PARAFAC2 workload the oracle finishes in seconds (20 dB SNR)
