@@ -227,6 +227,19 @@ __device__ inline void load4<__half>(const __half* p, float* f) {
   f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y;
 }
 
+// Two FP32 fused multiply-adds in one instruction (fma.rn.f32x2, sm_100
+// family): d.x = a.x b.x + c.x, d.y = a.y b.y + c.y, each rounded as fmaf.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
 __device__ inline void set_status(int* st, int bits) {
   if (st) atomicOr(st, bits);
 }
@@ -235,6 +248,11 @@ __device__ inline void set_status(int* st, int bits) {
 __device__ inline void cp_async16(void* smem, const void* gmem, int src_bytes) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+// cp.async 8-byte copy with zero fill of the bytes past src_bytes.
+__device__ inline void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
 }
 // cp.async 4-byte copy with zero fill when src_bytes == 0.
 __device__ inline void cp_async4(void* smem, const void* gmem, int src_bytes) {
