@@ -73,7 +73,9 @@ typedef enum { DPAR2_F32 = 0, DPAR2_BF16 = 1, DPAR2_F16 = 2 } dpar2_dtype;
 #define DPAR2_FLAG_FIVE_LAUNCH 0x20u /* ALS iterations as five launches with single-block H and V updates
                                         (the form used for R > 32) instead of three */
 #define DPAR2_FLAG_NO_PERSIST 0x40u  /* ALS iterations as launches per iteration instead of the one
-                                        persistent launch used for R <= 20 when tol < 0 */
+                                        persistent launch used when tol < 0, R <= 20 and the slices fit
+                                        one pass of its warps (K <= (SMs - 1) x 54 at R <= 10,
+                                        (SMs - 1) x 8 at R <= 20) */
 
 typedef struct {
   int R;          /* target rank (Alg. 1 / Alg. 3 parameter), 1 <= R <= 64 */

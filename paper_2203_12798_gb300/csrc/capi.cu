@@ -1041,9 +1041,10 @@ dpar2_status dpar2_fit(dpar2_ctx* ctx, const dpar2_comp* comp, const dpar2_optio
       else launch_als_iteration(b, it, s);
     };
     tbegin(ctx, s, DPAR2_PH_ALS);
-    // one persistent launch for the whole loop (fixed iteration count, R <= 20)
+    // one persistent launch for the whole loop (fixed iteration count, R <= 20,
+    // every slice in one pass of the slice blocks' warps)
     bool persisted = false;
-    if (opt->tol < 0 && persist_supported(R) && ctx->num_sms >= 2 &&
+    if (opt->tol < 0 && persist_supported(R) && ctx->num_sms >= 2 && K <= persist_capacity(R, ctx->num_sms) &&
         !(opt->flags & (DPAR2_FLAG_FIVE_LAUNCH | DPAR2_FLAG_NO_PERSIST))) {
       const int nsb = ctx->num_sms - 1;
       AlsBufs bp = b;

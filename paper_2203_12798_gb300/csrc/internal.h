@@ -243,6 +243,7 @@ struct PersistArgs {
   int* abort;     // set by the launcher (bar + 2)
 };
 bool persist_supported(int R);
+int64_t persist_capacity(int R, int num_sms);
 // Post-fit analyses (k_analytics.cu).
 // parts: 3 K ldp bf16 values of scratch; nrm: K doubles.
 bool launch_similarity(int K, int L, const float* U, int64_t ldu, double gamma, float* S, int64_t lds, void* parts,

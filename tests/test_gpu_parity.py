@@ -288,10 +288,10 @@ def test_three_launch_iteration_equals_five_launch(api, ctx, R):
 
 
 # (R, K): the persistent ALS launch at padded ranks (R = 7 runs as 10, 15 as
-# 20), with fewer slices than blocks (K = 40), and with more slices than one
-# pass of the warps holds (10 * 3 * 18 * (SMs - 1) slices at R <= 10, 8 * (SMs
-# - 1) at R = 20), so that warps own several groups.
-PERSIST_CASES = [(7, 40), (15, 300), (20, 2600), (10, 9000)]
+# 20), with fewer slices than blocks (K = 40), and near the one-pass capacity
+# of its warps (3 * 18 * (SMs - 1) slices at R <= 10, 8 * (SMs - 1) at R = 20;
+# past it the library uses the per-iteration launches, K = 9000).
+PERSIST_CASES = [(7, 40), (15, 300), (20, 1000), (10, 8000), (10, 9000)]
 
 
 @pytest.mark.parametrize("R,K", PERSIST_CASES)
