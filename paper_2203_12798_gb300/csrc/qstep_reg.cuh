@@ -80,12 +80,12 @@ __device__ __forceinline__ void qstep_warp(int K, int Ra, const float* __restric
 #pragma unroll
       for (int i = 0; i < R; ++i) Fs[i * R + c] = (act && i < Ra && c < Ra) ? Ft[k * RaRa + i * Ra + c] : 0.f;
     }
-    float wk[R];
-    float wc = 0.f;  // W(k, c), picked without indexing wk by the lane's column
+    // W(k, c) of this lane's column, and the scaled H rows W(k, r) H(c, r) of
+    // T's second factor in the group's P scratch (read back by column)
+    const float wc = (act && c < Ra) ? W[k * Ra + c] : 0.f;
+    if (lane_act) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      wk[r] = (act && r < Ra) ? W[k * Ra + r] : 0.f;
-      if (r == c) wc = wk[r];
+      for (int r = 0; r < R; ++r) Ps[r * R + c] = (act && r < Ra ? W[k * Ra + r] : 0.f) * hs[c * R + r];
     }
     __syncwarp();
     // A1 = F~_k Psi, column c
@@ -107,9 +107,10 @@ __device__ __forceinline__ void qstep_warp(int K, int Ra, const float* __restric
     for (int i = 0; i < R; ++i) {
       float s = 0.f;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s = fmaf(Ts[i * R + r], wk[r] * hs[c * R + r], s);
+      for (int r = 0; r < R; ++r) s = fmaf(Ts[i * R + r], Ps[r * R + c], s);
       t[i] = s;
     }
+    __syncwarp();  // P scratch is free again
     float v[R];
     if (Prot) {
       // V0 = Prot_k (padded with the identity), column c
@@ -176,6 +177,7 @@ __device__ __forceinline__ void qstep_warp(int K, int Ra, const float* __restric
       }
       const bool top = rk >= R || above < rk;
       float rmax = 0.f;  // largest ratio over pairs of kept columns
+#pragma unroll 1
       for (int rr = 0; rr < M - 1; ++rr) {
         int p;
         if (c == 0) {
