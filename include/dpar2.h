@@ -98,7 +98,11 @@ typedef struct dpar2_comp dpar2_comp;
  * until dpar2_comp_free).  Shapes:
  *   A       sum(I_k) x R   stage-1 left factors A_k stacked by slice (Eq. fstage_svd)
  *   Bk      K x R          stage-1 singular values (diagonal of B_k)
- *   M       K x J x R      block k = C_k B_k (the k-th J x R block of M), or NULL
+ *   Ms      3 x KR x Jq    M^T in three BF16 parts whose sum is M exactly (part p
+ *                          at Ms + p KR Jq elements; row k R + r holds column r of
+ *                          M_k = C_k B_k, the k-th J x R block of M; Jq = J rounded
+ *                          up to 64, columns past J zero), or NULL; dpar2_comp_m
+ *                          reassembles M in FP32
  *   D       J x R          stage-2 left factor (Eq. matricization_svd)
  *   E       R              stage-2 singular values
  *   Ft      K x R x R      F^(k) E, the k-th R x R block of F times E (Eq. verticalF)
@@ -106,11 +110,12 @@ typedef struct dpar2_comp dpar2_comp;
  *   offsets K + 1          slice row offsets (int64, device copy)            */
 typedef struct {
   int K, J, R, ell;
+  int Jq;    /* J rounded up to 64 */
   int64_t N; /* sum_k I_k */
   const int64_t* offsets;
   const float* A;
   const float* Bk;
-  const float* M;
+  const void* Ms;
   const float* D;
   const float* E;
   const float* Ft;
@@ -302,6 +307,11 @@ DPAR2_API size_t dpar2_comp_bytes(const dpar2_comp* comp);
 /* Device bytes the object actually holds (adds B_k, M, ||X_k||^2, offsets). */
 DPAR2_API size_t dpar2_comp_device_bytes(const dpar2_comp* comp);
 DPAR2_API dpar2_status dpar2_comp_view_get(const dpar2_comp* comp, dpar2_comp_view* view);
+/* M (device K x J x R FP32, block k = C_k B_k) reassembled from the three BF16
+ * parts of M^T the compression holds (inspection; stream-ordered on `stream`,
+ * NULL = the context's stream).  Errors: INVALID_ARG for a null argument or a
+ * compression whose M was dropped (DPAR2_FLAG_DROP_M). */
+DPAR2_API dpar2_status dpar2_comp_m(dpar2_ctx* ctx, const dpar2_comp* comp, float* M, void* stream);
 DPAR2_API void dpar2_comp_free(dpar2_comp* comp);
 
 /* Learned sketch (range-finder loss of a trainable test matrix Omega).

@@ -39,8 +39,8 @@ class Options(ctypes.Structure):
 
 class CompView(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("J", ctypes.c_int), ("R", ctypes.c_int), ("ell", ctypes.c_int),
-                ("N", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("A", ctypes.c_void_p),
-                ("Bk", ctypes.c_void_p), ("M", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("Jq", ctypes.c_int), ("N", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("Bk", ctypes.c_void_p), ("Ms", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p),
                 ("Ft", ctypes.c_void_p), ("xnorm2", ctypes.c_void_p), ("rank1", ctypes.c_void_p)]
 
 
@@ -69,6 +69,7 @@ SIGNATURES = {
     "dpar2_comp_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_device_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_view_get": (ctypes.c_int, [VP, ctypes.POINTER(CompView)]),
+    "dpar2_comp_m": (ctypes.c_int, [VP, VP, VP, VP]),
     "dpar2_comp_free": (None, [VP]),
     "dpar2_sketch_loss_fwd": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP,
                                              I64, ctypes.c_int, VP, ctypes.c_int, DP, VP]),
@@ -386,7 +387,11 @@ class Compressed:
             return out
 
         R, K, J, N = v.R, v.K, v.J, v.N
-        return dict(A=cp(v.A, (N, R)), Bk=cp(v.Bk, (K, R)), M=cp(v.M, (K, J, R)) if v.M else None,
+        M = None
+        if v.Ms:
+            M = torch.empty((K, J, R), dtype=torch.float32, device=dev)
+            self.ctx._check(lib().dpar2_comp_m(self.ctx._h, self._h, _ptr(M), _stream()))
+        return dict(A=cp(v.A, (N, R)), Bk=cp(v.Bk, (K, R)), M=M,
                     D=cp(v.D, (J, R)), E=cp(v.E, (R,)), Ft=cp(v.Ft, (K, R, R)),
                     xnorm2=cp(v.xnorm2, (K,), torch.float64), rank1=cp(v.rank1, (K,), torch.int32))
 

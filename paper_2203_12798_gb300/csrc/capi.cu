@@ -315,7 +315,8 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
   int* rank1 = static_cast<int*>(comp->rank1.p) + k0;
   double* xn2 = static_cast<double*>(comp->xnorm2.p) + k0;
   float* Bk = static_cast<float*>(comp->Bk.p) + (size_t)k0 * R;
-  float* Mb = static_cast<float*>(comp->M.p) + (size_t)k0 * J * R;
+  void* Mb = static_cast<__nv_bfloat16*>(comp->M.p) + (size_t)k0 * R * comp->Jq;
+  const int64_t mpart = (int64_t)comp->K * R * comp->Jq;
   float* Aout = static_cast<float*>(comp->A.p) + (size_t)comp->h_offsets[k0] * R;
   auto tb = [&](int ph) { if (timed) tbegin(ctx, s, ph); };
   auto te = [&](int ph) { if (timed) tend(ctx, s, ph); };
@@ -472,8 +473,7 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
   float* T = wsget<float>(ctx, "T", (size_t)Kc * LP * R);
   launch_gram_b1(B1, Jp, J, Kc, ell, LP, GB, s);
   launch_eig_top(GB, M2, Kc, ell, LP, R, T, nullptr, ctx->d_status, s);
-  launch_mblock(B1, Jp, J, Kc, ell, LP, R, T, Bk, Mb,
-                rank1, 1e-5f, s);
+  launch_mblock(B1, Jp, J, Kc, ell, LP, R, T, Bk, Mb, mpart, comp->Jq, rank1, 1e-5f, s);
   launch_seg_product(Y, LP, LP, T, (int64_t)LP * R, R, Aout, R, d_off, Kc, maxI, s);
 
   te(DPAR2_PH_SMALL);
@@ -495,28 +495,47 @@ void stage2_all(dpar2_ctx* ctx, dpar2_comp* comp, const dpar2_options* opt, cons
   }
   float* om2p = wsget<float>(ctx, "om2_pad", (size_t)KR * LP);
   launch_pad_omega(om2, (int)KR, ell, (int)KR, LP, DPAR2_F32, om2p, s);
-  const int kchunk = s2_sketch_chunk(K, J, ctx->num_sms);
-  const int nch = (K + kchunk - 1) / kchunk;
-  float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nch * J * LP);
+  // tensor-core passes over the BF16 parts of M^T; right operands split the same way
+  const void* Ms = comp->M.p;
+  const int Jq = comp->Jq;
+  const int64_t KRq = round_up64(KR, 64);
+  const int NB = s2_nb(LP);
+  void* bsk = wsget<uint16_t>(ctx, "s2_bsk", (size_t)NB * KRq);
+  void* bpj = wsget<uint16_t>(ctx, "s2_bpj", (size_t)NB * Jq);
+  const int nchS = s2_tc_chunks(true, KR, J, Jq, ctx->num_sms);
+  const int nchP = s2_tc_chunks(false, KR, J, Jq, ctx->num_sms);
+  float* Y2p = wsget<float>(ctx, "Y2p", (size_t)nchS * J * LP);
   float* Y2 = wsget<float>(ctx, "Y2", (size_t)J * LP);
-  launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, om2p, LP, Y2p, kchunk, s);
-  launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+  float* B2pp = wsget<float>(ctx, "B2pp", (size_t)nchP * KR * LP);
+  float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
+  // Y2 = M F (F: KR x LP)
+  auto sketch = [&](const float* F) {
+    launch_s2_split_rhs(F, KR, LP, KRq, bsk, s);
+    require(launch_s2_tc(true, Ms, KR, J, Jq, bsk, KRq, LP, Y2p, nchS, ctx->num_sms, ctx->d_status, s),
+            DPAR2_ERR_CUDA, "tensor map encoding failed");
+    launch_sum_parts(Y2p, nchS, (int64_t)J * LP, Y2, s);
+  };
+  // B2p = M^T G (G: J x LP)
+  auto project = [&](const float* G) {
+    launch_s2_split_rhs(G, J, LP, Jq, bpj, s);
+    require(launch_s2_tc(false, Ms, KR, J, Jq, bpj, Jq, LP, B2pp, nchP, ctx->num_sms, ctx->d_status, s),
+            DPAR2_ERR_CUDA, "tensor map encoding failed");
+    launch_sum_parts(B2pp, nchP, KR * LP, B2p, s);
+  };
+  sketch(om2p);
   int64_t* off2 = wsget<int64_t>(ctx, "off2", 4);
   const int64_t h_off2[4] = {0, (int64_t)J, 0, KR};
   h2d_i64(ctx, off2, h_off2, sizeof(h_off2) / sizeof(int64_t), s);
   float* M2s = wsget<float>(ctx, "M2s", (size_t)LP * LP);
   cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
   for (int it = 0; it < opt->q; ++it) {
-    // Y2 <- M (M^T Q2): reuse the stage-2 kernels with Omega2 := M^T Q2
+    // Y2 <- M (M^T Q2)
     DP2_COUNTED(k_apply_m2<<<dim3((unsigned)((J + 127) / 128), 1), 128, 0, s>>>(Y2, off2, LP, M2s));
-    float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
-    launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
-    launch_s2_sketch(static_cast<const float*>(comp->M.p), K, J, R, B2p, LP, Y2p, kchunk, s);
-    launch_sum_parts(Y2p, nch, (int64_t)J * LP, Y2, s);
+    project(Y2);
+    sketch(B2p);
     cholqr2(ctx, Y2, off2, 1, J, ell, LP, M2s, nullptr, s, "s2");
   }
-  float* B2p = wsget<float>(ctx, "B2p", (size_t)KR * LP);
-  launch_s2_project(static_cast<const float*>(comp->M.p), K, J, R, Y2, LP, B2p, s);
+  project(Y2);
   double* G2 = wsget<double>(ctx, "G2", (size_t)LP * LP);
   {
     const int ns = gram_splits(1, KR);
@@ -589,7 +608,8 @@ dpar2_comp* new_comp(dpar2_ctx* ctx, int K, int J, const int64_t* row_offsets, c
   alloc(comp, comp->offsets, (K + 1) * sizeof(int64_t));
   alloc(comp, comp->A, (size_t)N * R * 4);
   alloc(comp, comp->Bk, (size_t)K * R * 4);
-  alloc(comp, comp->M, (size_t)K * J * R * 4);
+  comp->Jq = round_up(J, 64);
+  alloc(comp, comp->M, (size_t)3 * K * R * comp->Jq * 2);
   alloc(comp, comp->D, (size_t)J * R * 4);
   alloc(comp, comp->E, (size_t)R * 4);
   alloc(comp, comp->Ft, (size_t)K * R * R * 4);
@@ -1221,7 +1241,7 @@ dpar2_status dpar2_reconstruct_error(dpar2_ctx* ctx, const dpar2_comp* comp, con
     double* fpart = wsget<double>(ctx, "re_fit", (size_t)nblk + 4);
     if (!X) {
       // identity mode: A_k^T X_k = B_k C_k^T, so V^T M_k stands for V^T X_k^T A_k
-      launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
+      launch_vtm(K, J, R, V, comp->M.p, (int64_t)K * R * comp->Jq, comp->Jq, P, s);
       launch_fitness(K, R, P, up, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
                      s);
       DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1));
@@ -1341,7 +1361,7 @@ dpar2_status dpar2_reconstruct_error_noalloc(dpar2_ctx* ctx, const dpar2_comp* c
     float* apart = reinterpret_cast<float*>(base + bP + bD);
     double* fpart = reinterpret_cast<double*>(base + bP + bD + bA);
     launch_psi_vtv(J, R, static_cast<const float*>(comp->D.p), V, Psi, VtV, apart, s);
-    launch_vtm(K, J, R, V, static_cast<const float*>(comp->M.p), P, s);
+    launch_vtm(K, J, R, V, comp->M.p, (int64_t)K * R * comp->Jq, comp->Jq, P, s);
     launch_fitness(K, R, P, Upol, H, W, VtV, static_cast<const double*>(comp->xnorm2.p), fpart, nblk, fpart + nblk,
                    s);
     DP2_COUNTED(k_sum_f64<<<1, 256, 0, s>>>(static_cast<const double*>(comp->xnorm2.p), K, fpart + nblk + 1));
@@ -1371,13 +1391,25 @@ dpar2_status dpar2_comp_view_get(const dpar2_comp* c, dpar2_comp_view* v) {
   v->offsets = static_cast<const int64_t*>(c->offsets.p);
   v->A = static_cast<const float*>(c->A.p);
   v->Bk = static_cast<const float*>(c->Bk.p);
-  v->M = static_cast<const float*>(c->M.p);
+  v->Jq = c->Jq;
+  v->Ms = c->M.p;
   v->D = static_cast<const float*>(c->D.p);
   v->E = static_cast<const float*>(c->E.p);
   v->Ft = static_cast<const float*>(c->Ft.p);
   v->xnorm2 = static_cast<const double*>(c->xnorm2.p);
   v->rank1 = static_cast<int32_t*>(c->rank1.p);
   return DPAR2_OK;
+}
+
+dpar2_status dpar2_comp_m(dpar2_ctx* ctx, const dpar2_comp* comp, float* M, void* stream) {
+  if (!ctx) return DPAR2_ERR_INVALID_ARG;
+  if (!comp || !M || !comp->M.p) {
+    ctx->err = "comp and M must be non-null and the compression must hold M";
+    return DPAR2_ERR_INVALID_ARG;
+  }
+  return guarded(ctx, stream, [&](cudaStream_t s) {
+    launch_ms_to_m(comp->M.p, (int64_t)comp->K * comp->R * comp->Jq, comp->K, comp->J, comp->Jq, comp->R, M, s);
+  });
 }
 
 void dpar2_comp_free(dpar2_comp* c) {

@@ -249,6 +249,15 @@ __device__ inline void cp_async16(void* smem, const void* gmem, int src_bytes) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
 }
+// v = h + m + l exactly (three BF16 parts, each rounded to nearest from the
+// remainder of the ones before; exact away from the subnormal range).
+__device__ __forceinline__ void split3_bf16(float v, __nv_bfloat16* h, __nv_bfloat16* m, __nv_bfloat16* l) {
+  *h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(*h);
+  *m = __float2bfloat16_rn(r1);
+  *l = __float2bfloat16_rn(r1 - __bfloat162float(*m));
+}
+
 // cp.async 8-byte copy with zero fill of the bytes past src_bytes.
 __device__ inline void cp_async8(void* smem, const void* gmem, int src_bytes) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);

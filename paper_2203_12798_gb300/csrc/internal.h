@@ -60,6 +60,7 @@ struct dpar2_ctx {
 struct dpar2_comp {
   dpar2_ctx* owner = nullptr;  // context whose pool and work stream hold the buffers
   int K = 0, J = 0, R = 0, ell = 0, LP = 0;
+  int Jq = 0;  // J rounded up to 64: columns of the BF16 parts of M^T held in M
   int64_t N = 0, maxI = 0;
   std::vector<int64_t> h_offsets;
   dp2::DevBuf offsets, A, Bk, M, D, E, Ft, xnorm2, rank1, DtD;
@@ -158,18 +159,28 @@ bool launch_eig_wide(const double* G, const float* M2, int K, int ell, int LP, i
                      int* status, cudaStream_t s);
 bool launch_eig_reg(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,
                     int* status, cudaStream_t s);
-void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
-                   int* rank, float tau, cudaStream_t s);
+// M_k blocks written as M^T (rows k R + r, Jq columns) in three BF16 parts,
+// part p at Ms + p pstride elements (Ms: the first row of the K slices given)
+void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, void* Ms,
+                   int64_t pstride, int Jq, int* rank, float tau, cudaStream_t s);
 void launch_seg_product(const float* In, int ldin, int nin, const float* T, int64_t tstride, int nout, float* Out,
                         int ldout, const int64_t* d_off, int K, int64_t maxI, cudaStream_t s);
 
 // ---- stage 2 ----
-// slices per block of the stage-2 sketch (sizes the nch = ceil(K / kchunk) partials)
-int s2_sketch_chunk(int K, int J, int num_sms);
-void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, int LP, float* Y2p, int kchunk,
-                      cudaStream_t s);
+// Tensor-core passes over the BF16 parts of M^T (Ms: 3 x KR x Jq): the sketch
+// (part[c] = J x LP partial of M Omega2) or the projection (part[c] = KR x LP
+// partial of M^T Q2); Bs = the right operand split by launch_s2_split_rhs
+// (s2_nb(LP) x bcols, bcols = KR rounded up to 64 for the sketch, Jq for the
+// projection); nch chunks from s2_tc_chunks.  False if no tensor map could be
+// made.
+int s2_nb(int LP);
+int s2_tc_chunks(bool sketch, int64_t KR, int J, int Jq, int num_sms);
+bool launch_s2_tc(bool sketch, const void* Ms, int64_t KR, int J, int Jq, const void* Bs, int64_t bcols, int LP,
+                  float* part, int nch, int num_sms, int* status, cudaStream_t s);
+void launch_s2_split_rhs(const float* F, int64_t nf, int LP, int64_t bcols, void* Bs, cudaStream_t s);
+// M (K x J x R FP32) from the parts (inspection)
+void launch_ms_to_m(const void* Ms, int64_t pstride, int K, int J, int Jq, int R, float* M, cudaStream_t s);
 void launch_sum_parts(const float* part, int nparts, int64_t n, float* out, cudaStream_t s);
-void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s);
 // E_r = ||Ft(:, r)||, dropped columns zeroed in Ft and D.  part: kEnormBlocks x R
 // doubles, keep: R floats, ndrop: 1 int (device scratch).
 constexpr int kEnormBlocks = 304;
@@ -276,7 +287,8 @@ int qstep_wide_blocks(int K, int R, int cap);
 int qstep_blocks(int K, int R, int nblk);
 void launch_upol_h(int K, int R, const float* Upol, const float* H, float* Tk, cudaStream_t s);
 void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, cudaStream_t s);
-void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s);
+void launch_vtm(int K, int J, int R, const float* V, const void* Ms, int64_t pstride, int Jq, float* P,
+                cudaStream_t s);
 void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,
                     cudaStream_t s);
 // AtA (K x ldg x ldg FP64, A_k^T A_k) or null for orthonormal A_k

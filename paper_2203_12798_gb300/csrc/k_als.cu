@@ -812,16 +812,20 @@ __global__ void k_p_from_cv(int K, int R, const float* __restrict__ CV, const fl
   }
 }
 
-// P_k (R x R) = V^T M_k for an arbitrary V (J x R), one block per slice.
-__global__ void k_vtm(int J, int R, const float* __restrict__ V, const float* __restrict__ Mblk,
-                      float* __restrict__ P) {
+// P_k (R x R) = V^T M_k for an arbitrary V (J x R), one block per slice; M_k
+// from the three BF16 parts of M^T (column b of M_k is row k R + b of each
+// part, part p at Ms + p pstride).
+__global__ void k_vtm(int J, int R, const float* __restrict__ V, const __nv_bfloat16* __restrict__ Ms,
+                      int64_t pstride, int Jq, float* __restrict__ P) {
   const int k = blockIdx.x, RR = R * R;
-  const float* mk = Mblk + (int64_t)k * J * R;
   for (int e = threadIdx.x; e < RR; e += blockDim.x) {
     const int a = e / R, b = e % R;
+    const __nv_bfloat16* m = Ms + ((int64_t)k * R + b) * Jq;
     float s = 0.f, c = 0.f;
     for (int j = 0; j < J; ++j) {
-      const float x = V[(int64_t)j * R + a] * mk[(int64_t)j * R + b];
+      const float mv =
+          (__bfloat162float(m[j + 2 * pstride]) + __bfloat162float(m[j + pstride])) + __bfloat162float(m[j]);
+      const float x = V[(int64_t)j * R + a] * mv;
       const float t = s + x;
       c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
       s = t;
@@ -965,8 +969,9 @@ void launch_p_from_cv(int K, int R, const float* CV, const float* Ft, float* P, 
   DP2_COUNTED(k_p_from_cv<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(K, R, CV, Ft, P));
 }
 
-void launch_vtm(int K, int J, int R, const float* V, const float* Mblk, float* P, cudaStream_t s) {
-  DP2_COUNTED(k_vtm<<<K, 128, 0, s>>>(J, R, V, Mblk, P));
+void launch_vtm(int K, int J, int R, const float* V, const void* Ms, int64_t pstride, int Jq, float* P,
+                cudaStream_t s) {
+  DP2_COUNTED(k_vtm<<<K, 128, 0, s>>>(J, R, V, static_cast<const __nv_bfloat16*>(Ms), pstride, Jq, P));
 }
 
 void launch_psi_vtv(int J, int R, const float* D, const float* V, double* Psi, double* VtV, float* part,

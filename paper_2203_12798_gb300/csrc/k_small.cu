@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(GB_THREADS, 4) k_gram_b1(const float* __restri
     tb = ta + p;
   }
   const bool act = grp < NG;
-  float acc[4][4];
+  // acc[a][h] holds entries (4 ta + a, 4 tb + 2 h) and (.., 4 tb + 2 h + 1):
+  // packed FP32 FMAs update both
+  float2 acc[4][2];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
   const float* src = B1 + (int64_t)k * LP * Jp;
   float pre[PER];
   auto fetch = [&](int j0) {
@@ -236,11 +236,13 @@ __global__ void __launch_bounds__(GB_THREADS, 4) k_gram_b1(const float* __restri
         const float4 va = *reinterpret_cast<const float4*>(&bs[jj][4 * ta]);
         const float4 vb = *reinterpret_cast<const float4*>(&bs[jj][4 * tb]);
         const float xa[4] = {va.x, va.y, va.z, va.w};
-        const float xb[4] = {vb.x, vb.y, vb.z, vb.w};
+        const float2 b01 = make_float2(vb.x, vb.y), b23 = make_float2(vb.z, vb.w);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], xb[b], acc[a][b]);
+        for (int a = 0; a < 4; ++a) {
+          const float2 aa = make_float2(xa[a], xa[a]);
+          acc[a][0] = ffma2(aa, b01, acc[a][0]);
+          acc[a][1] = ffma2(aa, b23, acc[a][1]);
+        }
       }
     }
   }
@@ -249,7 +251,8 @@ __global__ void __launch_bounds__(GB_THREADS, 4) k_gram_b1(const float* __restri
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) red[NG > 1 ? grp : 0][4 * ta + a][4 * tb + b] = acc[a][b];
+      for (int b = 0; b < 4; ++b)
+        red[NG > 1 ? grp : 0][4 * ta + a][4 * tb + b] = (b & 1) ? acc[a][b >> 1].y : acc[a][b >> 1].x;
   }
   __syncthreads();
   double* g = G + (int64_t)k * LP * LP;
@@ -467,6 +470,28 @@ __global__ void __launch_bounds__(32) k_eig_top(const double* __restrict__ G, co
 }
 
 // -------------------------------------------------------- M blocks C_k B_k ----
+// M is stored for the stage-2 tensor-core passes as M^T (KR x Jq, Jq = J
+// rounded up to 64) in three BF16 parts (part p at Ms + p pstride) whose sum
+// is M exactly: row k R + r of each part holds column r of M_k, zero past J.
+// Writes M_k(j, r) = val(j, r) for rows k R .. k R + R - 1, two columns per
+// thread and store.
+template <typename F>
+__device__ inline void store_mt_parts(__nv_bfloat16* __restrict__ Ms, int64_t pstride, int k, int R, int J, int Jq,
+                                      int tid, int nthreads, F val) {
+  for (int r = 0; r < R; ++r) {
+    __nv_bfloat16* d = Ms + ((int64_t)k * R + r) * Jq;
+    for (int j = 2 * tid; j < Jq; j += 2 * nthreads) {
+      const float v0 = j < J ? val(j, r) : 0.f, v1 = j + 1 < J ? val(j + 1, r) : 0.f;
+      __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+      split3_bf16(v0, &h0, &m0, &l0);
+      split3_bf16(v1, &h1, &m1, &l1);
+      *reinterpret_cast<__nv_bfloat162*>(d + j) = __halves2bfloat162(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(d + pstride + j) = __halves2bfloat162(m0, m1);
+      *reinterpret_cast<__nv_bfloat162*>(d + 2 * pstride + j) = __halves2bfloat162(l0, l1);
+    }
+  }
+}
+
 // M_k (J x R) = B1_k^T T_k; sigma_r = ||M_k(:, r)|| (the stage-1 singular
 // values B_k); columns with sigma_r <= tau * max sigma are zeroed in M_k and
 // T_k (numerical rank rule).  Two passes over B1_k (norms and signs, then
@@ -494,8 +519,8 @@ __device__ inline void mblock_col(const float* __restrict__ b1, int Jp, int j, i
 template <int RB>
 __global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 2 : 1) k_mblock(const float* __restrict__ B1, int Jp, int J, int ell,
                                                        int LP, int R, float* __restrict__ T,
-                                                       float* __restrict__ Bk, float* __restrict__ Mblk,
-                                                       int* __restrict__ rank, float tau) {
+                                                       float* __restrict__ Bk, __nv_bfloat16* __restrict__ Ms,
+                                                       int64_t pstride, int Jq, int* __restrict__ rank, float tau) {
   __shared__ __align__(16) float ts[kMaxEll * RB];
   __shared__ double red[MB_THREADS / 32][RB];
   __shared__ double red2[MB_THREADS / 32][RB];
@@ -563,27 +588,37 @@ __global__ void __launch_bounds__(MB_THREADS, RB <= 16 ? 2 : 1) k_mblock(const f
   }
   __syncthreads();
   for (int e = tid; e < LP * R; e += MB_THREADS) t[e] *= keep[e % R];
-  float* mk = Mblk + (int64_t)k * J * R;
-  for (int j = tid; j < J; j += MB_THREADS) {
+  // second pass over B1_k (rows L2 resident from the first): one column per
+  // thread, all components, stored as the three parts of M^T
+  for (int j = tid; j < Jq; j += MB_THREADS) {
     float o[RB];
-    mblock_col<RB>(b1, Jp, j, ell, ts, o);
+    if (j < J) {
+      mblock_col<RB>(b1, Jp, j, ell, ts, o);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) o[r] = 0.f;
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r)
-      if (r < R) mk[(int64_t)j * R + r] = o[r] * keep[r];
+      if (r < R) {
+        __nv_bfloat16* d = Ms + ((int64_t)k * R + r) * Jq + j;
+        split3_bf16(o[r] * keep[r], d, d + pstride, d + 2 * pstride);
+      }
   }
 }
 
 // Single-pass form for M_k that fits in shared memory: every column of B1_k is
 // read once (all l rows at once), M_k is kept in shared memory while its
 // column norms and sums are reduced, then scaled by the keep / sign factors
-// and written out contiguously.  EB = l rounded up to 8.
+// and written out as the three parts of M^T.  EB = l rounded up to 8.
 constexpr int MB1_THREADS = 256;
 
 template <int RB, int EB>
 __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restrict__ B1, int Jp, int J, int ell,
                                                             int LP, int R, float* __restrict__ T,
-                                                            float* __restrict__ Bk, float* __restrict__ Mblk,
-                                                            int* __restrict__ rank, float tau) {
+                                                            float* __restrict__ Bk, __nv_bfloat16* __restrict__ Ms,
+                                                            int64_t pstride, int Jq, int* __restrict__ rank,
+                                                            float tau) {
   constexpr int RP = (RB + 3) / 4 * 4;  // T_k rows padded for 16-byte loads
   extern __shared__ __align__(16) float msm[];  // J x R
   __shared__ __align__(16) float ts[EB * RP];
@@ -682,8 +717,8 @@ __global__ void __launch_bounds__(MB1_THREADS, 2) k_mblock1(const float* __restr
   }
   __syncthreads();
   for (int e = tid; e < LP * R; e += MB1_THREADS) t[e] *= keep[e % R];
-  float* mk = Mblk + (int64_t)k * J * R;
-  for (int e = tid; e < J * R; e += MB1_THREADS) mk[e] = msm[e] * keep[e % R];
+  store_mt_parts(Ms, pstride, k, R, J, Jq, tid, MB1_THREADS,
+                 [&](int j, int r) { return msm[j * R + r] * keep[r]; });
 }
 
 // -------------------------------------------- row-segment small products ----
@@ -884,12 +919,14 @@ void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, in
   DP2_COUNTED(k_eig_top<<<K, 32, smem, s>>>(G, M2, ell, LP, R, T, lam, status));
 }
 
-void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, float* Mblk,
-                   int* rank, float tau, cudaStream_t s) {
+void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R, float* T, float* Bk, void* Ms_,
+                   int64_t pstride, int Jq, int* rank, float tau, cudaStream_t s) {
+  __nv_bfloat16* Ms = static_cast<__nv_bfloat16*>(Ms_);
 #define DP2_MB(RB)                                                                                   \
   do {                                                                                               \
     cudaFuncSetAttribute(k_mblock<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, MB_SMEM_CAP);    \
-    DP2_COUNTED(k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau)); \
+    DP2_COUNTED(k_mblock<RB><<<K, MB_THREADS, MB_SMEM_CAP, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Ms, pstride, Jq, \
+                                                                 rank, tau));                        \
   } while (0)
   // single pass when M_k fits twice per SM in shared memory
   const size_t msm = (size_t)J * R * sizeof(float);
@@ -897,7 +934,8 @@ void launch_mblock(const float* B1, int Jp, int J, int K, int ell, int LP, int R
 #define DP2_MB1(RB, EB)                                                                                  \
   do {                                                                                                   \
     cudaFuncSetAttribute(k_mblock1<RB, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);      \
-    DP2_COUNTED(k_mblock1<RB, EB><<<K, MB1_THREADS, msm, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Mblk, rank, tau));      \
+    DP2_COUNTED(k_mblock1<RB, EB><<<K, MB1_THREADS, msm, s>>>(B1, Jp, J, ell, LP, R, T, Bk, Ms, pstride, Jq, rank, \
+                                                              tau));                                             \
   } while (0)
   if (msm <= 100 * 1024) {
     if (R == 10 && eb == 24) { DP2_MB1(10, 24); return; }

@@ -1,248 +1,342 @@
 // Stage-2 passes over M = [C_1 B_1 ... C_K B_K] (J x KR; Sec. III-B, the
-// randomized SVD of the matricized stage-1 factors):
-//   sketch      Y2 (J x l)   = M Omega2   = sum_k M_k Omega2_k,
-//   projection  B2^T (KR x l) = M^T Q2,   block k = M_k^T Q2,
-// with M stored as K blocks M_k (J x R, row-major).  Both are tall-skinny
-// FP32 GEMMs bound by the single read of M (about 2 l FMAs per element); they
-// run on CUDA cores with packed FP32 FMAs (two per instruction): the sketch
-// one row of Y2 per thread, the projection register tiles (4 rows x l/4
-// columns per thread) fed by a cp.async double-buffered shared-memory
-// pipeline.
+// randomized SVD of the matricized stage-1 factors) on the tensor cores:
+//   sketch      Y2 (J x l)    = M Omega2   (reduction over the KR columns of M)
+//   projection  B2^T (KR x l) = M^T Q2     (reduction over the J rows of M)
+// M is held as M^T (KR x Jq, Jq = J rounded up to 64, zero columns past J) in
+// three BF16 parts whose sum is M exactly (written by the M-block kernels);
+// the FP32 right operand (Omega2 or Q2) is split the same way, its parts
+// stacked as rows p LP + c of an NB x K-extent BF16 matrix (NB = 3 LP rounded
+// up to 16).  Per K step, three MMAs (one per part of M) accumulate all nine
+// part products into one FP32 accumulator of NB columns, and the epilogue adds
+// the three column groups: FP32 accuracy from 16-bit operands, M read once per
+// pass (6 bytes per element).
+//
+// One kernel serves both passes (template MNA):
+//   sketch      MMA M = 128 columns j of M, K = rows kr of M^T: each part's A
+//               tile is M^T rows seen MN-major (two 64-column atoms 8 KB
+//               apart, 8-row K groups 1 KB apart); B = split Omega2^T rows.
+//   projection  MMA M = 128 rows kr of M^T, K = columns j: A K-major; B =
+//               split Q2^T rows.
+// Work item = (M tile, chunk of K steps); the item writes its partial output
+// rows (LP floats each) to part[chunk], and a fixed-order sum over the chunks
+// follows.  Warp roles as in the stage-1 passes: warp 0 issues the TMA loads,
+// warp 1 the MMAs (TMEM accumulator double buffered across items), warps 2-5
+// drain the accumulator.  Every mbarrier wait is bounded; on a timeout every
+// role stops, waits (bounded) for its copies / MMAs in flight, TMEM is freed
+// and the status word gets ST_TIMEOUT.
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace dp2 {
+namespace tc {
 
-constexpr int S2_THREADS = 128;
-constexpr int S2_PJ = 32;   // projection: j per pipeline stage
+constexpr int S2T_BM = 128, S2T_BK = 64, S2T_ST = 3, S2T_THREADS = 192;
+constexpr int S2T_PART = S2T_BM * S2T_BK * 2;  // one part's A tile: 16 KB
 
-// ---- sketch: block (j-tile, chunk of kchunk slices) -> Y2p[chunk] (J x LP) ----
-// Thread = row j of Y2 (LP accumulators as float2 pairs).  Each warp copies
-// the rows of its 32 j's of the next slices' M_k (32 R contiguous floats per
-// slice) into a ring of S2_RING shared-memory buffers with cp.async, S2_RING
-// - 1 slices ahead of the one it multiplies, so that the loads of M overlap
-// the packed FP32 FMAs; the Omega2_k rows of sg slices at a time are staged
-// for the whole block and read by every thread (broadcast).
-constexpr int S2_ROWS = 128;  // rows j per sketch block (4 warps)
-constexpr int S2_RING = 4;    // M_k row buffers per warp
+template <int NB>
+struct S2Smem {
+  static constexpr int A = 3 * S2T_PART;
+  static constexpr int B = NB * S2T_BK * 2;
+  static constexpr int ACC = (NB + 31) / 32 * 32;  // TMEM columns per accumulator
+  static constexpr uint32_t NCOL = 2 * ACC <= 64 ? 64 : (2 * ACC <= 128 ? 128 : (2 * ACC <= 256 ? 256 : 512));
+  static constexpr int BYTES = 1024 + S2T_ST * (A + B) + 256;
+  static_assert(B % 1024 == 0, "B tiles must stay 1024-byte aligned");
+  static_assert(BYTES <= 227 * 1024, "shared memory");
+};
 
-template <int LP>
-__global__ void __launch_bounds__(S2_ROWS) k_s2_sketch(const float* __restrict__ Mblk, int K, int J, int R,
-                                                       const float* __restrict__ om2, int kchunk, int sg,
-                                                       float* __restrict__ Y2p) {
-  extern __shared__ __align__(16) float s2s[];  // sg x R x LP Omega2 rows, then 4 x S2_RING x 32 R M rows
-  float* oms = s2s;
+// Item `it` -> (M tile, first and last K step).
+__device__ __forceinline__ void s2t_item(int64_t it, int nmt, int nks, int nchunk, int* mt, int* k0, int* k1) {
+  *mt = (int)(it % nmt);
+  const int c = (int)(it / nmt);
+  *k0 = (int)((int64_t)c * nks / nchunk);
+  *k1 = (int)((int64_t)(c + 1) * nks / nchunk);
+}
+
+template <bool MNA, int LP>
+__global__ void __launch_bounds__(S2T_THREADS, 1) k_s2_tc(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, int nrows,
+                                                          int nmt, int nks, int nchunk, float* __restrict__ part,
+                                                          int* status) {
+  constexpr int NB = (3 * LP + 15) / 16 * 16;
+  using S = S2Smem<NB>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint8_t* sA = base;
+  uint8_t* sB = base + S2T_ST * S::A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + S2T_ST * S::B);
+  uint64_t* empty = full + S2T_ST;
+  uint64_t* accfull = empty + S2T_ST;
+  uint64_t* accempty = accfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* ring = s2s + sg * R * LP + warp * (S2_RING * 32 * R);
-  const int jw = blockIdx.x * S2_ROWS + warp * 32;  // first row of this warp
-  const int j = jw + lane;
-  const int ch = blockIdx.y;
-  const int k0 = ch * kchunk, k1 = min(K, k0 + kchunk);
-  const bool even = (R & 1) == 0;
-  const int nrows = max(0, min(32, J - jw));
-  float2 acc[LP / 2];
-#pragma unroll
-  for (int c = 0; c < LP / 2; ++c) acc[c] = make_float2(0.f, 0.f);
-  // copy of slice k's rows jw .. jw + 31 (zero past J) into ring buffer b
-  auto issue = [&](int k, int b) {
-    const float* src = Mblk + ((int64_t)k * J + jw) * R;
-    float* dst = ring + b * 32 * R;
-    const int nv = nrows * R;
-    if (even) {
-      for (int e = lane; e < 16 * R; e += 32) {
-        const bool ok = 2 * e < nv;
-        cp_async8(dst + 2 * e, ok ? src + 2 * e : Mblk, ok ? 8 : 0);
-      }
-    } else {
-      for (int e = lane; e < 32 * R; e += 32) {
-        const bool ok = e < nv;
-        cp_async4(dst + e, ok ? src + e : Mblk, ok ? 4 : 0);
-      }
+  const int64_t nitems = (int64_t)nmt * nchunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S2T_ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
-    cp_async_commit();
-  };
-  for (int kg = k0; kg < k1; kg += sg) {
-    const int ng = min(sg, k1 - kg);
-    __syncthreads();  // every warp is done with the previous group's Omega2 rows
-    const float4* src = reinterpret_cast<const float4*>(om2 + (int64_t)kg * R * LP);
-    for (int e = threadIdx.x; e < ng * R * LP / 4; e += S2_ROWS) reinterpret_cast<float4*>(oms)[e] = src[e];
-    for (int s = 0; s < min(S2_RING - 1, ng); ++s) issue(kg + s, s);
-    __syncthreads();
-    for (int s = 0; s < ng; ++s) {
-      if (s + S2_RING - 1 < ng) {
-        issue(kg + s + S2_RING - 1, (s + S2_RING - 1) % S2_RING);
-        cp_async_wait<S2_RING - 1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncwarp();
-      const float* mrow = ring + (s % S2_RING) * 32 * R + lane * R;
-      const float* om = oms + s * R * LP;
-      if (even) {
-        for (int r = 0; r < R; r += 2) {
-          const float2 mv = *reinterpret_cast<const float2*>(mrow + r);
-          const float2 m0 = make_float2(mv.x, mv.x), m1 = make_float2(mv.y, mv.y);
-          const float4* o0 = reinterpret_cast<const float4*>(om + r * LP);
-          const float4* o1 = reinterpret_cast<const float4*>(om + (r + 1) * LP);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 128);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, S::NCOL);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    const uint64_t pol_a = policy_evict_first();  // M: streamed once
+    const uint64_t pol_b = policy_evict_last();   // right operand: shared by every M tile
+    int s = 0;
+    uint32_t ph = 0, inflight = 0;
+    for (int64_t it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x) {
+      int mt, k0, k1;
+      s2t_item(it, nmt, nks, nchunk, &mt, &k0, &k1);
+      for (int kc = k0; kc < k1; ++kc) {
+        if (!wait_bounded(&empty[s], ph ^ 1, abort_flag)) break;
+        mbar_arrive_expect_tx(&full[s], S::A + S::B);
+        uint8_t* a = sA + s * S::A;
 #pragma unroll
-          for (int c4 = 0; c4 < LP / 4; ++c4) {
-            const float4 w0 = o0[c4], w1 = o1[c4];
-            acc[2 * c4] = ffma2(m0, make_float2(w0.x, w0.y), acc[2 * c4]);
-            acc[2 * c4 + 1] = ffma2(m0, make_float2(w0.z, w0.w), acc[2 * c4 + 1]);
-            acc[2 * c4] = ffma2(m1, make_float2(w1.x, w1.y), acc[2 * c4]);
-            acc[2 * c4 + 1] = ffma2(m1, make_float2(w1.z, w1.w), acc[2 * c4 + 1]);
+        for (int p = 0; p < 3; ++p) {
+          if (MNA) {
+            // M^T rows kc*64 .. +63, columns mt*128 .. +127 as two 64-column boxes
+            tma_load_3d_hint(a + p * S2T_PART, &tmA, &full[s], mt * S2T_BM, kc * S2T_BK, p, pol_a);
+            tma_load_3d_hint(a + p * S2T_PART + S2T_PART / 2, &tmA, &full[s], mt * S2T_BM + 64, kc * S2T_BK, p,
+                             pol_a);
+          } else {
+            // M^T rows mt*128 .. +127, columns kc*64 .. +63
+            tma_load_3d_hint(a + p * S2T_PART, &tmA, &full[s], kc * S2T_BK, mt * S2T_BM, p, pol_a);
           }
         }
-      } else {
-        for (int r = 0; r < R; ++r) {
-          const float mv = mrow[r];
-          const float2 m2 = make_float2(mv, mv);
-          const float4* o4 = reinterpret_cast<const float4*>(om + r * LP);
-#pragma unroll
-          for (int c4 = 0; c4 < LP / 4; ++c4) {
-            const float4 w = o4[c4];
-            acc[2 * c4] = ffma2(m2, make_float2(w.x, w.y), acc[2 * c4]);
-            acc[2 * c4 + 1] = ffma2(m2, make_float2(w.z, w.w), acc[2 * c4 + 1]);
-          }
-        }
-      }
-      __syncwarp();  // every lane is done with this buffer before it is refilled
-    }
-  }
-  if (j < J) {
-    float4* dst = reinterpret_cast<float4*>(Y2p + ((int64_t)ch * J + j) * LP);
-#pragma unroll
-    for (int c4 = 0; c4 < LP / 4; ++c4)
-      dst[c4] = make_float4(acc[2 * c4].x, acc[2 * c4].y, acc[2 * c4 + 1].x, acc[2 * c4 + 1].y);
-  }
-}
-
-// ---- projection: block of spb slices (rows (k, r)) -> B2p rows ----
-// smem per stage: As[S2_PJ][128] (M rows j for the block's (k, r) columns),
-// Bs[S2_PJ][LP] (Q2 rows).
-template <int LP>
-__global__ void __launch_bounds__(S2_THREADS) k_s2_project(const float* __restrict__ Mblk, int K, int J, int R,
-                                                           const float* __restrict__ Q2, int spb,
-                                                           float* __restrict__ B2p) {
-  constexpr int CG = LP / 4;
-  extern __shared__ __align__(16) float s2sm[];
-  // stage b: As(b) = s2sm + b S2_PJ 128, Bs(b) = s2sm + 2 S2_PJ 128 + b S2_PJ LP
-  float* const as0 = s2sm;
-  float* const bs0 = s2sm + 2 * S2_PJ * 128;
-  const int tid = threadIdx.x;
-  const int kb = blockIdx.x * spb;
-  const int nk = min(spb, K - kb);
-  const int rows = nk * R;  // <= 128
-  const int rg = tid >> 2, cg = tid & 3;
-  float2 acc[4][CG / 2];  // packed pairs of columns (CG = LP / 4 is even)
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < CG / 2; ++c) acc[a][c] = make_float2(0.f, 0.f);
-  // element w = tid + q S2_THREADS of one slice's tile is (jj, r) = divmod(w, R);
-  // stepping q advances it by divmod(S2_THREADS, R)
-  const int dq = S2_THREADS / R, dr = S2_THREADS - dq * R;
-  const int jj0 = tid / R, r0 = tid - jj0 * R;
-  auto stage = [&](int j0, int buf) {
-    // for every slice s of the block: M_k rows j0 .. j0 + S2_PJ - 1 -> As[jj][s R + r]
-    float* dst = as0 + buf * S2_PJ * 128;
-    for (int s = 0; s < nk; ++s) {
-      const float* src = Mblk + ((int64_t)(kb + s) * J + j0) * R;
-      int jj = jj0, r = r0;
-      for (int w = tid; w < S2_PJ * R; w += S2_THREADS) {
-        const bool ok = j0 + jj < J;
-        cp_async4(dst + jj * 128 + s * R + r, ok ? src + w : Mblk, ok ? 4 : 0);
-        jj += dq;
-        r += dr;
-        if (r >= R) {
-          r -= R;
-          ++jj;
+        tma_load_2d_hint(sB + s * S::B, &tmB, &full[s], kc * S2T_BK, 0, pol_b);
+        inflight = 1;
+        if (++s == S2T_ST) {
+          s = 0;
+          ph ^= 1;
         }
       }
     }
-    for (int e = tid; e < S2_PJ * LP / 4; e += S2_THREADS) {
-      const int jj = (4 * e) / LP;
-      const bool ok = j0 + jj < J;
-      cp_async16(bs0 + buf * S2_PJ * LP + 4 * e, ok ? Q2 + (int64_t)j0 * LP + 4 * e : Q2, ok ? 16 : 0);
-    }
-    cp_async_commit();
-  };
-  const int nt = (J + S2_PJ - 1) / S2_PJ;
-  stage(0, 0);
-  for (int t = 0; t < nt; ++t) {
-    const int buf = t & 1;
-    if (t + 1 < nt) {
-      stage((t + 1) * S2_PJ, buf ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const float* as = as0 + buf * S2_PJ * 128;
-    const float* bs = bs0 + buf * S2_PJ * LP;
-#pragma unroll 4
-    for (int jj = 0; jj < S2_PJ; ++jj) {
-      const float4 a4 = *reinterpret_cast<const float4*>(as + jj * 128 + 4 * rg);
-      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
-      float2 bv[CG / 2];
-#pragma unroll
-      for (int c = 0; c < CG / 2; ++c) bv[c] = *reinterpret_cast<const float2*>(bs + jj * LP + cg * CG + 2 * c);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float2 m2 = make_float2(av[a], av[a]);
-#pragma unroll
-        for (int c = 0; c < CG / 2; ++c) acc[a][c] = ffma2(m2, bv[c], acc[a][c]);
+    if (*abort_flag && inflight) {
+      const int ls = (s + S2T_ST - 1) % S2T_ST;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&full[ls], lph) && globaltimer() - t0 < kWaitNs) {
       }
     }
-    __syncthreads();
-  }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issue
+    const uint32_t idesc = idesc_f16(S2T_BM, NB, true, MNA, false);
+    int s = 0;
+    uint32_t ph = 0;
+    int t = 0;
+    bool issued = false;
+    for (int64_t it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x, ++t) {
+      int mt, k0, k1;
+      s2t_item(it, nmt, nks, nchunk, &mt, &k0, &k1);
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accempty[acc], aph ^ 1, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * S::ACC;
+      bool ok = true;
+      for (int kc = k0; kc < k1; ++kc) {
+        if (!wait_bounded(&full[s], ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t bd = sdesc_sw128(smem_u32(sB + s * S::B), 16, 1024);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int row = 4 * rg + a;
-    if (row < rows) {
-      float* dst = B2p + ((int64_t)kb * R + row) * LP + cg * CG;
+        for (int p = 0; p < 3; ++p) {
+          const uint32_t aaddr = smem_u32(sA + s * S::A + p * S2T_PART);
+          const uint64_t ad = MNA ? sdesc_sw128(aaddr, 8192, 1024) : sdesc_sw128(aaddr, 16, 1024);
 #pragma unroll
-      for (int c = 0; c < CG / 2; ++c) {
-        dst[2 * c] = acc[a][c].x;
-        dst[2 * c + 1] = acc[a][c].y;
+          for (int kk = 0; kk < S2T_BK / 16; ++kk)
+            tc_mma(d, ad + (uint64_t)(MNA ? kk * 128 : kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                   (kc != k0 || p != 0 || kk != 0) ? 1u : 0u);
+        }
+        tc_commit(&empty[s]);
+        issued = true;
+        if (++s == S2T_ST) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      tc_commit(&accfull[acc]);
+    }
+    if (*abort_flag && issued) {
+      const int ls = (s + S2T_ST - 1) % S2T_ST;
+      const uint32_t lph = (s == 0) ? (ph ^ 1) : ph;
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(&empty[ls], lph) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    int t = 0;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++t) {
+      int mt, k0, k1;
+      s2t_item(it, nmt, nks, nchunk, &mt, &k0, &k1);
+      const int acc = t & 1;
+      const uint32_t aph = (t >> 1) & 1;
+      if (!wait_bounded(&accfull[acc], aph, abort_flag)) break;
+      tc_fence_after();
+      // column p LP + c holds the products with part p of the right operand
+      float o[LP];
+#pragma unroll
+      for (int c = 0; c < LP; ++c) o[c] = 0.f;
+#pragma unroll
+      for (int g = S::ACC / 32 - 1; g >= 0; --g) {  // lo parts first
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * S::ACC + g * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (g * 32 + i < 3 * LP) o[(g * 32 + i) % LP] += v[i];
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[acc]);
+      const int row = mt * S2T_BM + q * 32 + lane;
+      const int c = (int)(it / nmt);
+      if (row < nrows) {
+        float4* dst = reinterpret_cast<float4*>(part + ((int64_t)c * nrows + row) * LP);
+#pragma unroll
+        for (int c4 = 0; c4 < LP / 4; ++c4) dst[c4] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
       }
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, S::NCOL);
+  }
+  if (threadIdx.x == 0 && *abort_flag) set_status(status, ST_TIMEOUT);
 }
 
-// Chunk of slices per sketch block: about twelve resident blocks per SM, so
-// that enough rows are in flight to cover the memory latency.
-int s2_sketch_chunk(int K, int J, int num_sms) {
-  const int jt = (J + S2_ROWS - 1) / S2_ROWS;
-  const int want_chunks = std::max(1, (12 * num_sms + jt - 1) / jt);
-  return std::max(1, (K + want_chunks - 1) / want_chunks);
+// Right operand split: F (nf x LP FP32, row-major) -> Bs (NB x bcols BF16),
+// row p LP + c = part p of column c of F (F = part 0 + part 1 + part 2
+// exactly), columns past nf and rows past 3 LP zero.  One thread per row of F.
+__global__ void k_s2_split_rhs(const float* __restrict__ F, int64_t nf, int LP, int NB, int64_t bcols,
+                               __nv_bfloat16* __restrict__ Bs) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < bcols; x += (int64_t)gridDim.x * blockDim.x) {
+    for (int c4 = 0; c4 < LP / 4; ++c4) {
+      const float4 v = x < nf ? reinterpret_cast<const float4*>(F + x * LP)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float w[4] = {v.x, v.y, v.z, v.w};
+      for (int u = 0; u < 4; ++u) {
+        const int c = 4 * c4 + u;
+        __nv_bfloat16 h, m, l;
+        split3_bf16(w[u], &h, &m, &l);
+        Bs[(int64_t)c * bcols + x] = h;
+        Bs[(int64_t)(LP + c) * bcols + x] = m;
+        Bs[(int64_t)(2 * LP + c) * bcols + x] = l;
+      }
+    }
+    for (int r = 3 * LP; r < NB; ++r) Bs[(int64_t)r * bcols + x] = __float2bfloat16_rn(0.f);
+  }
 }
 
-template <typename F>
-static void set_smem_attr(F* f, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// M (K x J x R FP32, block k = C_k B_k) from its three BF16 parts of M^T.
+__global__ void k_ms_to_m(const __nv_bfloat16* __restrict__ Ms, int64_t pstride, int K, int J, int Jq, int R,
+                          float* __restrict__ M) {
+  const int64_t n = (int64_t)K * J * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / ((int64_t)J * R);
+    const int j = (int)((i / R) % J), r = (int)(i % R);
+    const int64_t e = (k * R + r) * Jq + j;
+    M[i] = (__bfloat162float(Ms[e + 2 * pstride]) + __bfloat162float(Ms[e + pstride])) + __bfloat162float(Ms[e]);
+  }
 }
 
-void launch_s2_sketch(const float* Mblk, int K, int J, int R, const float* om2, int LP, float* Y2p, int kchunk,
-                      cudaStream_t s) {
-  const int nch = (K + kchunk - 1) / kchunk;
-  dim3 grid((J + S2_ROWS - 1) / S2_ROWS, nch);
-  // Omega2 rows of up to 16 slices per staging round, within 24 KB; the
-  // M row rings of the four warps
-  const int sg = std::max(1, std::min(16, (24 * 1024) / (R * LP * (int)sizeof(float))));
-  const size_t smem = ((size_t)sg * R * LP + (size_t)4 * S2_RING * 32 * R) * sizeof(float);
-  DP2_LP_SWITCH(LP, (set_smem_attr(k_s2_sketch<L>, smem),
-                     DP2_COUNTED(k_s2_sketch<L><<<grid, S2_ROWS, smem, s>>>(Mblk, K, J, R, om2, kchunk, sg, Y2p))));
+}  // namespace tc
+
+// Chunks of the K steps: the fewest that keep the slowest CTA's share of K
+// steps (rounds of items x steps per item, plus one step of overhead per item)
+// near the even split over the SMs.
+int s2_chunks(int nmt, int nks, int num_sms) {
+  int best = 1;
+  int64_t bestc = INT64_MAX;
+  for (int S = 1; S <= std::min(nks, 64); ++S) {
+    const int64_t items = (int64_t)nmt * S;
+    const int64_t rounds = (items + num_sms - 1) / num_sms;
+    const int64_t cost = rounds * ((nks + S - 1) / S + 1);
+    if (cost < bestc) {
+      bestc = cost;
+      best = S;
+    }
+  }
+  return best;
 }
 
-void launch_s2_project(const float* Mblk, int K, int J, int R, const float* Q2, int LP, float* B2p, cudaStream_t s) {
-  const int spb = std::max(1, 128 / R);
-  const size_t smem = (size_t)2 * (S2_PJ * 128 + S2_PJ * LP) * sizeof(float);
-  DP2_LP_SWITCH(LP, (set_smem_attr(k_s2_project<L>, smem),
-                     DP2_COUNTED(k_s2_project<L><<<(unsigned)((K + spb - 1) / spb), S2_THREADS, smem, s>>>(Mblk, K, J, R, Q2,
-                                                                                              spb, B2p))));
+template <bool MNA, int LP>
+static void s2_launch(const CUtensorMap& ma, const CUtensorMap& mb, int grid, int nrows, int nmt, int nks, int nch,
+                      float* part, int* status, cudaStream_t s) {
+  constexpr int NB = (3 * LP + 15) / 16 * 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_s2_tc<MNA, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::S2Smem<NB>::BYTES);
+    attr = true;
+  }
+  DP2_COUNTED(tc::k_s2_tc<MNA, LP><<<grid, tc::S2T_THREADS, tc::S2Smem<NB>::BYTES, s>>>(ma, mb, nrows, nmt, nks, nch,
+                                                                                        part, status));
+}
+
+int s2_nb(int LP) { return (3 * LP + 15) / 16 * 16; }
+
+bool launch_s2_tc(bool sketch, const void* Ms, int64_t KR, int J, int Jq, const void* Bs, int64_t bcols, int LP,
+                  float* part, int nch, int num_sms, int* status, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  const int NB = s2_nb(LP);
+  if (!make_map3_rows(&ma, Ms, (uint64_t)Jq, (uint64_t)KR, 3, 64, sketch ? 64 : 128)) return false;
+  if (!make_map(&mb, Bs, true, (uint64_t)bcols, (uint64_t)NB, (uint64_t)bcols, 64, (uint32_t)NB)) return false;
+  const int nrows = sketch ? J : (int)KR;
+  const int nmt = (nrows + tc::S2T_BM - 1) / tc::S2T_BM;
+  const int nks = (int)((sketch ? KR : (int64_t)Jq) + tc::S2T_BK - 1) / tc::S2T_BK;
+  const int grid = (int)std::min<int64_t>((int64_t)nmt * nch, num_sms);
+  bool ok = false;
+  DP2_LP_SWITCH(LP, (sketch ? s2_launch<true, L>(ma, mb, grid, nrows, nmt, nks, nch, part, status, s)
+                            : s2_launch<false, L>(ma, mb, grid, nrows, nmt, nks, nch, part, status, s),
+                     ok = true));
+  return ok;
+}
+
+int s2_tc_chunks(bool sketch, int64_t KR, int J, int Jq, int num_sms) {
+  const int nrows = sketch ? J : (int)KR;
+  const int nmt = (nrows + tc::S2T_BM - 1) / tc::S2T_BM;
+  const int nks = (int)((sketch ? KR : (int64_t)Jq) + tc::S2T_BK - 1) / tc::S2T_BK;
+  return s2_chunks(nmt, nks, num_sms);
+}
+
+void launch_s2_split_rhs(const float* F, int64_t nf, int LP, int64_t bcols, void* Bs, cudaStream_t s) {
+  const int64_t g = std::min<int64_t>((bcols + 255) / 256, 4096);
+  DP2_COUNTED(tc::k_s2_split_rhs<<<(unsigned)std::max<int64_t>(g, 1), 256, 0, s>>>(
+      F, nf, LP, s2_nb(LP), bcols, static_cast<__nv_bfloat16*>(Bs)));
+}
+
+void launch_ms_to_m(const void* Ms, int64_t pstride, int K, int J, int Jq, int R, float* M, cudaStream_t s) {
+  const int64_t n = (int64_t)K * J * R;
+  const int64_t g = std::min<int64_t>((n + 255) / 256, 8192);
+  DP2_COUNTED(tc::k_ms_to_m<<<(unsigned)std::max<int64_t>(g, 1), 256, 0, s>>>(
+      static_cast<const __nv_bfloat16*>(Ms), pstride, K, J, Jq, R, M));
 }
 
 }  // namespace dp2

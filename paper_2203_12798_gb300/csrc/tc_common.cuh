@@ -4,7 +4,7 @@
 // of the 128-byte-swizzled operand layout and the kind::f16 instruction
 // descriptor (device side); creation of tiled tensor maps through the
 // driver's cuTensorMapEncodeTiled (host side).  Used by k_tc.cu (stage-1
-// passes) and k_analytics.cu (similarity Gram).
+// passes), k_stage2.cu (stage-2 passes) and k_analytics.cu (similarity Gram).
 #pragma once
 #include <cuda.h>
 
@@ -221,6 +221,21 @@ inline bool make_map3_box(CUtensorMap* m, const void* base, bool bf16, uint64_t 
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 3-D map over [nz][ny][nx] BF16 elements stored contiguously, box {bx, by, 1}.
+inline bool make_map3_rows(CUtensorMap* m, const void* base, uint64_t nx, uint64_t ny, uint64_t nz, uint32_t bx,
+                           uint32_t by) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {nx, ny, nz};
+  cuuint64_t strides[2] = {nx * 2, nx * ny * 2};
+  cuuint32_t box[3] = {bx, by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
