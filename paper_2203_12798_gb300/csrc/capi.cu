@@ -248,8 +248,7 @@ void cholqr2(dpar2_ctx* ctx, float* Y, const int64_t* d_off, int K, int64_t maxI
   double* Gp = nsplit > 1 ? wsget<double>(ctx, (t + "_Gp").c_str(), (size_t)K * nsplit * LP * LP) : nullptr;
   launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-11, M1, nullptr, ctx->d_status, true, s);
-  launch_formq(Y, LP, d_off, K, (int)maxI, M1, s);
-  launch_gram_dd(Y, LP, d_off, K, ell, G, Gp, nsplit, s);
+  launch_formq_gram(Y, LP, d_off, K, ell, M1, G, Gp, nsplit, s);
   launch_chol_drop(G, K, ell, LP, 1e-6, M2, rank, ctx->d_status, false, s);
 }
 

@@ -62,6 +62,54 @@ __device__ inline void df_mac(DF& s, float a, float b) {
   s.lo += err + e;
 }
 __device__ inline double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+
+// Packed pairs of FP32 values in one 64-bit register and the f32x2
+// arithmetic of the sm_100 family (each half rounded as the scalar op),
+// used for two independent double-float accumulations per instruction.
+__device__ __forceinline__ uint64_t f2pack(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t add_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma_f2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// Two double-float accumulators (hi, lo pairs); df_mac2 is df_mac on both
+// halves: s += a b with a the packed multiplier and na = -a.
+struct DF2 {
+  uint64_t hi, lo;
+};
+__device__ __forceinline__ void df_mac2(DF2& s, uint64_t a, uint64_t na, uint64_t b) {
+  const uint64_t p = mul_f2(a, b);
+  const uint64_t ne = fma_f2(na, b, p);  // p - a b exactly: minus the rounding error of p
+  const uint64_t t = add_f2(s.hi, p);
+  const uint64_t bp = sub_f2(t, s.hi);
+  const uint64_t err = add_f2(sub_f2(s.hi, sub_f2(t, bp)), sub_f2(p, bp));
+  s.hi = t;
+  s.lo = add_f2(s.lo, sub_f2(err, ne));
+}
 // Double-float a + b (TwoSum of the high parts, low parts added, renormalised).
 __device__ inline DF df_add(DF a, DF b) {
   const float s = a.hi + b.hi;

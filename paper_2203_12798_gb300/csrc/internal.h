@@ -149,7 +149,10 @@ void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell
 // fp64: factorise in FP64 (first CholeskyQR step) or FP32 (second step).
 void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float* Minv, int* rank, int* status,
                       bool fp64, cudaStream_t s);
-void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s);
+// Y <- Y Minv_k per slice (Q1 of the first CholeskyQR step) and G = the Gram
+// of the new Y, in one pass (partials and their sum as launch_gram_dd)
+void launch_formq_gram(float* Y, int LP, const int64_t* d_off, int K, int ell, const float* Minv, double* G,
+                       double* Gpart, int nsplit, cudaStream_t s);
 void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s);
 void launch_gram_b1(const float* B1, int Jp, int J, int K, int ell, int LP, double* G, cudaStream_t s);
 void launch_eig_top(const double* G, const float* M2, int K, int ell, int LP, int R, float* T, float* lam,

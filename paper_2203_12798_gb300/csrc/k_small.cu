@@ -19,73 +19,161 @@ __device__ inline double warp_max_d(double v) {
 }
 
 // ----------------------------------------------------------------- Gram ----
-// G_k (ell x ell, pitch LP, FP64) = Y_k^T Y_k over the rows of slice k.
-constexpr int GR_THREADS = 256;
-constexpr int GR_ROWS = 64;
+// G_k (LP x LP, FP64) = Z_k^T Z_k over the rows of slice k, the rows split in
+// nsplit contiguous ranges (one per blockIdx.y, partial Grams summed after),
+// with Z = Y, or with FORMQ Z = Y Minv_k written back over Y (the first
+// CholeskyQR step's Q1, whose Gram is the second step's).  Double-float
+// accumulation of exact products (TwoProduct + TwoSum, about 48 significant
+// bits), register tiled: a thread owns a 4 x 4 tile of the upper block
+// triangle of the first 4 TE columns (TE = ceil(l / 4); columns past l are
+// zero) for the rows of its row group, so that two 16-byte shared-memory loads
+// feed 16 products, accumulated two at a time with packed f32x2 arithmetic;
+// chunks of 128 rows are staged by cp.async one chunk ahead; the row groups'
+// tiles are added in a fixed order at the end.
+constexpr int GT_THREADS = 256;
+constexpr int GT_ROWS = 128;
 
-// GR_MAXP = pair slots per thread, ceil(ell (ell + 1) / 2 / 256) (1 for ell <= 22).
-// Double-float accumulation of exact products (TwoProduct + TwoSum), two
-// independent accumulators per pair (even and odd rows).
-template <int GR_MAXP>
-__global__ void __launch_bounds__(GR_THREADS) k_gram_dd(const float* __restrict__ Y, int LP,
-                                                        const int64_t* __restrict__ off, int ell,
-                                                        double* __restrict__ G, int nsplit) {
-  extern __shared__ __align__(16) float ys[];
-  const int k = blockIdx.x, tid = threadIdx.x, split = blockIdx.y;
-  const int P = ell * (ell + 1) / 2;
-  int pa[GR_MAXP], pb[GR_MAXP];
-  DF acc[GR_MAXP];   // (hi, lo) double-float
-  DF acc2[GR_MAXP];  // second double-float accumulator (odd rows): two independent chains
-#pragma unroll
-  for (int i = 0; i < GR_MAXP; ++i) {
-    int p = tid + i * GR_THREADS;
-    int a = 0, b = 0;
-    if (p < P) {
-      while (p >= ell - a) { p -= ell - a; ++a; }
-      b = a + p;
-    }
-    pa[i] = a;
-    pb[i] = b;
-    acc[i].hi = 0.f;
-    acc[i].lo = 0.f;
-    acc2[i].hi = 0.f;
-    acc2[i].lo = 0.f;
+template <int LP, int TE>
+struct GramT {
+  static constexpr int NT = TE * (TE + 1) / 2;  // tiles
+  static constexpr int NG = GT_THREADS / NT;     // row groups
+  static constexpr int CH = GT_ROWS * LP;        // floats per staged chunk
+  static constexpr int RED = NG * NT * 16 * 2;   // floats of the group reduction
+  static constexpr int stage_floats(bool formq) { return 2 * CH + (formq ? CH + LP * LP : 0); }
+  static constexpr int smem(bool formq) {
+    return 4 * (stage_floats(formq) > RED ? stage_floats(formq) : RED);
   }
-  // rows of slice k, split in nsplit contiguous ranges (one per blockIdx.y)
-  const int64_t s0 = off[k], s1 = off[k + 1];
-  const int64_t chunk = round_up64((s1 - s0 + nsplit - 1) / nsplit, GR_ROWS);
-  const int64_t r0 = min64(s1, s0 + split * chunk), r1 = min64(s1, r0 + chunk);
-  for (int64_t rs = r0; rs < r1; rs += GR_ROWS) {
-    const int nr = (int)min64(GR_ROWS, r1 - rs);
-    __syncthreads();
-    for (int p = tid; p < nr * LP / 4; p += GR_THREADS)
-      reinterpret_cast<float4*>(ys)[p] = reinterpret_cast<const float4*>(Y + rs * LP)[p];
-    __syncthreads();
-    int i = 0;
-    for (; i + 1 < nr; i += 2) {
-      const float* y0 = ys + i * LP;
-      const float* y1 = y0 + LP;
+};
+
+template <int LP, int TE, bool FORMQ>
+__global__ void __launch_bounds__(GT_THREADS) k_gram_t(float* __restrict__ Y, const int64_t* __restrict__ off,
+                                                      const float* __restrict__ Minv, int ell,
+                                                      double* __restrict__ G, int nsplit) {
+  using C = GramT<LP, TE>;
+  constexpr int NT = C::NT, NG = C::NG, CH = C::CH;
+  extern __shared__ __align__(16) float gsm[];
+  float* ybuf = gsm;                          // 2 x CH: staged rows of Y
+  float* qbuf = gsm + 2 * CH;                 // CH: rows of Q1 (FORMQ)
+  float* msm = qbuf + CH;                     // LP x LP: Minv_k (FORMQ)
+  float2* red = reinterpret_cast<float2*>(gsm);  // NG x NT x 16 (after the last chunk)
+  const int k = blockIdx.x, split = blockIdx.y, tid = threadIdx.x;
+  const int grp = tid / NT, tt = tid % NT;
+  const bool act = grp < NG;
+  int ta = 0, tb = 0;
+  {
+    int p = tt;
+    while (p >= TE - ta) {
+      p -= TE - ta;
+      ++ta;
+    }
+    tb = ta + p;
+  }
+  DF2 acc[4][2];  // acc[a][h]: entries (4 ta + a, 4 tb + 2 h) and (.., 4 tb + 2 h + 1)
 #pragma unroll
-      for (int q = 0; q < GR_MAXP; ++q) {
-        df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
-        df_mac(acc2[q], y1[pa[q]], y1[pb[q]]);
+  for (int a = 0; a < 4; ++a) acc[a][0].hi = acc[a][0].lo = acc[a][1].hi = acc[a][1].lo = 0ull;
+  if (FORMQ)
+    for (int e = tid; e < LP * LP; e += GT_THREADS) msm[e] = Minv[(int64_t)k * LP * LP + e];
+  const int64_t s0 = off[k], s1 = off[k + 1];
+  const int64_t chunk = round_up64((s1 - s0 + nsplit - 1) / nsplit, GT_ROWS);
+  const int64_t r0 = min64(s1, s0 + split * chunk), r1 = min64(s1, r0 + chunk);
+  const int nch = (int)((r1 - r0 + GT_ROWS - 1) / GT_ROWS);
+  // rows rs .. rs + GT_ROWS - 1 (zero past r1) -> dst
+  auto stage = [&](int64_t rs, float* dst) {
+    const int nv = (int)min64(GT_ROWS, r1 - rs) * LP;
+    const float* src = Y + rs * LP;
+    for (int e = 4 * tid; e < CH; e += 4 * GT_THREADS) {
+      const bool ok = e < nv;
+      cp_async16(dst + e, ok ? src + e : Y, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  if (nch > 0) stage(r0, ybuf);
+  for (int c = 0; c < nch; ++c) {
+    const int64_t rs = r0 + (int64_t)c * GT_ROWS;
+    const int nr = (int)min64(GT_ROWS, r1 - rs);
+    const float* cur = ybuf + (c & 1) * CH;
+    if (c + 1 < nch) {
+      stage(rs + GT_ROWS, ybuf + ((c + 1) & 1) * CH);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float* z = cur;
+    if (FORMQ) {
+      // Q1 rows = Y rows Minv_k: two threads per row, LP / 2 columns each
+      constexpr int QC = LP / 2;
+      const int row = tid >> 1, cq = (tid & 1) * QC;
+      float q[QC];
+#pragma unroll
+      for (int u = 0; u < QC; ++u) q[u] = 0.f;
+      const float* yr = cur + row * LP;
+#pragma unroll 4
+      for (int i = 0; i < LP; ++i) {
+        const float yv = yr[i];
+#pragma unroll
+        for (int u = 0; u < QC; ++u) q[u] = fmaf(yv, msm[i * LP + cq + u], q[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < QC; ++u) qbuf[row * LP + cq + u] = q[u];
+      __syncthreads();
+      float4* dst = reinterpret_cast<float4*>(Y + rs * LP);
+      for (int e = tid; e < nr * LP / 4; e += GT_THREADS) dst[e] = reinterpret_cast<const float4*>(qbuf)[e];
+      z = qbuf;
+    }
+    if (act) {
+      for (int i = grp; i < nr; i += NG) {
+        const float4 va = *reinterpret_cast<const float4*>(z + i * LP + 4 * ta);
+        const float4 vb = *reinterpret_cast<const float4*>(z + i * LP + 4 * tb);
+        const float xa[4] = {va.x, va.y, va.z, va.w};
+        const uint64_t b01 = f2pack(vb.x, vb.y), b23 = f2pack(vb.z, vb.w);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const uint64_t a2 = f2pack(xa[a], xa[a]), na2 = f2pack(-xa[a], -xa[a]);
+          df_mac2(acc[a][0], a2, na2, b01);
+          df_mac2(acc[a][1], a2, na2, b23);
+        }
       }
     }
-    if (i < nr) {
-      const float* y0 = ys + i * LP;
-#pragma unroll
-      for (int q = 0; q < GR_MAXP; ++q) df_mac(acc[q], y0[pa[q]], y0[pb[q]]);
-    }
+    __syncthreads();  // the chunk's buffers are refilled next
   }
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 hi = f2unpack(acc[a][h].hi), lo = f2unpack(acc[a][h].lo);
+        red[(grp * NT + tt) * 16 + 4 * a + 2 * h] = make_float2(hi.x, lo.x);
+        red[(grp * NT + tt) * 16 + 4 * a + 2 * h + 1] = make_float2(hi.y, lo.y);
+      }
+  }
+  __syncthreads();
   double* g = G + ((int64_t)k * nsplit + split) * LP * LP;
-#pragma unroll
-  for (int q = 0; q < GR_MAXP; ++q) {
-    if (tid + q * GR_THREADS < P) {
-      const double v = df_value(acc[q]) + df_value(acc2[q]);
-      g[pa[q] * LP + pb[q]] = v;
-      g[pb[q] * LP + pa[q]] = v;
+  for (int e = tid; e < NT * 16; e += GT_THREADS) {
+    DF sum;
+    sum.hi = sum.lo = 0.f;
+    for (int gq = 0; gq < NG; ++gq) {
+      const float2 v = red[gq * NT * 16 + e];
+      DF d;
+      d.hi = v.x;
+      d.lo = v.y;
+      sum = df_add(sum, d);
+    }
+    int p = e / 16, ua = 0;
+    while (p >= TE - ua) {
+      p -= TE - ua;
+      ++ua;
+    }
+    const int a = 4 * ua + (e % 16) / 4, b = 4 * (ua + p) + e % 4;
+    if (a < LP && b < LP) {
+      // diagonal tiles hold (a, b) and (b, a): equal sums of equal products
+      const double v = a < ell && b < ell ? df_value(sum) : 0.0;
+      g[a * LP + b] = v;
+      g[b * LP + a] = v;
     }
   }
+  for (int e = tid; e < LP * LP; e += GT_THREADS)
+    if (e / LP >= 4 * TE || e % LP >= 4 * TE) g[e] = 0.0;
 }
 
 // ------------------------------------------------------- Cholesky (drop) ----
@@ -136,33 +224,6 @@ __global__ void __launch_bounds__(32) k_chol_drop(const double* __restrict__ G, 
     if (nd) set_status(status, ST_RANK_DROP);
     if (bad) set_status(status, ST_NONFINITE);
   }
-}
-
-// ------------------------------------------------------------- Q = Y Minv ----
-template <int LP>
-__global__ void __launch_bounds__(128) k_formq(float* __restrict__ Y, const int64_t* __restrict__ off,
-                                               const float* __restrict__ Minv) {
-  __shared__ __align__(16) float ms[LP * LP];
-  const int k = blockIdx.y;
-  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) ms[e] = Minv[(int64_t)k * LP * LP + e];
-  __syncthreads();
-  const int64_t row = off[k] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= off[k + 1]) return;
-  float y[LP], q[LP];
-#pragma unroll
-  for (int c4 = 0; c4 < LP / 4; ++c4) {
-    float4 v = reinterpret_cast<const float4*>(Y + row * LP)[c4];
-    y[4 * c4] = v.x; y[4 * c4 + 1] = v.y; y[4 * c4 + 2] = v.z; y[4 * c4 + 3] = v.w;
-  }
-#pragma unroll
-  for (int c = 0; c < LP; ++c) q[c] = 0.f;
-#pragma unroll
-  for (int i = 0; i < LP; ++i)
-#pragma unroll
-    for (int c = 0; c < LP; ++c) q[c] = fmaf(y[i], ms[i * LP + c], q[c]);
-#pragma unroll
-  for (int c4 = 0; c4 < LP / 4; ++c4)
-    reinterpret_cast<float4*>(Y + row * LP)[c4] = make_float4(q[4 * c4], q[4 * c4 + 1], q[4 * c4 + 2], q[4 * c4 + 3]);
 }
 
 // out[k] = sum_i part[k * n + i] in a fixed order.
@@ -847,31 +908,57 @@ __global__ void k_sum_splits(const double* __restrict__ Gpart, int nsplit, int K
   if (lane == 0) G[w] = s;
 }
 
-template <int NP>
-static void gram_np(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
-                    cudaStream_t s) {
-  const dim3 grid(K, nsplit);
-  const size_t smem = GR_ROWS * LP * sizeof(float);
-  DP2_COUNTED(k_gram_dd<NP><<<grid, GR_THREADS, smem, s>>>(Y, LP, d_off, ell, G, nsplit));
+template <int LP, int TE, bool FORMQ>
+static void gram_t_launch(float* Y, const int64_t* d_off, int K, int ell, const float* Minv, double* G, int nsplit,
+                          cudaStream_t s) {
+  constexpr int smem = GramT<LP, TE>::smem(FORMQ);
+  static bool attr = false;
+  if (!attr) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_gram_t<LP, TE, FORMQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  DP2_COUNTED(k_gram_t<LP, TE, FORMQ><<<dim3(K, nsplit), GT_THREADS, smem, s>>>(Y, d_off, Minv, ell, G, nsplit));
 }
 
-static void gram_dispatch(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, int nsplit,
-                          cudaStream_t s) {
-  const int np = (ell * (ell + 1) / 2 + GR_THREADS - 1) / GR_THREADS;
-  if (np <= 1) gram_np<1>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 2) gram_np<2>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 3) gram_np<3>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else if (np <= 5) gram_np<5>(Y, LP, d_off, K, ell, G, nsplit, s);
-  else gram_np<9>(Y, LP, d_off, K, ell, G, nsplit, s);
+// TE = ceil(ell / 4) when that is LP / 4 - 1 (LP = ell rounded up to 8),
+// else LP / 4 (a Gram of fewer columns than the pitch computes the rest and
+// writes zeros there)
+template <int LP, bool FORMQ>
+static void gram_t_dispatch(float* Y, const int64_t* d_off, int K, int ell, const float* Minv, double* G,
+                            int nsplit, cudaStream_t s) {
+  constexpr int T1 = LP / 4, T0 = LP / 4 > 1 ? LP / 4 - 1 : 1;
+  if ((ell + 3) / 4 == T0) gram_t_launch<LP, T0, FORMQ>(Y, d_off, K, ell, Minv, G, nsplit, s);
+  else gram_t_launch<LP, T1, FORMQ>(Y, d_off, K, ell, Minv, G, nsplit, s);
+}
+
+static void gram_run(float* Y, int LP, const int64_t* d_off, int K, int ell, const float* Minv, double* G,
+                     int nsplit, bool formq, cudaStream_t s) {
+  if (formq) {
+    DP2_LP_SWITCH(LP, (gram_t_dispatch<L, true>(Y, d_off, K, ell, Minv, G, nsplit, s)));
+  } else {
+    DP2_LP_SWITCH(LP, (gram_t_dispatch<L, false>(Y, d_off, K, ell, Minv, G, nsplit, s)));
+  }
 }
 
 void launch_gram_dd(const float* Y, int LP, const int64_t* d_off, int K, int ell, double* G, double* Gpart,
                     int nsplit, cudaStream_t s) {
+  float* Yw = const_cast<float*>(Y);  // read only without FORMQ
   if (nsplit <= 1 || !Gpart) {
-    gram_dispatch(Y, LP, d_off, K, ell, G, 1, s);
+    gram_run(Yw, LP, d_off, K, ell, nullptr, G, 1, false, s);
     return;
   }
-  gram_dispatch(Y, LP, d_off, K, ell, Gpart, nsplit, s);
+  gram_run(Yw, LP, d_off, K, ell, nullptr, Gpart, nsplit, false, s);
+  const int64_t n = (int64_t)LP * LP, warps = (int64_t)K * n;
+  DP2_COUNTED(k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G));
+}
+
+void launch_formq_gram(float* Y, int LP, const int64_t* d_off, int K, int ell, const float* Minv, double* G,
+                       double* Gpart, int nsplit, cudaStream_t s) {
+  if (nsplit <= 1 || !Gpart) {
+    gram_run(Y, LP, d_off, K, ell, Minv, G, 1, true, s);
+    return;
+  }
+  gram_run(Y, LP, d_off, K, ell, Minv, Gpart, nsplit, true, s);
   const int64_t n = (int64_t)LP * LP, warps = (int64_t)K * n;
   DP2_COUNTED(k_sum_splits<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Gpart, nsplit, K, (int)n, G));
 }
@@ -887,11 +974,6 @@ void launch_chol_drop(const double* G, int K, int ell, int LP, double tau, float
     DP2_COUNTED(k_chol_drop<double><<<K, 32, 2 * ell * ell * sizeof(double), s>>>(G, ell, LP, tau, Minv, rank, status));
   else
     DP2_COUNTED(k_chol_drop<float><<<K, 32, 2 * ell * ell * sizeof(float), s>>>(G, ell, LP, tau, Minv, rank, status));
-}
-
-void launch_formq(float* Y, int LP, const int64_t* d_off, int K, int maxI, const float* M1, cudaStream_t s) {
-  dim3 grid((maxI + 127) / 128, K);
-  DP2_LP_SWITCH(LP, (DP2_COUNTED(k_formq<L><<<grid, 128, 0, s>>>(Y, d_off, M1))));
 }
 
 void launch_reduce_rows_f64(const double* part, int K, int n, double* out, cudaStream_t s) {
