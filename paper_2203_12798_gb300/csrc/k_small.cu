@@ -803,10 +803,38 @@ __global__ void k_seg_product(const float* __restrict__ In, int ldin, int nin, c
   float o[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) o[r] = 0.f;
-  for (int c = 0; c < nin; ++c) {
-    const float v = in[c];
+  if ((ldin & 3) == 0 && (nin & 3) == 0 && (reinterpret_cast<uintptr_t>(In) & 15) == 0) {
+    // 16-byte loads, four of them issued before their products
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    int c4 = 0;
+    for (; c4 + 4 <= nin / 4; c4 += 4) {
+      float4 v[4];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) o[r] = fmaf(v, tsm[c * NB + r], o[r]);
+      for (int u = 0; u < 4; ++u) v[u] = in4[c4 + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < NB; ++r) o[r] = fmaf(w[q], tsm[(4 * (c4 + u) + q) * NB + r], o[r]);
+      }
+    }
+    for (; c4 < nin / 4; ++c4) {
+      const float4 v = in4[c4];
+      const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < NB; ++r) o[r] = fmaf(w[q], tsm[(4 * c4 + q) * NB + r], o[r]);
+    }
+  } else {
+#pragma unroll 4
+    for (int c = 0; c < nin; ++c) {
+      const float v = in[c];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) o[r] = fmaf(v, tsm[c * NB + r], o[r]);
+    }
   }
   float* out = Out + row * ldout;
 #pragma unroll
