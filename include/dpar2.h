@@ -198,7 +198,7 @@ DPAR2_API dpar2_status dpar2_compress(dpar2_ctx* ctx, int K, int J, const int64_
  *                (dpar2_reconstruct_error's streamed mode); or NULL: chunk
  *                buffers of the context are used and X is not kept.  ldx: as for
  *                dpar2_compress (ignored when X_dev is NULL).
- *   chunk_bytes  target bytes of X per chunk (0: 1 GB); a chunk holds at
+ *   chunk_bytes  target bytes of X per chunk (0: 2 GB); a chunk holds at
  *                least one slice.  Context scratch: three staging buffers of
  *                the largest chunk (unless ldx == J) and, without X_dev, three
  *                chunk buffers of it; copies run up to three chunks ahead.

@@ -104,18 +104,24 @@ __global__ void __launch_bounds__(GT_THREADS) k_gram_t(float* __restrict__ Y, co
       // Q1 rows = Y rows Minv_k: two threads per row, LP / 2 columns each
       constexpr int QC = LP / 2;
       const int row = tid >> 1, cq = (tid & 1) * QC;
-      float q[QC];
+      float2 q[QC / 2];  // packed FP32 FMAs over column pairs
 #pragma unroll
-      for (int u = 0; u < QC; ++u) q[u] = 0.f;
+      for (int u = 0; u < QC / 2; ++u) q[u] = make_float2(0.f, 0.f);
       const float* yr = cur + row * LP;
 #pragma unroll 4
       for (int i = 0; i < LP; ++i) {
-        const float yv = yr[i];
+        const float2 yv = make_float2(yr[i], yr[i]);
+        const float4* m4 = reinterpret_cast<const float4*>(msm + i * LP + cq);
 #pragma unroll
-        for (int u = 0; u < QC; ++u) q[u] = fmaf(yv, msm[i * LP + cq + u], q[u]);
+        for (int u = 0; u < QC / 4; ++u) {
+          const float4 m = m4[u];
+          q[2 * u] = ffma2(yv, make_float2(m.x, m.y), q[2 * u]);
+          q[2 * u + 1] = ffma2(yv, make_float2(m.z, m.w), q[2 * u + 1]);
+        }
       }
+      float4* qo = reinterpret_cast<float4*>(qbuf + row * LP + cq);
 #pragma unroll
-      for (int u = 0; u < QC; ++u) qbuf[row * LP + cq + u] = q[u];
+      for (int u = 0; u < QC / 4; ++u) qo[u] = make_float4(q[2 * u].x, q[2 * u].y, q[2 * u + 1].x, q[2 * u + 1].y);
       __syncthreads();
       float4* dst = reinterpret_cast<float4*>(Y + rs * LP);
       for (int e = tid; e < nr * LP / 4; e += GT_THREADS) dst[e] = reinterpret_cast<const float4*>(qbuf)[e];
