@@ -333,6 +333,8 @@ def main_ours(args):
         e1.record()
         barrier()
         n_launch = api.kernel_launches() - n_launch0
+    # the tensor-core projection's (schedule, work-item width) the timed steps used
+    pj_sched, pj_cols = ctx.projection_config()
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         tt = torch.tensor([ms], device="cuda")
@@ -475,7 +477,11 @@ def main_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-               "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": workload_config(args),
+               "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+               "config": dict(workload_config(args), projection=(
+                   {"schedule": ["round-robin", "longest-slices-first"][pj_sched], "cols_per_item": pj_cols,
+                    "chosen_by": "autotuner (both schedules x both widths timed on the first compression)"}
+                   if pj_sched >= 0 else None)),
                "roofline": {"bound": "hbm", "kernel": f"stage-1 {dom} pass", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": measured_traffic(dom, dom_bytes, args),
                             "peak_source": peak_src,

@@ -89,6 +89,14 @@ typedef struct {
                      the least-loaded CTA; -1 = autotuned (both timed on the first
                      compression of a problem shape, the faster kept by the context) */
   unsigned flags; /* DPAR2_FLAG_* */
+  int proj_cols;  /* X columns per work item of the tensor-core projection: 0 = the widest
+                     that TMEM holds double-buffered (512 for l <= 21, 256 for l <= 32, 128
+                     above), or that width halved (256 / 128); with schedule = -1 and
+                     proj_cols = 0 both widths are timed with both schedules on the first
+                     compression of a problem shape and the fastest pair is kept.  Every
+                     width computes each column of B_k identically; ||X_k||^2 is summed in
+                     FP32 within each work item, so it differs between the widths at the
+                     FP32 rounding level (the schedule changes nothing) */
 } dpar2_options;
 
 typedef struct dpar2_ctx dpar2_ctx;
@@ -123,7 +131,7 @@ typedef struct {
   int32_t* rank1; /* per-slice numerical rank of the stage-1 sketch (device, K) */
 } dpar2_comp_view;
 
-/* Fill *opt with R=10, p=10, q=0, seed=0, max_iter=32, tol=-1, schedule=-1. */
+/* Fill *opt with R=10, p=10, q=0, seed=0, max_iter=32, tol=-1, schedule=-1, proj_cols=0. */
 DPAR2_API dpar2_status dpar2_options_default(dpar2_options* opt);
 
 /* Create a context bound to CUDA device `device`.  Owns scratch memory that
@@ -307,6 +315,11 @@ DPAR2_API size_t dpar2_comp_bytes(const dpar2_comp* comp);
 /* Device bytes the object actually holds (adds B_k, M, ||X_k||^2, offsets). */
 DPAR2_API size_t dpar2_comp_device_bytes(const dpar2_comp* comp);
 DPAR2_API dpar2_status dpar2_comp_view_get(const dpar2_comp* comp, dpar2_comp_view* view);
+/* The tensor-core projection's slice-to-CTA schedule (0 round-robin, 1
+ * longest slices first) and X columns per work item used by the context's
+ * last compression (the autotuned pair when it was tuned); -1 / 0 if none ran
+ * (FP32 X, CUDA-core passes).  Host values; the paper has no counterpart. */
+DPAR2_API dpar2_status dpar2_projection_config(const dpar2_ctx* ctx, int* schedule, int* cols);
 /* M (device K x J x R FP32, block k = C_k B_k) reassembled from the three BF16
  * parts of M^T the compression holds (inspection; stream-ordered on `stream`,
  * NULL = the context's stream).  Errors: INVALID_ARG for a null argument or a

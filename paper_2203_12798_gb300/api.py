@@ -34,7 +34,7 @@ class Dpar2Error(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("schedule", ctypes.c_int),
-                ("flags", ctypes.c_uint)]
+                ("flags", ctypes.c_uint), ("proj_cols", ctypes.c_int)]
 
 
 class CompView(ctypes.Structure):
@@ -69,6 +69,7 @@ SIGNATURES = {
     "dpar2_comp_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_device_bytes": (ctypes.c_size_t, [VP]),
     "dpar2_comp_view_get": (ctypes.c_int, [VP, ctypes.POINTER(CompView)]),
+    "dpar2_projection_config": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "dpar2_comp_m": (ctypes.c_int, [VP, VP, VP, VP]),
     "dpar2_comp_free": (None, [VP]),
     "dpar2_sketch_loss_fwd": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), VP,
@@ -188,7 +189,7 @@ class Context:
 
     # ------------------------------------------------------------- method
     def compress(self, X: torch.Tensor, offsets, R=10, p=10, q=0, seed=0, omega=None, omega2=None, flags=0,
-                 J=None, schedule=-1) -> "Compressed":
+                 J=None, schedule=-1, proj_cols=0) -> "Compressed":
         """X: CUDA tensor (sum I_k) x ldx of float32/bfloat16/float16 (columns >= J ignored)."""
         assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
         J = X.shape[1] if J is None else J
@@ -197,6 +198,7 @@ class Context:
         opt = Options()
         lib().dpar2_options_default(ctypes.byref(opt))
         opt.R, opt.p, opt.q, opt.seed, opt.flags, opt.schedule = R, p, q, seed, flags, schedule
+        opt.proj_cols = proj_cols
         h = ctypes.c_void_p()
         offp = ctypes.cast(off.data_ptr(), ctypes.POINTER(ctypes.c_int64))
         self._check(lib().dpar2_compress(self._h, K, J, offp, _ptr(X), X.stride(0), _DT[X.dtype],
@@ -205,7 +207,7 @@ class Context:
         return Compressed(self, h, off)
 
     def compress_host(self, Xh: torch.Tensor, offsets, R=10, p=10, q=0, seed=0, omega=None, omega2=None, flags=0,
-                      X_dev=None, chunk_bytes=0, schedule=-1) -> "Compressed":
+                      X_dev=None, chunk_bytes=0, schedule=-1, proj_cols=0) -> "Compressed":
         """Xh: host tensor (sum I_k) x J of float32/bfloat16/float16, packed rows
         (pin_memory() for asynchronous copies); X_dev: optional CUDA tensor
         (sum I_k) x ldx receiving X."""
@@ -216,6 +218,7 @@ class Context:
         opt = Options()
         lib().dpar2_options_default(ctypes.byref(opt))
         opt.R, opt.p, opt.q, opt.seed, opt.flags, opt.schedule = R, p, q, seed, flags, schedule
+        opt.proj_cols = proj_cols
         h = ctypes.c_void_p()
         offp = ctypes.cast(off.data_ptr(), ctypes.POINTER(ctypes.c_int64))
         ldx = X_dev.stride(0) if X_dev is not None else 0
@@ -223,6 +226,13 @@ class Context:
                                               ctypes.byref(opt), _ptr(omega), _ptr(omega2), _ptr(X_dev), ldx,
                                               chunk_bytes, ctypes.byref(h), _stream()))
         return Compressed(self, h, off)
+
+    def projection_config(self):
+        """(schedule, columns per work item) of the last compression's tensor-core
+        projection; (-1, 0) if none ran."""
+        sch, cols = ctypes.c_int(-1), ctypes.c_int(0)
+        self._check(lib().dpar2_projection_config(self._h, ctypes.byref(sch), ctypes.byref(cols)))
+        return sch.value, cols.value
 
     def fit(self, comp: "Compressed", max_iter=32, tol=-1.0, seed=0, V0=None, want_U=False, want_upol=True,
             fitness=True, flags=0):

@@ -356,14 +356,40 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
   // column block, norm warp)
   std::vector<int64_t> hp, htoff;
   int64_t maxPad = 0;
-  ProjSched pj;  // the projection's slice-to-CTA schedule (choice -1: tune on this call)
+  ProjSched pj;  // the projection's slice-to-CTA schedule for its first candidate
   const std::string tkey = tune_key(Kc, J, ell, dtype, N, maxI);
   int64_t* d_poff = nullptr;
   void* Qs = nullptr;
   double* xp = nullptr;
   int PNS = 0, POFF = 0;  // layout of the projection's Q operand
   proj_layout(ell, &PNS, &POFF);
-  const int nJb_tc = (Jp + project_tc_cols(PNS) - 1) / project_tc_cols(PNS);
+  // (schedule, work-item width) pairs of the projection: the options' fixed
+  // pair, the pair tuned before for this problem shape, or every candidate
+  // (both schedules, both widths unless one is given) timed on this call
+  auto njb_of = [&](int hv) { return (Jp + project_tc_cols(PNS, hv) - 1) / project_tc_cols(PNS, hv); };
+  const int hv_fixed = opt->proj_cols / 128;
+  const std::string tkey_w = tkey + ":w" + std::to_string(hv_fixed);
+  std::vector<std::pair<int, int>> pj_cand;
+  if (opt->schedule >= 0) {
+    pj_cand.push_back({opt->schedule > 1 ? 0 : opt->schedule, hv_fixed ? hv_fixed : project_hv_default(PNS)});
+  } else {
+    auto it = ctx->tuned.find(tkey_w);
+    if (it != ctx->tuned.end()) {
+      pj_cand.push_back({it->second & 1, it->second >> 1});
+    } else {
+      for (int sch = 0; sch < 2; ++sch) {
+        if (hv_fixed) {
+          pj_cand.push_back({sch, hv_fixed});
+        } else {
+          pj_cand.push_back({sch, project_hv_default(PNS)});
+          if (project_hv_alt(PNS)) pj_cand.push_back({sch, project_hv_alt(PNS)});
+        }
+      }
+    }
+  }
+  int nJb_max = 0;
+  for (auto& c : pj_cand) nJb_max = std::max(nJb_max, njb_of(c.second));
+  const int pj_hv0 = pj_cand[0].second, nJb_tc = njb_of(pj_hv0);
   if (use_tc) {
     hp.assign(Kc + 1, 0);
     for (int k = 0; k < Kc; ++k) {
@@ -374,14 +400,8 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
     d_poff = wsget<int64_t>(ctx, "poff", (size_t)Kc + 1);
     h2d_i64(ctx, d_poff, hp.data(), (Kc + 1), s);
     Qs = wsget<uint16_t>(ctx, "Qs", (size_t)PNS * hp[Kc]);
-    xp = wsget<double>(ctx, "xpart_tc", (size_t)Kc * nJb_tc * kProjNormWarps);
-    int choice = opt->schedule;
-    if (choice < 0) {
-      auto it = ctx->tuned.find(tkey);
-      if (it != ctx->tuned.end()) choice = it->second;
-    }
-    pj = proj_sched(ctx, choice > 1 ? 0 : choice, off, Kc, nJb_tc, tkey, s);
-    if (choice < 0) pj.choice = -1;
+    xp = wsget<double>(ctx, "xpart_tc", (size_t)Kc * nJb_max * kProjNormWarps);
+    pj = proj_sched(ctx, pj_cand[0].first, off, Kc, nJb_tc, tkey, s);
   }
   // ---- power iterations Y <- X (X^T Q), re-orthonormalised ----
   int64_t* d_toff = nullptr;
@@ -398,7 +418,7 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
       // row scales of the operand), which leave the next CholeskyQR2's Q unchanged
       launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, Kc, hp[Kc], maxPad, dtype, Qs, s);
       bool ok = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, hp[Kc], PNS, POFF, LP, B1, xp, nJb_tc, true,
-                                  ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
+                                  ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists, pj_hv0);
       require(ok, DPAR2_ERR_CUDA, "tensor map encoding failed");
       void* Ms = wsget<uint16_t>(ctx, "Ms", (size_t)Kc * 3 * LPN * Jpad);
       launch_sl_rowsplit(B1, Kc, Jp, J, Jpad, ell, LP, LPN, dtype, Ms, nullptr,
@@ -424,36 +444,61 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
     const int64_t Npad = hp[Kc];
     launch_qsplit(Y, LP, PNS, POFF, d_off, d_poff, Kc, Npad, maxPad, dtype, Qs, s);
     tb(DPAR2_PH_PROJECT);
-    if (pj.choice < 0) {
-      // autotune: time both schedules on this call's projection (identical
-      // results) and keep the faster for this problem shape
-      cudaEvent_t ev[3];
+    int nJb_last = nJb_tc;
+    if (pj_cand.size() > 1) {
+      // autotune: time every candidate on this call's projection (the same B1;
+      // ||X_k||^2 partials laid out per width) and keep the fastest pair for
+      // this problem shape
+      const int nc = (int)pj_cand.size();
+      std::vector<cudaEvent_t> ev(nc + 1);
       for (auto& e : ev) CK(cudaEventCreate(&e));
-      const ProjSched cand[2] = {proj_sched(ctx, 0, off, Kc, nJb_tc, tkey, s),
-                                 proj_sched(ctx, 1, off, Kc, nJb_tc, tkey, s)};
       CK(cudaEventRecord(ev[0], s));
-      for (int c = 0; c < 2; ++c) {
-        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
-                                      true, ctx->num_sms, ctx->d_status, s, cand[c].lptr, cand[c].items,
-                                      cand[c].nlists);
+      for (int c = 0; c < nc; ++c) {
+        const ProjSched cs = proj_sched(ctx, pj_cand[c].first, off, Kc, njb_of(pj_cand[c].second), tkey, s);
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp,
+                                      njb_of(pj_cand[c].second), true, ctx->num_sms, ctx->d_status, s, cs.lptr,
+                                      cs.items, cs.nlists, pj_cand[c].second);
         CK(cudaEventRecord(ev[c + 1], s));
       }
-      CK(cudaEventSynchronize(ev[2]));
-      float t0 = 0.f, t1 = 0.f;
-      CK(cudaEventElapsedTime(&t0, ev[0], ev[1]));
-      CK(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+      CK(cudaEventSynchronize(ev[nc]));
+      int best = 0;
+      float tbest = 0.f;
+      for (int c = 0; c < nc; ++c) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev[c], ev[c + 1]));
+        if (c == 0 || t < tbest) {
+          tbest = t;
+          best = c;
+        }
+      }
       for (auto& e : ev) cudaEventDestroy(e);
-      ctx->tuned[tkey] = t1 < t0 ? 1 : 0;
+      ctx->tuned[tkey_w] = pj_cand[best].first + 2 * pj_cand[best].second;
+      ctx->pj_last_schedule = pj_cand[best].first;
+      ctx->pj_last_cols = project_tc_cols(PNS, pj_cand[best].second);
+      nJb_last = njb_of(pj_cand[nc - 1].second);
+      if (pj_cand[best].second != pj_cand[nc - 1].second) {
+        // the ||X_k||^2 partials (FP32 within a work item) follow the width:
+        // leave those of the chosen width, as later calls of this shape will
+        const ProjSched cs = proj_sched(ctx, pj_cand[best].first, off, Kc, njb_of(pj_cand[best].second), tkey, s);
+        projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp,
+                                      njb_of(pj_cand[best].second), true, ctx->num_sms, ctx->d_status, s, cs.lptr,
+                                      cs.items, cs.nlists, pj_cand[best].second);
+        nJb_last = njb_of(pj_cand[best].second);
+      }
     } else {
       projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp, nJb_tc,
-                                    true, ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists);
+                                    true, ctx->num_sms, ctx->d_status, s, pj.lptr, pj.items, pj.nlists, pj_hv0);
+      ctx->pj_last_schedule = pj_cand[0].first;
+      ctx->pj_last_cols = project_tc_cols(PNS, pj_hv0);
     }
     if (projected) {
       xpart = xp;
-      nJb_used = nJb_tc * kProjNormWarps;
+      nJb_used = nJb_last * kProjNormWarps;
     }
   } else {
     tb(DPAR2_PH_PROJECT);
+    ctx->pj_last_schedule = -1;
+    ctx->pj_last_cols = 0;
   }
   if (projected) {
   } else if (opt->flags & DPAR2_FLAG_PER_SLICE) {
@@ -570,6 +615,14 @@ dpar2_status check_compress(dpar2_ctx* ctx, int K, int J, const int64_t* row_off
     require(opt->R >= 1 && opt->R <= kMaxR && opt->R <= J, DPAR2_ERR_SHAPE, "need 1 <= R <= min(J, 64)");
     require(opt->p >= 0 && opt->R + opt->p <= std::min(J, kMaxEll), DPAR2_ERR_SHAPE, "need R + p <= min(J, 64)");
     require(opt->q >= 0 && opt->q <= 8, DPAR2_ERR_INVALID_ARG, "need 0 <= q <= 8");
+    {
+      int ns = 0, offp = 0;
+      proj_layout(opt->R + opt->p, &ns, &offp);
+      const int hv = opt->proj_cols / 128;
+      require(opt->proj_cols == 0 || (opt->proj_cols % 128 == 0 &&
+                                      (hv == project_hv_default(ns) || hv == project_hv_alt(ns))),
+              DPAR2_ERR_INVALID_ARG, "proj_cols must be 0 or a work-item width of the projection for this l");
+    }
     require(ldx >= J, DPAR2_ERR_SHAPE, "ldx < J");
     require((ldx * (int64_t)dtype_size(dtype)) % 16 == 0, DPAR2_ERR_INVALID_ARG,
             "ldx * sizeof(dtype) must be a multiple of 16 bytes");
@@ -679,6 +732,7 @@ dpar2_status dpar2_options_default(dpar2_options* opt) {
   opt->tol = -1.0;
   opt->schedule = -1;
   opt->flags = 0;
+  opt->proj_cols = 0;
   return DPAR2_OK;
 }
 
@@ -1400,6 +1454,13 @@ dpar2_status dpar2_comp_view_get(const dpar2_comp* c, dpar2_comp_view* v) {
   v->Ft = static_cast<const float*>(c->Ft.p);
   v->xnorm2 = static_cast<const double*>(c->xnorm2.p);
   v->rank1 = static_cast<int32_t*>(c->rank1.p);
+  return DPAR2_OK;
+}
+
+dpar2_status dpar2_projection_config(const dpar2_ctx* ctx, int* schedule, int* cols) {
+  if (!ctx || !schedule || !cols) return DPAR2_ERR_INVALID_ARG;
+  *schedule = ctx->pj_last_schedule;
+  *cols = ctx->pj_last_cols;
   return DPAR2_OK;
 }
 

@@ -50,6 +50,7 @@ struct dpar2_ctx {
   // autotuned choices (projection schedule) per problem shape
   std::map<std::string, int> tuned;
   std::string pj_lists_key;  // problem shape whose projection work lists are on the device
+  int pj_last_schedule = -1, pj_last_cols = 0;  // the last compression's projection (schedule, width)
   // pinned host staging for the small index tables a call copies to the device
   // (asynchronous copies; a call's regions are reused by the next call, after
   // the synchronisation every call ends with)
@@ -104,12 +105,20 @@ void proj_layout(int ell, int* NS, int* OFF);
 // two that launch_project_tc divides out when called with qscale
 void launch_qsplit(const float* Q, int LP, int NS, int OFF, const int64_t* d_off, const int64_t* d_poff, int K,
                    int64_t Npad, int64_t maxPad, dpar2_dtype dt, void* out, cudaStream_t s);
-// X columns per work item of the tensor-core projection (nJb = ceil(Jp / cols))
-int project_tc_cols(int NS);
+// Work-item width of the tensor-core projection in halves of 128 columns:
+// the default (as many as TMEM holds double-buffered) and the narrower
+// candidate the autotuner also times (0: none)
+int project_hv_default(int NS);
+int project_hv_alt(int NS);
+// X columns per work item of the tensor-core projection (nJb = ceil(Jp / cols));
+// hv 0 = the default width
+int project_tc_cols(int NS, int hv = 0);
+// false if no tensor map could be made or hv is not a width of this NS
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int NS, int OFF,
                        int LP, float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status,
-                       cudaStream_t s, const int* lptr = nullptr, const int* items = nullptr, int nlists = 0);
+                       cudaStream_t s, const int* lptr = nullptr, const int* items = nullptr, int nlists = 0,
+                       int hv = 0);
 // Work lists of the tensor-core projection (items k nJb + jb): longest slices
 // first, each onto the least-loaded of `nlists` CTAs.  Host side; lptr gets
 // nlists + 1 entries, items K nJb.

@@ -399,15 +399,17 @@ constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
 constexpr int PJ_NORM_WARPS = kProjNormWarps;          // warps 6 .. 6 + PJ_NORM_WARPS - 1
 constexpr int PJ_THREADS = 32 * (6 + PJ_NORM_WARPS);
 
-template <int NS_>
+template <int NS_, int HV_ = (NS_ <= 64 ? 4 : (NS_ <= 128 ? 2 : 1))>
 struct ProjSmem {
   // NS = MMA N: the three 16-bit parts of the Q rows, part t of column c in
   // row t OFF + c (OFF = l rounded up to 4, or 32 / 64), padded to 48, 64, 96
-  // or 192.  HV column halves of PJ_BM columns per work item, as many as let
-  // the double-buffered accumulators (2 HV NS columns) fit TMEM's 512: wider
-  // rows per TMA load, one Q tile per stage for all halves.
+  // or 192.  HV column halves of PJ_BM columns per work item: by default as
+  // many as let the double-buffered accumulators (2 HV NS columns) fit TMEM's
+  // 512 (wider rows per TMA load, one Q tile per stage for all halves); half
+  // as many is the narrower candidate the autotuner also times.
   static constexpr int NS = NS_;
-  static constexpr int HV = NS <= 64 ? 4 : (NS <= 128 ? 2 : 1);
+  static constexpr int HV = HV_;
+  static_assert(2 * HV * NS <= 512, "double-buffered accumulators within TMEM");
   static constexpr int A = HV * PJ_BM * PJ_BK * 2;  // 2 HV 64-column boxes of 64 rows, 8 KB each
   static constexpr int B = NS * PJ_BK * 2;
   static constexpr int FIT = (227 * 1024 - 1024 - 256) / (A + B);
@@ -428,7 +430,7 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int NS>
+template <int NS, int HV>
 __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_constant__ CUtensorMap tmX,
                                                        const __grid_constant__ CUtensorMap tmQ,
                                                        const int64_t* __restrict__ off,
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
                                                        double* __restrict__ xpart, int nJb, int bf16, int qscale,
                                                        const int* __restrict__ lptr, const int* __restrict__ items,
                                                        int* status) {
-  using S = ProjSmem<NS>;
+  using S = ProjSmem<NS, HV>;
   constexpr int ST = S::STAGES;
   constexpr uint32_t NCOL = 2 * S::HV * S::NS <= 256 ? 256 : 512;
   extern __shared__ uint8_t smem_raw[];
@@ -882,33 +884,33 @@ void proj_layout(int ell, int* NS, int* OFF) {
   *NS = 3 * o <= 48 ? 48 : (3 * o <= 64 ? 64 : 96);
 }
 
-int project_tc_cols(int NS) {
-  switch (NS) {
-    case 48: return tc::ProjSmem<48>::COLS;
-    case 64: return tc::ProjSmem<64>::COLS;
-    case 96: return tc::ProjSmem<96>::COLS;
-    default: return tc::ProjSmem<192>::COLS;
-  }
-}
+int project_hv_default(int NS) { return NS <= 64 ? 4 : (NS <= 128 ? 2 : 1); }
+int project_hv_alt(int NS) { return NS <= 128 ? project_hv_default(NS) / 2 : 0; }
 
-template <int NS>
+int project_tc_cols(int NS, int hv) { return (hv > 0 ? hv : project_hv_default(NS)) * tc::PJ_BM; }
+
+template <int NS, int HV>
 static void project_launch(const CUtensorMap& mx, const CUtensorMap& mq, int grid, const int64_t* d_off,
                            const int64_t* d_poff, int K, int J, int Jp, int LP, int OFF, float* B1, double* xpart,
                            int nJb, int bf, int qs, const int* lptr, const int* items, int* status, cudaStream_t s) {
+  using S = tc::ProjSmem<NS, HV>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc::k_project_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::ProjSmem<NS>::BYTES);
+    cudaFuncSetAttribute(tc::k_project_tc<NS, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
     attr = true;
   }
-  DP2_COUNTED(tc::k_project_tc<NS><<<grid, tc::PJ_THREADS, tc::ProjSmem<NS>::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, OFF,
-                                                                           B1, xpart, nJb, bf, qs, lptr, items, status));
+  DP2_COUNTED(tc::k_project_tc<NS, HV><<<grid, tc::PJ_THREADS, S::BYTES, s>>>(mx, mq, d_off, d_poff, K, J, Jp, LP, OFF,
+                                                                             B1, xpart, nJb, bf, qs, lptr, items,
+                                                                             status));
 }
 
 bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, const int64_t* d_off,
                        const int64_t* d_poff, int K, int J, int Jp, const void* Qs, int64_t Npad, int NS, int OFF,
                        int LP, float* B1, double* xpart, int nJb, bool qscale, int num_sms, int* status,
-                       cudaStream_t s, const int* lptr, const int* items, int nlists) {
+                       cudaStream_t s, const int* lptr, const int* items, int nlists, int hv) {
   const bool bf = dt == DPAR2_BF16;
+  if (hv <= 0) hv = project_hv_default(NS);
+  if (hv != project_hv_default(NS) && hv != project_hv_alt(NS)) return false;
   CUtensorMap mx, mq;
   // no L2 promotion: a box row (128 bytes) of X starts anywhere on a 16-byte
   // boundary, so 256-byte promotion fetches neighbouring columns that belong to
@@ -919,13 +921,19 @@ bool launch_project_tc(const void* X, dpar2_dtype dt, int64_t ldx, int64_t N, co
   if (!make_map3(&mq, Qs, bf, (uint64_t)tc::PJ_BK, (uint64_t)NS, (uint64_t)(Npad / tc::PJ_BK))) return false;
   const int grid = lptr ? nlists : (int)std::min<int64_t>((int64_t)K * nJb, num_sms);
   const int bfi = bf ? 1 : 0, qs = qscale ? 1 : 0;
-  switch (NS) {
-    case 48: project_launch<48>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
-    case 64: project_launch<64>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
-    case 96: project_launch<96>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
-    case 192: project_launch<192>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s); break;
+#define DP2_PJ(NSV, HVV) \
+  project_launch<NSV, HVV>(mx, mq, grid, d_off, d_poff, K, J, Jp, LP, OFF, B1, xpart, nJb, bfi, qs, lptr, items, status, s)
+  switch (NS * 8 + hv) {
+    case 48 * 8 + 4: DP2_PJ(48, 4); break;
+    case 48 * 8 + 2: DP2_PJ(48, 2); break;
+    case 64 * 8 + 4: DP2_PJ(64, 4); break;
+    case 64 * 8 + 2: DP2_PJ(64, 2); break;
+    case 96 * 8 + 2: DP2_PJ(96, 2); break;
+    case 96 * 8 + 1: DP2_PJ(96, 1); break;
+    case 192 * 8 + 1: DP2_PJ(192, 1); break;
     default: return false;
   }
+#undef DP2_PJ
   return true;
 }
 

@@ -40,5 +40,5 @@ def test_options_default_through_abi():
 
     o = api.Options()
     assert api.lib().dpar2_options_default(ctypes.byref(o)) == 0
-    assert (o.R, o.p, o.q, o.max_iter, o.tol, o.schedule) == (10, 10, 0, 32, -1.0, -1)
+    assert (o.R, o.p, o.q, o.max_iter, o.tol, o.schedule, o.proj_cols) == (10, 10, 0, 32, -1.0, -1, 0)
     assert api.lib().dpar2_options_default(None) == 1

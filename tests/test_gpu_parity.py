@@ -163,8 +163,9 @@ def test_power_iteration_matches_oracle(api, ctx, dtype, q):
 
 
 def test_projection_schedules_agree(api, ctx):
-    # round-robin work items, longest-first work lists and the autotuned
-    # choice compute every (slice, column block) item the same way
+    # round-robin work items, longest-first work lists, both work-item widths
+    # and the autotuned choice compute every (slice, column block) item the
+    # same way
     rng = np.random.default_rng(5)
     I = np.concatenate([rng.integers(20, 200, 60), [1500, 900, 3000]])
     off = torch.zeros(len(I) + 1, dtype=torch.int64)
@@ -177,9 +178,32 @@ def test_projection_schedules_agree(api, ctx):
     for sch in (0, 1, -1, -1):
         c = ctx.compress(Xd, off, R=10, p=10, omega=om, omega2=om2, J=300, schedule=sch)
         outs.append(c.tensors())
+    # ||X_k||^2 is summed in FP32 within each work item, so it depends on the
+    # width (at the FP32 level) but on nothing else
     for t in outs[1:]:
-        for name in ("A", "M", "D", "Ft", "xnorm2"):
+        for name in ("A", "M", "D", "Ft"):
             assert torch.equal(t[name], outs[0][name]), name
+        torch.testing.assert_close(t["xnorm2"], outs[0]["xnorm2"], rtol=1e-6, atol=0)
+    assert torch.equal(outs[1]["xnorm2"], outs[0]["xnorm2"])
+    # the tuning call leaves what later calls of the shape compute
+    for name in ("A", "M", "D", "Ft", "xnorm2"):
+        assert torch.equal(outs[3][name], outs[2][name]), name
+    # the autotuned pair is one of the candidates and is reported
+    sch, cols = ctx.projection_config()
+    assert sch in (0, 1) and cols in (256, 512)
+    # the narrower work items (256 columns) compute every column of B_k the same way
+    narrow = []
+    for sch in (0, 1, -1):
+        c = ctx.compress(Xd, off, R=10, p=10, omega=om, omega2=om2, J=300, schedule=sch, proj_cols=256)
+        narrow.append(c.tensors())
+        assert ctx.projection_config()[1] == 256
+    for t in narrow:
+        for name in ("A", "M", "D", "Ft"):
+            assert torch.equal(t[name], outs[0][name]), name
+        assert torch.equal(t["xnorm2"], narrow[0]["xnorm2"])
+        torch.testing.assert_close(t["xnorm2"], outs[0]["xnorm2"], rtol=1e-6, atol=0)
+    with pytest.raises(api.Dpar2Error):
+        ctx.compress(Xd, off, R=10, p=10, J=300, proj_cols=128)
 
 
 def test_per_slice_launches_match_grouped(api, ctx):
