@@ -288,6 +288,26 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
+// Two FP32 products in one instruction (mul.rn.f32x2): d.x = a.x b.x, d.y = a.y b.y.
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
+// Plane rotation of two entries of a column, x <- cs x + sg y, both rounded as
+// fmaf(cs, x, sg * y), two entries per packed instruction.
+__device__ __forceinline__ void rot2(float& x0, float& x1, float y0, float y1, float cs, float sg) {
+  const float2 p = fmul2(make_float2(sg, sg), make_float2(y0, y1));
+  const float2 r = ffma2(make_float2(cs, cs), make_float2(x0, x1), p);
+  x0 = r.x;
+  x1 = r.y;
+}
+
 __device__ inline void set_status(int* st, int bits) {
   if (st) atomicOr(st, bits);
 }

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(32 * EIG_WARPS) k_eig_reg(int K, const double*
         const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
         const float sg = lo ? -sn : sn;
 #pragma unroll
-        for (int i = 0; i < N; ++i) t[i] = fmaf(cs, t[i], sg * tp[i]);
+        for (int i = 0; i + 1 < N; i += 2) rot2(t[i], t[i + 1], tp[i], tp[i + 1], cs, sg);
+        if (N & 1) t[N - 1] = fmaf(cs, t[N - 1], sg * tp[N - 1]);
         na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
       }
     }

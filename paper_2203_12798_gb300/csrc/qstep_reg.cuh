@@ -212,9 +212,13 @@ __device__ __forceinline__ void qstep_warp(int K, int Ra, const float* __restric
             const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
             const float sg = lo ? -sn : sn;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-              t[i] = fmaf(cs, t[i], sg * tp[i]);
-              v[i] = fmaf(cs, v[i], sg * vp[i]);
+            for (int i = 0; i + 1 < R; i += 2) {
+              rot2(t[i], t[i + 1], tp[i], tp[i + 1], cs, sg);
+              rot2(v[i], v[i + 1], vp[i], vp[i + 1], cs, sg);
+            }
+            if (R & 1) {
+              t[R - 1] = fmaf(cs, t[R - 1], sg * tp[R - 1]);
+              v[R - 1] = fmaf(cs, v[R - 1], sg * vp[R - 1]);
             }
             na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
           }
@@ -235,12 +239,20 @@ __device__ __forceinline__ void qstep_warp(int K, int Ra, const float* __restric
             na = lo ? fmaf(-tt, gm, na) : fmaf(tt, gm, na);
           }
 #pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float tpi = __shfl_sync(FULL, t[i], src);
-            const float vpi = __shfl_sync(FULL, v[i], src);
+          for (int i = 0; i + 1 < R; i += 2) {
+            const float tp0 = __shfl_sync(FULL, t[i], src), tp1 = __shfl_sync(FULL, t[i + 1], src);
+            const float vp0 = __shfl_sync(FULL, v[i], src), vp1 = __shfl_sync(FULL, v[i + 1], src);
             if (rot) {
-              t[i] = fmaf(cs, t[i], sg * tpi);
-              v[i] = fmaf(cs, v[i], sg * vpi);
+              rot2(t[i], t[i + 1], tp0, tp1, cs, sg);
+              rot2(v[i], v[i + 1], vp0, vp1, cs, sg);
+            }
+          }
+          if (R & 1) {
+            const float tpi = __shfl_sync(FULL, t[R - 1], src);
+            const float vpi = __shfl_sync(FULL, v[R - 1], src);
+            if (rot) {
+              t[R - 1] = fmaf(cs, t[R - 1], sg * tpi);
+              v[R - 1] = fmaf(cs, v[R - 1], sg * vpi);
             }
           }
         }
