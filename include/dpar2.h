@@ -91,12 +91,11 @@ typedef struct {
   unsigned flags; /* DPAR2_FLAG_* */
   int proj_cols;  /* X columns per work item of the tensor-core projection: 0 = the widest
                      that TMEM holds double-buffered (512 for l <= 21, 256 for l <= 32, 128
-                     above), or that width halved (256 / 128); with schedule = -1 and
-                     proj_cols = 0 both widths are timed with both schedules on the first
-                     compression of a problem shape and the fastest pair is kept.  Every
-                     width computes each column of B_k identically; ||X_k||^2 is summed in
-                     FP32 within each work item, so it differs between the widths at the
-                     FP32 rounding level (the schedule changes nothing) */
+                     above), or for l <= 21 also 256; with schedule = -1 and proj_cols = 0
+                     both widths are timed with both schedules on the first compression of a
+                     problem shape and the fastest pair is kept.  Every width computes each
+                     column of B_k identically and ||X_k||^2 from the same FP32 partial sums
+                     (their FP64 total differs at the FP64 rounding level) */
 } dpar2_options;
 
 typedef struct dpar2_ctx dpar2_ctx;

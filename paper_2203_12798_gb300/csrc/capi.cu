@@ -477,8 +477,9 @@ void stage1_range(dpar2_ctx* ctx, dpar2_comp* comp, const void* X, int64_t ldx, 
       ctx->pj_last_cols = project_tc_cols(PNS, pj_cand[best].second);
       nJb_last = njb_of(pj_cand[nc - 1].second);
       if (pj_cand[best].second != pj_cand[nc - 1].second) {
-        // the ||X_k||^2 partials (FP32 within a work item) follow the width:
-        // leave those of the chosen width, as later calls of this shape will
+        // the ||X_k||^2 partials are laid out per work item (their FP64 total
+        // follows the width at the FP64 rounding level): leave those of the
+        // chosen width, as later calls of this shape will
         const ProjSched cs = proj_sched(ctx, pj_cand[best].first, off, Kc, njb_of(pj_cand[best].second), tkey, s);
         projected = launch_project_tc(X, dtype, ldx, N, d_off, d_poff, Kc, J, Jp, Qs, Npad, PNS, POFF, LP, B1, xp,
                                       njb_of(pj_cand[best].second), true, ctx->num_sms, ctx->d_status, s, cs.lptr,

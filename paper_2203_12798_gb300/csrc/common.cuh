@@ -299,11 +299,15 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
   return d;
 }
 
+// (fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y)) in two packed instructions.
+__device__ __forceinline__ float2 fmac2(float a, float2 x, float b, float2 y) {
+  return ffma2(make_float2(a, a), x, fmul2(make_float2(b, b), y));
+}
+
 // Plane rotation of two entries of a column, x <- cs x + sg y, both rounded as
 // fmaf(cs, x, sg * y), two entries per packed instruction.
 __device__ __forceinline__ void rot2(float& x0, float& x1, float y0, float y1, float cs, float sg) {
-  const float2 p = fmul2(make_float2(sg, sg), make_float2(y0, y1));
-  const float2 r = ffma2(make_float2(cs, cs), make_float2(x0, x1), p);
+  const float2 r = fmac2(cs, make_float2(x0, x1), sg, make_float2(y0, y1));
   x0 = r.x;
   x1 = r.y;
 }

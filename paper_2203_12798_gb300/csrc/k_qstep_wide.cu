@@ -215,10 +215,18 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
             cs = rsqrtf(fmaf(tt, tt, 1.f));
             sn = cs * tt;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-              const float x = top[i], y = bot[i];
-              top[i] = fmaf(cs, x, -sn * y);
-              bot[i] = fmaf(sn, x, cs * y);
+            for (int i = 0; i + 1 < R; i += 2) {
+              const float2 x = make_float2(top[i], top[i + 1]), y = make_float2(bot[i], bot[i + 1]);
+              const float2 nt = fmac2(cs, x, -sn, y), nbt = fmac2(sn, x, cs, y);
+              top[i] = nt.x;
+              top[i + 1] = nt.y;
+              bot[i] = nbt.x;
+              bot[i + 1] = nbt.y;
+            }
+            if (R & 1) {
+              const float x = top[R - 1], y = bot[R - 1];
+              top[R - 1] = fmaf(cs, x, -sn * y);
+              bot[R - 1] = fmaf(sn, x, cs * y);
             }
             na = fmaf(-tt, gm, na);
             nb = fmaf(tt, gm, nb);
@@ -311,10 +319,18 @@ __global__ void __launch_bounds__(64 * qw_pairs<R>()) k_qstep_wide(
           const float2 p = act ? rb[rr * HP + lane] : make_float2(1.f, 0.f);
           if (p.y != 0.f) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-              const float x = vt[i], y = vb[i];
-              vt[i] = fmaf(p.x, x, -p.y * y);
-              vb[i] = fmaf(p.y, x, p.x * y);
+            for (int i = 0; i + 1 < R; i += 2) {
+              const float2 x = make_float2(vt[i], vt[i + 1]), y = make_float2(vb[i], vb[i + 1]);
+              const float2 nt = fmac2(p.x, x, -p.y, y), nbt = fmac2(p.y, x, p.x, y);
+              vt[i] = nt.x;
+              vt[i + 1] = nt.y;
+              vb[i] = nbt.x;
+              vb[i + 1] = nbt.y;
+            }
+            if (R & 1) {
+              const float x = vt[R - 1], y = vb[R - 1];
+              vt[R - 1] = fmaf(p.x, x, -p.y * y);
+              vb[R - 1] = fmaf(p.y, x, p.x * y);
             }
           }
 #pragma unroll

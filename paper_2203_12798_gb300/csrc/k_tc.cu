@@ -398,6 +398,7 @@ __device__ __forceinline__ float qsplit_scale(int64_t nrows) {
 constexpr int PJ_BM = 128, PJ_BK = 64, PJ_STAGES = 5;
 constexpr int PJ_NORM_WARPS = kProjNormWarps;          // warps 6 .. 6 + PJ_NORM_WARPS - 1
 constexpr int PJ_THREADS = 32 * (6 + PJ_NORM_WARPS);
+constexpr int PJ_NORM_GROUP = 4096;  // bytes of X per FP32 partial sum of squares
 
 template <int NS_, int HV_ = (NS_ <= 64 ? 4 : (NS_ <= 128 ? 2 : 1))>
 struct ProjSmem {
@@ -652,6 +653,8 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
     // current slice only, and writes its own partial sum per work item
     // (xpart is K x nJb x PJ_NORM_WARPS; a later kernel adds them in order).
     constexpr int BYTES_PER = S::A / PJ_NORM_WARPS;
+    constexpr int GROUP = BYTES_PER < PJ_NORM_GROUP ? BYTES_PER : PJ_NORM_GROUP;
+    static_assert(BYTES_PER % GROUP == 0, "norm groups");
     const int nw = warp - 6;
     int s = 0;
     uint32_t ph = 0;
@@ -673,23 +676,28 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) k_project_tc(const __grid_const
         // last chunk is aligned to the slice's end)
         const int valid = (int)min64(PJ_BK, nrows - (int64_t)c * PJ_BK);
         const uint8_t* a = sA + s * S::A + nw * BYTES_PER;
-        float a8[8];
+        // FP32 sums over fixed 4 KB groups (32 rows of a 64-column box), so
+        // that both work-item widths form the same group sums
 #pragma unroll
-        for (int e = 0; e < 8; ++e) a8[e] = 0.f;
+        for (int g0 = 0; g0 < BYTES_PER; g0 += GROUP) {
+          float a8[8];
 #pragma unroll
-        for (int it = 0; it < BYTES_PER / 512; ++it) {
-          const int byte = nw * BYTES_PER + it * 512 + lane * 16;
-          const int row = (byte % 8192) / 128;
-          if (row >= PJ_BK - valid) {
-            const uint4 u = *reinterpret_cast<const uint4*>(a + it * 512 + lane * 16);
-            float f[8];
-            if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
-            else Vec16<__half>::unpack(u, f);
+          for (int e = 0; e < 8; ++e) a8[e] = 0.f;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) a8[e] = fmaf(f[e], f[e], a8[e]);
+          for (int it = g0 / 512; it < (g0 + GROUP) / 512; ++it) {
+            const int byte = nw * BYTES_PER + it * 512 + lane * 16;
+            const int row = (byte % 8192) / 128;
+            if (row >= PJ_BK - valid) {
+              const uint4 u = *reinterpret_cast<const uint4*>(a + it * 512 + lane * 16);
+              float f[8];
+              if (bf16) Vec16<__nv_bfloat16>::unpack(u, f);
+              else Vec16<__half>::unpack(u, f);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) a8[e] = fmaf(f[e], f[e], a8[e]);
+            }
           }
+          acc += (double)(((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7])));
         }
-        acc += (double)(((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7])));
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (++s == ST) {
@@ -885,7 +893,9 @@ void proj_layout(int ell, int* NS, int* OFF) {
 }
 
 int project_hv_default(int NS) { return NS <= 64 ? 4 : (NS <= 128 ? 2 : 1); }
-int project_hv_alt(int NS) { return NS <= 128 ? project_hv_default(NS) / 2 : 0; }
+// the narrower width only where a norm warp's share of a stage stays a whole
+// number of 4 KB groups (so that ||X_k||^2 does not depend on the width)
+int project_hv_alt(int NS) { return NS <= 64 ? project_hv_default(NS) / 2 : 0; }
 
 int project_tc_cols(int NS, int hv) { return (hv > 0 ? hv : project_hv_default(NS)) * tc::PJ_BM; }
 
