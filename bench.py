@@ -481,10 +481,11 @@ def main_ours(args):
         out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-               "config": dict(workload_config(args), projection=(
-                   {"schedule": ["round-robin", "longest-slices-first"][pj_sched], "cols_per_item": pj_cols,
-                    "chosen_by": "autotuner (both schedules x both widths timed on the first compression)"}
-                   if pj_sched >= 0 else None)),
+               "config": workload_config(args),
+               "projection": ({"schedule": ["round-robin", "longest-slices-first"][pj_sched],
+                               "cols_per_item": pj_cols,
+                               "chosen_by": "autotuner (both schedules x both widths timed on the first compression)"}
+                              if pj_sched >= 0 else None),
                "roofline": {"bound": "hbm", "kernel": f"stage-1 {dom} pass", "achieved": achieved, "peak": peak,
                             "unit": "GB/s", "frac": achieved / peak, "traffic": measured_traffic(dom, dom_bytes, args),
                             "peak_source": peak_src,
