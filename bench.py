@@ -383,13 +383,17 @@ def main_ours(args):
         for _ in range(max(1, args.warmup - 1)):
             host_step()
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        for _ in range(args.steps):
+        # one event per step boundary: the total gives the value, the steps their
+        # spread (the host link is shared with other work on the machine)
+        fev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        fev[0].record()
+        for i in range(args.steps):
             res_h = host_step()
-        f1.record()
+            fev[i + 1].record()
         barrier()
-        e2e_ms = f0.elapsed_time(f1) / args.steps
+        torch.cuda.synchronize()
+        e2e_ms = fev[0].elapsed_time(fev[-1]) / args.steps
+        e2e_steps = sorted(fev[i].elapsed_time(fev[i + 1]) for i in range(args.steps))
         # the link's reference rate: one pinned host->device copy of the same bytes
         Xpk = torch.empty(N, J, dtype=tdt, device="cuda")
         h2d = []
@@ -427,6 +431,8 @@ def main_ours(args):
                "h2d_link_gbs": h2d_gbs, "link_bound_s": xbytes / (h2d_gbs * 1e9),
                "frac_of_link_bound": (xbytes / (h2d_gbs * 1e9)) / (e2e_ms / 1e3),
                "upload_then_compress_s": up_ms / 1e3,
+               "step_s": {"min": e2e_steps[0] / 1e3, "median": e2e_steps[len(e2e_steps) // 2] / 1e3,
+                          "max": e2e_steps[-1] / 1e3},
                "link_note": "link rate = one pinned cudaMemcpyAsync of the same bytes (packed rows); "
                             "upload_then_compress = dpar2_upload_rows of all of X, then dpar2_compress + dpar2_fit"}
         del Xh, Xd
