@@ -320,9 +320,10 @@ DPAR2_API dpar2_status dpar2_comp_view_get(const dpar2_comp* comp, dpar2_comp_vi
  * (FP32 X, CUDA-core passes).  Host values; the paper has no counterpart. */
 DPAR2_API dpar2_status dpar2_projection_config(const dpar2_ctx* ctx, int* schedule, int* cols);
 /* M (device K x J x R FP32, block k = C_k B_k) reassembled from the three BF16
- * parts of M^T the compression holds (inspection; stream-ordered on `stream`,
- * NULL = the context's stream).  Errors: INVALID_ARG for a null argument or a
- * compression whose M was dropped (DPAR2_FLAG_DROP_M). */
+ * parts of M^T the compression holds (inspection; ordered after the work
+ * already queued on `stream`, NULL = the default stream, and complete when the
+ * call returns).  Errors: INVALID_ARG for a null argument or a compression
+ * whose M was dropped (DPAR2_FLAG_DROP_M). */
 DPAR2_API dpar2_status dpar2_comp_m(dpar2_ctx* ctx, const dpar2_comp* comp, float* M, void* stream);
 DPAR2_API void dpar2_comp_free(dpar2_comp* comp);
 
